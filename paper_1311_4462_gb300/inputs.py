@@ -1,0 +1,90 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only draws random numbers; it holds none of the operator's arithmetic.
+
+* Links: U = exp(i * 0.3 * H) per link, H traceless hermitian built from a 3x3 matrix
+  A with iid N(0,1) real and imaginary parts, H = (A + A^dag)/2 - tr(.)/3.  The
+  exponential is taken through a hermitian eigendecomposition; rows 1-2 are then
+  re-orthonormalised and row 3 is set to conj(row1 x row2), so every link is in
+  SU(3) to rounding (which makes 12-real storage exact).
+* Spinors: iid N(0,1) real and imaginary parts per (site, flavour, spin, colour).
+* Z2 noise: (+-1 +- i)/sqrt(2) per entry.
+* Generators: numpy PCG64; seed conventions gauge 1000+k, spinor 2000+k, noise 3000+n.
+
+Canonical layouts (x fastest): spinor [Lt, Lz, Ly, Lx, nf, 4, 3],
+gauge [4, Lt, Lz, Ly, Lx, 3, 3] with mu = 0..3 <-> x, y, z, t.
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _expi_herm(H: np.ndarray, scale: float) -> np.ndarray:
+    w, V = np.linalg.eigh(H)
+    return (V * np.exp(1j * scale * w)[..., None, :]) @ np.conj(np.swapaxes(V, -1, -2))
+
+
+def reunitarize(U: np.ndarray) -> np.ndarray:
+    """Gram-Schmidt on rows 1 and 2, row 3 = conj(row1 x row2): the nearest-by-construction SU(3) matrix."""
+    r1 = U[..., 0, :]
+    r1 = r1 / np.linalg.norm(r1, axis=-1, keepdims=True)
+    r2 = U[..., 1, :]
+    r2 = r2 - np.sum(np.conj(r1) * r2, axis=-1, keepdims=True) * r1
+    r2 = r2 / np.linalg.norm(r2, axis=-1, keepdims=True)
+    r3 = np.conj(np.cross(r1, r2))
+    return np.stack([r1, r2, r3], axis=-2)
+
+
+def random_su3(n: int, g: np.random.Generator, scale: float = 0.3) -> np.ndarray:
+    A = g.standard_normal((n, 3, 3)) + 1j * g.standard_normal((n, 3, 3))
+    H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+    tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
+    H = H - tr[:, None, None] * np.eye(3)
+    chunks = np.array_split(H, max(1, min(64, n // 65536)))
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        U = np.concatenate(list(ex.map(lambda h: _expi_herm(h, scale), chunks)), axis=0)
+    return reunitarize(U)
+
+
+def gauge_field(L, seed: int, scale: float = 0.3) -> np.ndarray:
+    Lx, Ly, Lz, Lt = L
+    n = 4 * Lx * Ly * Lz * Lt
+    return random_su3(n, rng(seed), scale).reshape(4, Lt, Lz, Ly, Lx, 3, 3)
+
+
+def spinor_field(L, nf: int, seed: int) -> np.ndarray:
+    Lx, Ly, Lz, Lt = L
+    g = rng(seed)
+    shape = (Lt, Lz, Ly, Lx, nf, 4, 3)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def z2_noise(L, nf: int, seed: int) -> np.ndarray:
+    Lx, Ly, Lz, Lt = L
+    g = rng(seed)
+    shape = (Lt, Lz, Ly, Lx, nf, 4, 3)
+    re = 2.0 * g.integers(0, 2, size=shape) - 1.0
+    im = 2.0 * g.integers(0, 2, size=shape) - 1.0
+    return (re + 1j * im) / np.sqrt(2.0)
+
+
+def gauge_transform(L, seed: int) -> np.ndarray:
+    """Random SU(3) matrix per site, [Lt, Lz, Ly, Lx, 3, 3] (for gauge-covariance checks)."""
+    Lx, Ly, Lz, Lt = L
+    return random_su3(Lx * Ly * Lz * Lt, rng(seed), scale=1.5).reshape(Lt, Lz, Ly, Lx, 3, 3)
+
+
+def su3_algebra_direction(shape, seed: int) -> np.ndarray:
+    """Random traceless hermitian 3x3 matrices of the given leading shape (tangent directions)."""
+    g = rng(seed)
+    A = g.standard_normal(tuple(shape) + (3, 3)) + 1j * g.standard_normal(tuple(shape) + (3, 3))
+    H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+    tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
+    return H - tr[..., None, None] * np.eye(3)
