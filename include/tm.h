@@ -1,0 +1,189 @@
+/*
+ * tm.h -- C ABI of libtm: the even-odd preconditioned Wilson twisted-mass operator
+ * (degenerate and non-degenerate doublet) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Operator (eq. 2.1, kappa normalisation, DeGrand-Rossi gamma matrices, mu = x,y,z,t):
+ *   M psi(x) = R psi(x) - kappa (H psi)(x)
+ *   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)
+ *   R = 1 + 2 i kappa mu gamma5 tau3 + 2 kappa epsilon tau1       (doublet, tau on flavour)
+ *   R = 1 + 2 i kappa mu (+-1) gamma5                            (one flavour, tau3 = +-1)
+ * Periodic in x, y, z; hops across the time boundary carry -1 when t_antiperiodic != 0.
+ * H^dag is H with the two projectors exchanged; R^dag = R(-mu, epsilon).
+ * The even-odd blocks are H_eo (odd -> even) and H_oe (even -> odd); the paper's D_eo is read
+ * as H_eo, which makes the left-hand sides of eq. 2.2 and 2.3 the exact Schur complements.
+ *
+ * Conventions shared by every call:
+ *  - All pointers to field or gauge data are DEVICE pointers (cudaMalloc'd or from an
+ *    allocator such as torch).  The caller owns every field; the library never frees one.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call except
+ *    tm_gauge_create / tm_gauge_destroy / tm_solve / tm_solve_multi only enqueues work on
+ *    `stream` and returns; errors found on the host are reported before anything is enqueued.
+ *  - Every call returns a tm_status; nothing throws across the ABI.  tm_last_error() gives a
+ *    one-line message for the last failing call on the calling host thread.
+ *  - Calls that share one tm_gauge use its small reduction scratch area and must therefore be
+ *    ordered on one stream (calls on different streams that overlap on the GPU race).
+ *
+ * Field storage (tm_field): one parity of a spinor field in structure-of-arrays form,
+ *   data: [nrhs][nf][chunk][Vh] with the 24 reals of a site, ordered (spin*3 + colour)*2 + re/im,
+ *         cut into 16-byte chunks (FP64: 12, FP32: 6, FP16: 3 chunks per site and flavour);
+ *   norm: FP16 only, float [nrhs][nf][Vh], the site's max |real| (stored half = value / norm).
+ * Vh = Lx Ly Lz Lt / 2; even sites have (x+y+z+t) even; site index within a parity is
+ * (x + Lx (y + Ly (z + Lz t))) / 2.  tm_field_bytes() gives the sizes to allocate.
+ *
+ * Canonical (user) layout, complex128 or complex64, x fastest:
+ *   spinor [Lt][Lz][Ly][Lx][nf][4][3],  gauge [4][Lt][Lz][Ly][Lx][3][3] (row-major 3x3).
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TM_OK = 0,
+    TM_ERR_ARG = -1,     /* invalid argument (null pointer, odd extent, singular twist, ...) */
+    TM_ERR_CUDA = -2,    /* a CUDA call or kernel launch failed */
+    TM_ERR_NOCONV = -3,  /* solver hit maxiter before reaching the tolerance */
+    TM_ERR_NAN = -4,     /* solver saw a non-finite residual */
+    TM_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    TM_ERR_NOMEM = -6    /* device allocation failed, or a workspace is too small */
+} tm_status;
+
+/* twist_flavor (sec. 2.2): one flavour with tau3 = +1 / -1, or the two-flavour doublet. */
+typedef enum { TM_TWIST_PLUS = 1, TM_TWIST_MINUS = -1, TM_NDEG_DOUBLET = 2 } tm_flavor;
+/* storage precision: bytes per real; FP16 carries a per-site float norm, arithmetic is FP32. */
+typedef enum { TM_PREC_F64 = 8, TM_PREC_F32 = 4, TM_PREC_F16 = 2 } tm_prec;
+/* gauge link storage (sec. 3): 18 reals, 2 rows (12 reals), or 8 reals. */
+typedef enum { TM_RECON_18 = 18, TM_RECON_12 = 12, TM_RECON_8 = 8 } tm_recon;
+/* even-odd preconditioning: asymmetric (eq. 2.2) or symmetric (eq. 2.3). */
+typedef enum { TM_PC_ASYM = 0, TM_PC_SYM = 1 } tm_pc;
+/* canonical element type */
+typedef enum { TM_C128 = 0, TM_C64 = 1 } tm_canon;
+
+/*
+ * Fused local operation applied at the output site of tm_dslash (sec. 2.1, "all local
+ * operators are merged into dslash kernels"); D = H or H^dag, t = the input, x = the extra
+ * field argument, R / R^-1 daggered in tm_dslash_dagger:
+ */
+typedef enum {
+    TM_EPI_NONE = 0,        /* out = D t                                                    */
+    TM_EPI_TWINV = 1,       /* out = R^-1 D t             the fused R^-1_oo D_oe of sec. 2.1 */
+    TM_EPI_TWXPAY_ASYM = 2, /* out = R x - kappa^2 D t    the fused R_ee - kappa^2 D_eo      */
+    TM_EPI_TWXPAY_SYM = 3,  /* out = x - kappa^2 R^-1 D t (eq. 2.3)                         */
+    TM_EPI_XPAY = 4,        /* out = x + kappa D t                                          */
+    TM_EPI_TWINV_XPAY = 5   /* out = R^-1 (x + kappa D t)  odd-site reconstruction          */
+} tm_epilogue;
+
+typedef struct {
+    int L[4];             /* Lx, Ly, Lz, Lt: each even and >= 2; Vh = Lx Ly Lz Lt / 2 < 2^31 / 24 */
+    double kappa;         /* hopping parameter */
+    double mu;            /* twisted mass mu (mu-bar for the doublet) */
+    double epsilon;       /* epsilon-bar of the doublet; must be 0 for TM_TWIST_PLUS/MINUS */
+    int flavor;           /* tm_flavor */
+    int t_antiperiodic;   /* 1: antiperiodic in time, 0: periodic */
+    int recon;            /* tm_recon, used for every precision of the gauge handle */
+} tm_params;
+
+typedef struct {
+    void *data;  /* device pointer, layout above */
+    float *norm; /* device pointer, FP16 only (NULL otherwise) */
+    int prec;    /* tm_prec */
+    int nrhs;    /* right-hand sides stored back to back (1 for single fields) */
+} tm_field;
+
+typedef struct tm_gauge tm_gauge; /* opaque: packed links in FP64, FP32 and FP16 + scratch */
+
+/* Library version string. */
+const char *tm_version(void);
+
+/* Copy the message of the last failing call on this host thread into buf (NUL-terminated). */
+tm_status tm_last_error(char *buf, size_t n);
+
+/*
+ * Create a gauge handle on the current CUDA device.  U_canon: device pointer to the canonical
+ * complex128 gauge field (see above); it is read once and may be freed after the call
+ * returns.  The handle allocates and owns device memory for the packed links in all three
+ * precisions plus a reduction scratch area; it synchronises `stream` before returning.
+ * Errors: TM_ERR_ARG (params, null pointers, 1 + (2 kappa mu)^2 - (2 kappa eps)^2 <= 0 with
+ * a doublet), TM_ERR_NOMEM, TM_ERR_CUDA.
+ */
+tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out);
+
+/* Release a handle (NULL is accepted).  Waits for the device to finish using it. */
+tm_status tm_gauge_destroy(tm_gauge *g);
+
+/* Bytes to allocate for one parity field of `prec` with the handle's flavour count and nrhs. */
+tm_status tm_field_bytes(const tm_gauge *g, int prec, int nrhs, size_t *data_bytes, size_t *norm_bytes);
+
+/*
+ * Convert between the canonical full-lattice layout and one parity of a tm_field (the
+ * "converting routines" between a client's layout and the internal one, sec. 2).  pack reads
+ * the sites of `parity` from canon (canon_type = tm_canon); unpack writes only those sites of
+ * canon and leaves the others untouched.  For nrhs > 1 canon holds nrhs fields back to back.
+ */
+tm_status tm_pack(const tm_gauge *g, const tm_field *out, const void *canon, int canon_type, int parity,
+                  void *stream);
+tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_field *in, int parity,
+                    void *stream);
+
+/*
+ * One fused hopping kernel (sec. 2.1):  out(out_parity) = epilogue(H_{p,1-p} in), with
+ * H^dag and daggered twists in tm_dslash_dagger.  `x` has the output parity and is used by
+ * the XPAY epilogues (NULL otherwise).  out, in and x must share a precision; out must not
+ * alias in.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                    const tm_field *x, void *stream);
+tm_status tm_dslash_dagger(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity,
+                           int epilogue, const tm_field *x, void *stream);
+
+/*
+ * Even-even preconditioned operator, two fused launches through the odd temporary tmp_o:
+ *   TM_PC_ASYM:  out = (R_ee - kappa^2 H_eo R_oo^-1 H_oe) in               (eq. 2.2 LHS)
+ *   TM_PC_SYM:   out = (1 - kappa^2 R_ee^-1 H_eo R_oo^-1 H_oe) in          (eq. 2.3 LHS)
+ * dagger = 1 applies the adjoint (for SYM: 1 - kappa^2 H^dag_eo R_oo^-dag H^dag_oe R_ee^-dag,
+ * whose first launch twists every neighbour before the projection).  Fields share one
+ * precision; tmp_o is overwritten.
+ */
+tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
+                        int pc, int dagger, void *stream);
+
+/*
+ * Full unpreconditioned operator (eq. 2.1) on both parities: out = M in (dagger = 0) or
+ * M^dag in.  Two fused launches; out must not alias in.
+ */
+tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,
+                 const tm_field *in_o, int dagger, void *stream);
+
+/*
+ * Right-hand side of the even system from the full source b (eq. 2.2 / 2.3 RHS, derived by
+ * block elimination of M psi = b; the printed RHS is read with the sign and kappa of that
+ * elimination):
+ *   ASYM:  b'_e = b_e + kappa H_eo R_oo^-1 b_o
+ *   SYM:   b'_e = R_ee^-1 (b_e + kappa H_eo R_oo^-1 b_o)
+ * dagger = 1 daggers every factor (source of M^dag psi = b).  For SYM with dagger = 1 the
+ * system is preconditioned from the right, M_sym^dag y = b'_e with b'_e as for ASYM, and
+ * psi_e = R_ee^-dag y.  One fused launch (input twist in the prologue).
+ */
+tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_field *b_e, const tm_field *b_o,
+                         int pc, int dagger, void *stream);
+
+/*
+ * Odd half of the solution (eq. 2.4, read as the block elimination of M psi = b):
+ *   psi_o = R_oo^-1 (b_o + kappa H_oe psi_e)        (daggered factors when dagger = 1)
+ * One fused launch.
+ */
+tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_field *b_o, const tm_field *psi_e,
+                             int dagger, void *stream);
+
+/* Local twist on one parity: out = R in, R^-1 in (inverse = 1), daggered when dagger = 1. */
+tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H */

@@ -1,0 +1,196 @@
+"""GB300-native even-odd preconditioned Wilson twisted-mass operator (arXiv:1311.4462).
+
+Thin Python binding over ``libtm.so`` (C ABI: include/tm.h).  Every step of the operator
+runs in the library's CUDA kernels; torch only provides device memory and streams.  The
+functions below carry the same names as the C entry points without the ``tm_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib as L
+from ._lib import (TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM,
+                   TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_NDEG_DOUBLET, TM_PC_ASYM, TM_PC_SYM, TM_PREC_F16, TM_PREC_F32,
+                   TM_PREC_F64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
+
+PRECS = {"f64": TM_PREC_F64, "f32": TM_PREC_F32, "f16": TM_PREC_F16}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Params:
+    """Lattice and operator parameters (tm_params).  flavor: +1, -1 (one flavour) or 2 (doublet)."""
+
+    def __init__(self, L, kappa, mu, eps=0.0, flavor=TM_NDEG_DOUBLET, t_antiperiodic=True, recon=12):
+        self.L = tuple(int(v) for v in L)
+        self.kappa, self.mu, self.eps = float(kappa), float(mu), float(eps)
+        self.flavor = int(flavor)
+        self.t_antiperiodic = bool(t_antiperiodic)
+        self.recon = int(recon)
+
+    @property
+    def nf(self):
+        return 2 if self.flavor == TM_NDEG_DOUBLET else 1
+
+    @property
+    def volume(self):
+        Lx, Ly, Lz, Lt = self.L
+        return Lx * Ly * Lz * Lt
+
+    @property
+    def Vh(self):
+        return self.volume // 2
+
+    @property
+    def spinor_shape(self):
+        Lx, Ly, Lz, Lt = self.L
+        return (Lt, Lz, Ly, Lx, self.nf, 4, 3)
+
+    @property
+    def gauge_shape(self):
+        Lx, Ly, Lz, Lt = self.L
+        return (4, Lt, Lz, Ly, Lx, 3, 3)
+
+    def c(self):
+        p = L.tm_params()
+        p.L[:] = self.L
+        p.kappa, p.mu, p.epsilon = self.kappa, self.mu, self.eps
+        p.flavor, p.t_antiperiodic, p.recon = self.flavor, int(self.t_antiperiodic), self.recon
+        return p
+
+
+class Gauge:
+    """tm_gauge handle: packed links in FP64/FP32/FP16 (the handle's recon) on the current device."""
+
+    def __init__(self, params: Params, U, stream=None):
+        torch = _torch()
+        self.params = params
+        U = torch.as_tensor(U)
+        if U.device.type != "cuda":
+            U = U.to("cuda")
+        U = U.to(torch.complex128).contiguous()
+        assert tuple(U.shape) == params.gauge_shape, (U.shape, params.gauge_shape)
+        h = ctypes.c_void_p()
+        self._pc = params.c()
+        L.check(L.load().tm_gauge_create(ctypes.byref(self._pc), ctypes.c_void_p(U.data_ptr()), _stream(stream),
+                                         ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            L.load().tm_gauge_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_bytes(self, prec, nrhs=1):
+        d, n = ctypes.c_size_t(), ctypes.c_size_t()
+        L.check(L.load().tm_field_bytes(self.h, int(prec), int(nrhs), ctypes.byref(d), ctypes.byref(n)))
+        return d.value, n.value
+
+
+class Field:
+    """One parity of a spinor field in the library's layout; memory from torch."""
+
+    def __init__(self, gauge: Gauge, prec=TM_PREC_F32, nrhs=1):
+        torch = _torch()
+        self.gauge, self.prec, self.nrhs = gauge, int(prec), int(nrhs)
+        nd, nn = gauge.field_bytes(self.prec, self.nrhs)
+        self.data = torch.empty(nd, dtype=torch.uint8, device="cuda")
+        self.norm = torch.empty(max(nn // 4, 1), dtype=torch.float32, device="cuda") if nn else None
+        self.c = L.tm_field(self.data.data_ptr(), self.norm.data_ptr() if self.norm is not None else None, self.prec,
+                            self.nrhs)
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+    def zero_(self):
+        self.data.zero_()
+        if self.norm is not None:
+            self.norm.zero_()
+        return self
+
+
+def pack(gauge: Gauge, canon, parity: int, prec=TM_PREC_F32, nrhs=1, out: Field = None, stream=None) -> Field:
+    """tm_pack: canonical complex128/complex64 device tensor -> one parity Field."""
+    torch = _torch()
+    canon = torch.as_tensor(canon)
+    if canon.device.type != "cuda":
+        canon = canon.to("cuda")
+    canon = canon.contiguous()
+    ct = L.TM_C128 if canon.dtype == torch.complex128 else L.TM_C64
+    if canon.dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("canonical fields are complex128 or complex64")
+    f = out if out is not None else Field(gauge, prec, nrhs)
+    L.check(L.load().tm_pack(gauge.h, f.ref(), ctypes.c_void_p(canon.data_ptr()), ct, int(parity), _stream(stream)))
+    return f
+
+
+def unpack(gauge: Gauge, field: Field, parity: int, canon=None, dtype=None, stream=None):
+    """tm_unpack: writes the sites of `parity` into canon (a new zero tensor if None)."""
+    torch = _torch()
+    shape = gauge.params.spinor_shape
+    if field.nrhs > 1:
+        shape = (field.nrhs,) + shape
+    if canon is None:
+        canon = torch.zeros(shape, dtype=dtype or torch.complex128, device="cuda")
+    ct = L.TM_C128 if canon.dtype == torch.complex128 else L.TM_C64
+    L.check(L.load().tm_unpack(gauge.h, ctypes.c_void_p(canon.data_ptr()), ct, field.ref(), int(parity),
+                               _stream(stream)))
+    return canon
+
+
+def dslash(gauge, out: Field, inp: Field, out_parity: int, epilogue=TM_EPI_NONE, x: Field = None, stream=None):
+    L.check(L.load().tm_dslash(gauge.h, out.ref(), inp.ref(), int(out_parity), int(epilogue),
+                               x.ref() if x is not None else None, _stream(stream)))
+    return out
+
+
+def dslash_dagger(gauge, out: Field, inp: Field, out_parity: int, epilogue=TM_EPI_NONE, x: Field = None, stream=None):
+    L.check(L.load().tm_dslash_dagger(gauge.h, out.ref(), inp.ref(), int(out_parity), int(epilogue),
+                                      x.ref() if x is not None else None, _stream(stream)))
+    return out
+
+
+def precond_op(gauge, out_e: Field, in_e: Field, tmp_o: Field, pc=TM_PC_ASYM, dagger=False, stream=None):
+    L.check(L.load().tm_precond_op(gauge.h, out_e.ref(), in_e.ref(), tmp_o.ref(), int(pc), int(dagger),
+                                   _stream(stream)))
+    return out_e
+
+
+def mat(gauge, out_e: Field, out_o: Field, in_e: Field, in_o: Field, dagger=False, stream=None):
+    L.check(L.load().tm_mat(gauge.h, out_e.ref(), out_o.ref(), in_e.ref(), in_o.ref(), int(dagger), _stream(stream)))
+    return out_e, out_o
+
+
+def prepare_rhs(gauge, bprime_e: Field, b_e: Field, b_o: Field, pc=TM_PC_ASYM, dagger=False, stream=None):
+    L.check(L.load().tm_prepare_rhs(gauge.h, bprime_e.ref(), b_e.ref(), b_o.ref(), int(pc), int(dagger),
+                                    _stream(stream)))
+    return bprime_e
+
+
+def reconstruct_odd(gauge, psi_o: Field, b_o: Field, psi_e: Field, dagger=False, stream=None):
+    L.check(L.load().tm_reconstruct_odd(gauge.h, psi_o.ref(), b_o.ref(), psi_e.ref(), int(dagger), _stream(stream)))
+    return psi_o
+
+
+def twist(gauge, out: Field, inp: Field, inverse=False, dagger=False, stream=None):
+    L.check(L.load().tm_twist(gauge.h, out.ref(), inp.ref(), int(inverse), int(dagger), _stream(stream)))
+    return out
+
+
+def version() -> str:
+    return L.load().tm_version().decode()

@@ -1,0 +1,92 @@
+"""ctypes declarations for libtm.so (the C ABI in include/tm.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtm.so")
+
+TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOCONV, TM_ERR_NAN, TM_ERR_TIMEOUT, TM_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "TM_OK", -1: "TM_ERR_ARG", -2: "TM_ERR_CUDA", -3: "TM_ERR_NOCONV", -4: "TM_ERR_NAN",
+                -5: "TM_ERR_TIMEOUT", -6: "TM_ERR_NOMEM"}
+TM_TWIST_PLUS, TM_TWIST_MINUS, TM_NDEG_DOUBLET = 1, -1, 2
+TM_PREC_F64, TM_PREC_F32, TM_PREC_F16 = 8, 4, 2
+TM_PC_ASYM, TM_PC_SYM = 0, 1
+TM_C128, TM_C64 = 0, 1
+TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_EPI_TWINV_XPAY = range(6)
+TM_SOLVER_CG, TM_SOLVER_MIXED = 0, 1
+TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT = 0, 1
+
+
+class tm_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
+                ("epsilon", ctypes.c_double), ("flavor", ctypes.c_int), ("t_antiperiodic", ctypes.c_int),
+                ("recon", ctypes.c_int)]
+
+
+class tm_field(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("prec", ctypes.c_int), ("nrhs", ctypes.c_int)]
+
+
+class TMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+vp = ctypes.c_void_p
+FP = ctypes.POINTER(tm_field)
+
+# name -> argtypes (restype is tm_status = int unless noted)
+_SIGS = {
+    "tm_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+    "tm_gauge_create": [ctypes.POINTER(tm_params), vp, vp, ctypes.POINTER(vp)],
+    "tm_gauge_destroy": [vp],
+    "tm_field_bytes": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                       ctypes.POINTER(ctypes.c_size_t)],
+    "tm_pack": [vp, FP, vp, ctypes.c_int, ctypes.c_int, vp],
+    "tm_unpack": [vp, vp, ctypes.c_int, FP, ctypes.c_int, vp],
+    "tm_dslash": [vp, FP, FP, ctypes.c_int, ctypes.c_int, FP, vp],
+    "tm_dslash_dagger": [vp, FP, FP, ctypes.c_int, ctypes.c_int, FP, vp],
+    "tm_precond_op": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
+    "tm_mat": [vp, FP, FP, FP, FP, ctypes.c_int, vp],
+    "tm_prepare_rhs": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
+    "tm_reconstruct_odd": [vp, FP, FP, FP, ctypes.c_int, vp],
+    "tm_twist": [vp, FP, FP, ctypes.c_int, ctypes.c_int, vp],
+}
+
+
+def load():
+    """Load libtm.so.  There is no fallback: a missing or stale library is an error."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtm.so is not built ({LIB_PATH}); run paper_1311_4462_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.tm_version.restype = ctypes.c_char_p
+    lib.tm_version.argtypes = []
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().tm_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int):
+    if status != TM_OK:
+        raise TMError(status, last_error())
+    return status
+
+
+def exported_names():
+    return ["tm_version"] + list(_SIGS)

@@ -1,0 +1,474 @@
+// tm_api.cu -- the C ABI declared in include/tm.h: validation, the gauge handle, and the
+// composition of fused launches into the preconditioned operators of eq. 2.2-2.4.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "tm_dslash.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
+cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
+cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
+cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void *canon, int ctype, int parity,
+                               cudaStream_t s);
+cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, const tm_field *f, int parity,
+                                 cudaStream_t s);
+cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void *canon, cudaStream_t s);
+cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
+                         cudaStream_t s);
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+tm_status cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TM_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return TM_ERR_CUDA;
+}
+
+int prec_index(int prec)
+{
+    switch (prec) {
+    case TM_PREC_F64: return 0;
+    case TM_PREC_F32: return 1;
+    case TM_PREC_F16: return 2;
+    default: return -1;
+    }
+}
+
+int spinor_chunks(int prec) { return prec == TM_PREC_F64 ? 12 : (prec == TM_PREC_F32 ? 6 : 3); }
+size_t chunk_bytes(int) { return 16; }
+
+static int link_reals_per_chunk(int prec, int recon)
+{
+    // chunk geometry of LinkLayout<PREC, RECON> in tm_core.cuh
+    if (prec == TM_PREC_F64) return 2;
+    if (prec == TM_PREC_F32) return recon == 18 ? 2 : 4;
+    return recon == 18 ? 2 : (recon == 12 ? 4 : 8);
+}
+static size_t link_chunk_bytes(int prec, int recon) { return (size_t)link_reals_per_chunk(prec, recon) * prec; }
+
+// ---------------------------------------------------------------------------- twist tables
+// R = 1 + i a gamma5 tau3 + b tau1 (doublet) or 1 + i a s gamma5 (one flavour, s = +-1), with
+// a = 2 kappa mu, b = 2 kappa eps; gamma5 = +1 on spins 0,1 and -1 on spins 2,3.
+//   R^-1 = (1 - i a gamma5 tau3 - b tau1) / (1 + a^2 - b^2)   (doublet; X^2 = b^2 - a^2)
+//   R^-1 = (1 - i a s gamma5) / (1 + a^2)                      (one flavour)
+// R^dag = R(a -> -a); R^-dag = R^-1(a -> -a).
+static Twist<double> make_twist(const tm_gauge *g, int kind, int dagger)
+{
+    Twist<double> t;
+    memset(&t, 0, sizeof(t));
+    double a = 2.0 * g->p.kappa * g->p.mu;
+    const double b = 2.0 * g->p.kappa * g->p.epsilon;
+    if (dagger) a = -a;
+    for (int gi = 0; gi < 2; gi++) {
+        const double g5 = gi == 0 ? 1.0 : -1.0;
+        if (g->nf == 2) {
+            if (kind == TW_R) {
+                t.m[gi][0][0] = {1.0, a * g5};
+                t.m[gi][1][1] = {1.0, -a * g5};
+                t.m[gi][0][1] = t.m[gi][1][0] = {b, 0.0};
+            } else {
+                const double d = 1.0 / (1.0 + a * a - b * b);
+                t.m[gi][0][0] = {d, -a * g5 * d};
+                t.m[gi][1][1] = {d, a * g5 * d};
+                t.m[gi][0][1] = t.m[gi][1][0] = {-b * d, 0.0};
+            }
+        } else {
+            const double s = (double)g->p.flavor;
+            if (kind == TW_R) {
+                t.m[gi][0][0] = {1.0, a * s * g5};
+            } else {
+                const double d = 1.0 / (1.0 + a * a);
+                t.m[gi][0][0] = {d, -a * s * g5 * d};
+            }
+        }
+    }
+    return t;
+}
+
+static Twist<float> to_float(const Twist<double> &t)
+{
+    Twist<float> f;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+            for (int k = 0; k < 2; k++) f.m[i][j][k] = {(float)t.m[i][j][k].r, (float)t.m[i][j][k].i};
+    return f;
+}
+
+// ----------------------------------------------------------------------------- validation
+static tm_status check_field(const tm_gauge *g, const tm_field *f, const char *name)
+{
+    if (!f) { set_error("%s: null tm_field", name); return TM_ERR_ARG; }
+    if (prec_index(f->prec) < 0) { set_error("%s: unknown precision %d", name, f->prec); return TM_ERR_ARG; }
+    if (!f->data) { set_error("%s: null data pointer", name); return TM_ERR_ARG; }
+    if (f->prec == TM_PREC_F16 && !f->norm) { set_error("%s: FP16 field needs a norm array", name); return TM_ERR_ARG; }
+    if (f->nrhs < 1) { set_error("%s: nrhs must be >= 1", name); return TM_ERR_ARG; }
+    if (((uintptr_t)f->data & 15) != 0) { set_error("%s: data must be 16-byte aligned", name); return TM_ERR_ARG; }
+    (void)g;
+    return TM_OK;
+}
+
+static tm_status check_params(const tm_params *p)
+{
+    if (!p) { set_error("null tm_params"); return TM_ERR_ARG; }
+    long V = 1;
+    for (int m = 0; m < 4; m++) {
+        if (p->L[m] < 2 || (p->L[m] & 1)) {
+            set_error("L[%d] = %d: every extent must be even and >= 2", m, p->L[m]);
+            return TM_ERR_ARG;
+        }
+        V *= p->L[m];
+    }
+    if (V / 2 > (long)(0x7fffffff / 24)) { set_error("lattice too large for 32-bit site indexing"); return TM_ERR_ARG; }
+    if (p->flavor != TM_TWIST_PLUS && p->flavor != TM_TWIST_MINUS && p->flavor != TM_NDEG_DOUBLET) {
+        set_error("unknown flavor %d", p->flavor);
+        return TM_ERR_ARG;
+    }
+    if (p->flavor != TM_NDEG_DOUBLET && p->epsilon != 0.0) {
+        set_error("epsilon must be 0 for a single flavour");
+        return TM_ERR_ARG;
+    }
+    if (p->recon != 18 && p->recon != 12 && p->recon != 8) { set_error("recon must be 18, 12 or 8"); return TM_ERR_ARG; }
+    if (!(p->kappa > 0.0) || !isfinite(p->kappa) || !isfinite(p->mu) || !isfinite(p->epsilon)) {
+        set_error("kappa must be positive; kappa, mu, epsilon finite");
+        return TM_ERR_ARG;
+    }
+    const double a = 2 * p->kappa * p->mu, b = 2 * p->kappa * p->epsilon;
+    if (1.0 + a * a - b * b <= 1e-12) {
+        set_error("twist R is singular or indefinite: 1 + (2 kappa mu)^2 - (2 kappa eps)^2 = %g", 1.0 + a * a - b * b);
+        return TM_ERR_ARG;
+    }
+    return TM_OK;
+}
+
+// ------------------------------------------------------------------------------- dslash core
+template <typename T>
+static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out, const tm_field *in,
+                        const tm_field *x, int out_parity, int pidx)
+{
+    a.out = out->data;
+    a.out_norm = out->norm;
+    a.in = in->data;
+    a.in_norm = in->norm;
+    a.x = x ? x->data : nullptr;
+    a.x_norm = x ? x->norm : nullptr;
+    a.gauge = g->links[pidx];
+    a.Vh = g->Vh;
+    a.X1h = g->X1h;
+    a.Lx = g->p.L[0];
+    a.Ly = g->p.L[1];
+    a.Lz = g->p.L[2];
+    a.Lt = g->p.L[3];
+    a.out_parity = out_parity;
+    a.tbc = g->p.t_antiperiodic ? 1 : 0;
+}
+
+// Generic fused hopping launch: out = epi(H or H^dag (pro(in))).
+static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x,
+                               int out_parity, int dagger, int epi, double coef, const Twist<double> *tw_epi,
+                               const Twist<double> *tw_pro, cudaStream_t s)
+{
+    const int pidx = prec_index(in->prec);
+    const bool pro = tw_pro != nullptr;
+    Twist<double> z;
+    memset(&z, 0, sizeof(z));
+    const Twist<double> &te = tw_epi ? *tw_epi : z, &tp = tw_pro ? *tw_pro : z;
+    const int block = 128;
+    cudaError_t e;
+    if (pidx == 0) {
+        DslashArgs<double> a;
+        fill_common(a, g, out, in, x, out_parity, pidx);
+        a.epilogue = epi;
+        a.sigma = dagger ? -1.0 : 1.0;
+        a.coef = coef;
+        a.tw_epi = te;
+        a.tw_pro = tp;
+        e = launch_dslash_p64(a, g->nf, g->p.recon, pro, block, s);
+    } else {
+        DslashArgs<float> a;
+        fill_common(a, g, out, in, x, out_parity, pidx);
+        a.epilogue = epi;
+        a.sigma = dagger ? -1.0f : 1.0f;
+        a.coef = (float)coef;
+        a.tw_epi = to_float(te);
+        a.tw_pro = to_float(tp);
+        e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, block, s)
+                        : launch_dslash_p16(a, g->nf, g->p.recon, pro, block, s);
+    }
+    return cuda_check(e, "dslash launch");
+}
+
+static tm_status same_prec(const tm_field *a, const tm_field *b, const char *what)
+{
+    if (a->prec != b->prec) { set_error("%s: fields must share a precision", what); return TM_ERR_ARG; }
+    if (a->nrhs != b->nrhs) { set_error("%s: fields must share nrhs", what); return TM_ERR_ARG; }
+    return TM_OK;
+}
+
+#define TM_TRY(x)                     \
+    do {                              \
+        tm_status _st = (x);          \
+        if (_st != TM_OK) return _st; \
+    } while (0)
+
+static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                            const tm_field *x, void *stream, int dagger)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    TM_TRY(check_field(g, in, "in"));
+    TM_TRY(same_prec(out, in, "tm_dslash"));
+    if (out->nrhs != 1) { set_error("tm_dslash: single-RHS fields only"); return TM_ERR_ARG; }
+    if (out_parity != 0 && out_parity != 1) { set_error("out_parity must be 0 or 1"); return TM_ERR_ARG; }
+    if (out->data == in->data) { set_error("tm_dslash: out must not alias in"); return TM_ERR_ARG; }
+    const double k = g->p.kappa;
+    const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
+    const bool needx = epilogue >= TM_EPI_TWXPAY_ASYM;
+    if (epilogue < TM_EPI_NONE || epilogue > TM_EPI_TWINV_XPAY) { set_error("unknown epilogue %d", epilogue); return TM_ERR_ARG; }
+    if (needx) {
+        TM_TRY(check_field(g, x, "x"));
+        TM_TRY(same_prec(out, x, "tm_dslash"));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (epilogue) {
+    case TM_EPI_NONE: return dslash_launch(g, out, in, nullptr, out_parity, dagger, EPI_SCALE, 1.0, nullptr, nullptr, s);
+    case TM_EPI_TWINV: return dslash_launch(g, out, in, nullptr, out_parity, dagger, EPI_TW, 1.0, &Ri, nullptr, s);
+    case TM_EPI_TWXPAY_ASYM: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_TWX_AXPY, -k * k, &R, nullptr, s);
+    case TM_EPI_TWXPAY_SYM: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_X_TWAXPY, -k * k, &Ri, nullptr, s);
+    case TM_EPI_XPAY: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_XPAY, k, nullptr, nullptr, s);
+    default: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_TW_XPAY, k, &Ri, nullptr, s);
+    }
+}
+
+}  // namespace tmk
+
+using namespace tmk;
+
+// =============================================================================== C ABI
+extern "C" {
+
+const char *tm_version(void) { return "libtm 0.1 (sm_103a)"; }
+
+tm_status tm_last_error(char *buf, size_t n)
+{
+    if (!buf || n == 0) return TM_ERR_ARG;
+    snprintf(buf, n, "%s", g_err);
+    return TM_OK;
+}
+
+tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out)
+{
+    TM_TRY(check_params(p));
+    if (!U_canon || !out) { set_error("tm_gauge_create: null pointer"); return TM_ERR_ARG; }
+    *out = nullptr;
+    tm_gauge *g = new tm_gauge;
+    memset(g, 0, sizeof(*g));
+    g->p = *p;
+    g->nf = (p->flavor == TM_NDEG_DOUBLET) ? 2 : 1;
+    const long V = (long)p->L[0] * p->L[1] * p->L[2] * p->L[3];
+    g->Vh = (int)(V / 2);
+    g->X1h = p->L[0] / 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    tm_status st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
+    if (st == TM_OK) st = cuda_check(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
+                                     "cudaDeviceGetAttribute");
+    const int precs[3] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16};
+    for (int i = 0; i < 3 && st == TM_OK; i++) {
+        const int nreal = p->recon;
+        const size_t per_link = (size_t)nreal * precs[i];
+        const size_t chunks = per_link / link_chunk_bytes(precs[i], p->recon);
+        g->link_bytes[i] = 8ull * g->Vh * chunks * link_chunk_bytes(precs[i], p->recon);
+        if (cudaMalloc(&g->links[i], g->link_bytes[i]) != cudaSuccess) {
+            set_error("tm_gauge_create: cudaMalloc of %zu bytes failed", g->link_bytes[i]);
+            st = TM_ERR_NOMEM;
+            break;
+        }
+        st = cuda_check(launch_pack_gauge(g, i, g->links[i], U_canon, s), "pack gauge");
+    }
+    if (st == TM_OK) {
+        g->scratch_bytes = 1 << 20;
+        if (cudaMalloc((void **)&g->scratch, g->scratch_bytes) != cudaSuccess) {
+            set_error("tm_gauge_create: scratch allocation failed");
+            st = TM_ERR_NOMEM;
+        } else {
+            st = cuda_check(cudaMemsetAsync(g->scratch, 0, g->scratch_bytes, s), "scratch memset");
+        }
+    }
+    if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tm_gauge_create sync");
+    if (st != TM_OK) {
+        tm_gauge_destroy(g);
+        return st;
+    }
+    *out = g;
+    return TM_OK;
+}
+
+tm_status tm_gauge_destroy(tm_gauge *g)
+{
+    if (!g) return TM_OK;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 3; i++)
+        if (g->links[i]) cudaFree(g->links[i]);
+    if (g->scratch) cudaFree(g->scratch);
+    delete g;
+    return TM_OK;
+}
+
+tm_status tm_field_bytes(const tm_gauge *g, int prec, int nrhs, size_t *data_bytes, size_t *norm_bytes)
+{
+    if (!g || !data_bytes || !norm_bytes) { set_error("tm_field_bytes: null pointer"); return TM_ERR_ARG; }
+    if (prec_index(prec) < 0 || nrhs < 1) { set_error("tm_field_bytes: bad prec or nrhs"); return TM_ERR_ARG; }
+    const size_t sites = (size_t)g->Vh * g->nf * nrhs;
+    *data_bytes = sites * 24 * (size_t)prec;
+    *norm_bytes = (prec == TM_PREC_F16) ? sites * sizeof(float) : 0;
+    return TM_OK;
+}
+
+tm_status tm_pack(const tm_gauge *g, const tm_field *out, const void *canon, int canon_type, int parity, void *stream)
+{
+    if (!g || !canon) { set_error("tm_pack: null pointer"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
+    if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("unknown canon_type"); return TM_ERR_ARG; }
+    return cuda_check(launch_pack_spinor(g, out, canon, canon_type, parity, (cudaStream_t)stream), "tm_pack");
+}
+
+tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_field *in, int parity, void *stream)
+{
+    if (!g || !canon) { set_error("tm_unpack: null pointer"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, in, "in"));
+    if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
+    if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("unknown canon_type"); return TM_ERR_ARG; }
+    return cuda_check(launch_unpack_spinor(g, canon, canon_type, in, parity, (cudaStream_t)stream), "tm_unpack");
+}
+
+tm_status tm_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                    const tm_field *x, void *stream)
+{
+    return dslash_api(g, out, in, out_parity, epilogue, x, stream, 0);
+}
+
+tm_status tm_dslash_dagger(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                           const tm_field *x, void *stream)
+{
+    return dslash_api(g, out, in, out_parity, epilogue, x, stream, 1);
+}
+
+tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                        int dagger, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out_e, "out_e"));
+    TM_TRY(check_field(g, in_e, "in_e"));
+    TM_TRY(check_field(g, tmp_o, "tmp_o"));
+    TM_TRY(same_prec(out_e, in_e, "tm_precond_op"));
+    TM_TRY(same_prec(out_e, tmp_o, "tm_precond_op"));
+    if (out_e->nrhs != 1) { set_error("tm_precond_op: single-RHS fields only"); return TM_ERR_ARG; }
+    if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
+    if (out_e->data == in_e->data || tmp_o->data == in_e->data || tmp_o->data == out_e->data) {
+        set_error("tm_precond_op: out_e, in_e and tmp_o must be distinct");
+        return TM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double k2 = g->p.kappa * g->p.kappa;
+    const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
+    if (pc == TM_PC_ASYM) {
+        // tmp = R^-1_oo H_oe in ;  out = R_ee in - kappa^2 H_eo tmp
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, &Ri, nullptr, s));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, dagger, EPI_TWX_AXPY, -k2, &R, nullptr, s);
+    }
+    if (!dagger) {
+        // tmp = R^-1_oo H_oe in ;  out = in - kappa^2 R^-1_ee H_eo tmp
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, 0, EPI_X_TWAXPY, -k2, &Ri, nullptr, s);
+    }
+    // adjoint of the symmetric operator: tmp = R^-dag_oo H^dag_oe R^-dag_ee in ; out = in - kappa^2 H^dag_eo tmp
+    TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s));
+    return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s);
+}
+
+tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,
+                 const tm_field *in_o, int dagger, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out_e, "out_e"));
+    TM_TRY(check_field(g, out_o, "out_o"));
+    TM_TRY(check_field(g, in_e, "in_e"));
+    TM_TRY(check_field(g, in_o, "in_o"));
+    TM_TRY(same_prec(out_e, in_e, "tm_mat"));
+    TM_TRY(same_prec(out_o, in_o, "tm_mat"));
+    TM_TRY(same_prec(out_e, out_o, "tm_mat"));
+    if (out_e->nrhs != 1) { set_error("tm_mat: single-RHS fields only"); return TM_ERR_ARG; }
+    if (out_e->data == in_e->data || out_e->data == in_o->data || out_o->data == in_e->data ||
+        out_o->data == in_o->data) {
+        set_error("tm_mat: outputs must not alias inputs");
+        return TM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Twist<double> R = make_twist(g, TW_R, dagger);
+    const double k = g->p.kappa;
+    // out_p = R in_p - kappa H_{p,1-p} in_{1-p}
+    TM_TRY(dslash_launch(g, out_e, in_o, in_e, 0, dagger, EPI_TWX_AXPY, -k, &R, nullptr, s));
+    return dslash_launch(g, out_o, in_e, in_o, 1, dagger, EPI_TWX_AXPY, -k, &R, nullptr, s);
+}
+
+tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_field *b_e, const tm_field *b_o, int pc,
+                         int dagger, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, bprime_e, "bprime_e"));
+    TM_TRY(check_field(g, b_e, "b_e"));
+    TM_TRY(check_field(g, b_o, "b_o"));
+    TM_TRY(same_prec(bprime_e, b_e, "tm_prepare_rhs"));
+    TM_TRY(same_prec(bprime_e, b_o, "tm_prepare_rhs"));
+    if (bprime_e->nrhs != 1) { set_error("tm_prepare_rhs: single-RHS fields only"); return TM_ERR_ARG; }
+    if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
+    if (bprime_e->data == b_o->data) { set_error("tm_prepare_rhs: bprime_e must not alias b_o"); return TM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
+    const double k = g->p.kappa;
+    // b' = b_e + kappa H_eo (R^-1_oo b_o)   [the R^-1 twist is the prologue on every neighbour]
+    if (pc == TM_PC_SYM && !dagger)
+        return dslash_launch(g, bprime_e, b_o, b_e, 0, 0, EPI_TW_XPAY, k, &Ri, &Ri, s);
+    return dslash_launch(g, bprime_e, b_o, b_e, 0, dagger, EPI_XPAY, k, nullptr, &Ri, s);
+}
+
+tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_field *b_o, const tm_field *psi_e,
+                             int dagger, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, psi_o, "psi_o"));
+    TM_TRY(check_field(g, b_o, "b_o"));
+    TM_TRY(check_field(g, psi_e, "psi_e"));
+    TM_TRY(same_prec(psi_o, b_o, "tm_reconstruct_odd"));
+    TM_TRY(same_prec(psi_o, psi_e, "tm_reconstruct_odd"));
+    if (psi_o->nrhs != 1) { set_error("tm_reconstruct_odd: single-RHS fields only"); return TM_ERR_ARG; }
+    if (psi_o->data == psi_e->data) { set_error("tm_reconstruct_odd: psi_o must not alias psi_e"); return TM_ERR_ARG; }
+    const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
+    return dslash_launch(g, psi_o, psi_e, b_o, 1, dagger, EPI_TW_XPAY, g->p.kappa, &Ri, nullptr, (cudaStream_t)stream);
+}
+
+tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    TM_TRY(check_field(g, in, "in"));
+    TM_TRY(same_prec(out, in, "tm_twist"));
+    const Twist<double> T = make_twist(g, inverse ? TW_RINV : TW_R, dagger);
+    return cuda_check(launch_twist(g, out, in, T, (cudaStream_t)stream), "tm_twist");
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// tm_dslash.cuh -- the fused even-odd twisted-mass hopping kernel (sec. 2.1, eq. 2.1-2.3).
+//
+// One thread per output site of parity p computes the hopping sum
+//   acc(x) = sum_mu (1 - s g_mu) U_mu(x) in(x+mu) + (1 + s g_mu) U_mu(x-mu)^dag in(x-mu)
+// with s = +1 for H and s = -1 for H^dag (the projectors swap), gamma matrices in the
+// DeGrand-Rossi basis, and a factor -1 on hops across the antiperiodic time boundary.
+// Each (1 +- g_mu) has rank two, so only two spin rows h0, h1 are multiplied by the link
+// (2 x 66 flops) and spins 2, 3 of the result are +-h or +-i h of those rows.
+//
+// The local operators of the even-odd factorisation are fused in (sec. 2.1: "computed on the
+// fly"), selected by a uniform runtime switch:
+//   EPI_SCALE      out = c acc                     plain hopping block
+//   EPI_TW         out = T acc                     R^-1_oo D_oe  (T = R^-1 or R^-dag)
+//   EPI_TWX_AXPY   out = T x + c acc               R_ee x - kappa^2 D_eo t      (eq. 2.2 LHS)
+//   EPI_X_TWAXPY   out = x + c T acc               x - kappa^2 R^-1_ee D_eo t  (eq. 2.3 LHS)
+//   EPI_XPAY       out = x + c acc
+//   EPI_TW_XPAY    out = T (x + c acc)             odd reconstruction, symmetric RHS
+// and, as a compile-time option, a prologue that twists every neighbour spinor before the
+// projection (in -> T_pro in), which the adjoint of the symmetric operator needs.
+// For the doublet both flavours are computed by the same thread, so each link is loaded once
+// and used for both (sec. 2.1).
+#pragma once
+#include "tm_core.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+template <typename T>
+struct DslashArgs {
+    void *out;
+    float *out_norm;
+    const void *in;
+    const float *in_norm;
+    const void *x;
+    const float *x_norm;
+    const void *gauge;  // [mu][parity][chunk][Vh] of this precision / recon
+    int Vh, X1h, Lx, Ly, Lz, Lt;
+    int out_parity;
+    int tbc;
+    int epilogue;
+    T sigma;  // +1: H, -1: H^dag
+    T coef;
+    Twist<T> tw_epi, tw_pro;
+};
+
+template <typename T>
+__device__ __forceinline__ void acc_add(T *a, int k, C<T> w, T q)
+{
+    a[k] = fma(q, w.r, a[k]);
+    a[k + 1] = fma(q, w.i, a[k + 1]);
+}
+// a += q * i * w
+template <typename T>
+__device__ __forceinline__ void acc_addi(T *a, int k, C<T> w, T q)
+{
+    a[k] = fma(-q, w.i, a[k]);
+    a[k + 1] = fma(q, w.r, a[k + 1]);
+}
+
+// w = U h (forward) or U^dag h (backward), h one spin row (3 colours)
+template <typename T, bool FWD>
+__device__ __forceinline__ void link_mul(const Link<T> &U, const C<T> h[3], C<T> w[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (FWD) {
+            C<T> s = cmul(U.u[a][0], h[0]);
+            s = cadd(s, cmul(U.u[a][1], h[1]));
+            w[a] = cadd(s, cmul(U.u[a][2], h[2]));
+        } else {
+            C<T> s = cmulc(U.u[0][a], h[0]);
+            s = cadd(s, cmulc(U.u[1][a], h[1]));
+            w[a] = cadd(s, cmulc(U.u[2][a], h[2]));
+        }
+    }
+}
+
+// Project one flavour's spinor v with (1 + sp g_MU), multiply by the link, accumulate with
+// boundary sign sg.  Spin index k of colour c, re part, is at 2*(3k + c).
+template <int MU, bool FWD, typename T>
+__device__ __forceinline__ void hop_one(T *acc, const Link<T> &U, const T *v, T sp, T sg)
+{
+    C<T> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const C<T> p0 = {v[2 * c], v[2 * c + 1]}, p1 = {v[6 + 2 * c], v[7 + 2 * c]};
+        const C<T> p2 = {v[12 + 2 * c], v[13 + 2 * c]}, p3 = {v[18 + 2 * c], v[19 + 2 * c]};
+        if (MU == 0) {        // h0 = p0 + sp i p3,  h1 = p1 + sp i p2
+            h0[c] = {fma(-sp, p3.i, p0.r), fma(sp, p3.r, p0.i)};
+            h1[c] = {fma(-sp, p2.i, p1.r), fma(sp, p2.r, p1.i)};
+        } else if (MU == 1) { // h0 = p0 - sp p3,  h1 = p1 + sp p2
+            h0[c] = {fma(-sp, p3.r, p0.r), fma(-sp, p3.i, p0.i)};
+            h1[c] = {fma(sp, p2.r, p1.r), fma(sp, p2.i, p1.i)};
+        } else if (MU == 2) { // h0 = p0 + sp i p2,  h1 = p1 - sp i p3
+            h0[c] = {fma(-sp, p2.i, p0.r), fma(sp, p2.r, p0.i)};
+            h1[c] = {fma(sp, p3.i, p1.r), fma(-sp, p3.r, p1.i)};
+        } else {              // h0 = p0 + sp p2,  h1 = p1 + sp p3
+            h0[c] = {fma(sp, p2.r, p0.r), fma(sp, p2.i, p0.i)};
+            h1[c] = {fma(sp, p3.r, p1.r), fma(sp, p3.i, p1.i)};
+        }
+    }
+    C<T> w0[3], w1[3];
+    link_mul<T, FWD>(U, h0, w0);
+    link_mul<T, FWD>(U, h1, w1);
+    const T q = sg * sp;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc_add(acc, 2 * c, w0[c], sg);
+        acc_add(acc, 6 + 2 * c, w1[c], sg);
+        if (MU == 0) {        // row2 = -sp i h1, row3 = -sp i h0
+            acc_addi(acc, 12 + 2 * c, w1[c], -q);
+            acc_addi(acc, 18 + 2 * c, w0[c], -q);
+        } else if (MU == 1) { // row2 = sp h1, row3 = -sp h0
+            acc_add(acc, 12 + 2 * c, w1[c], q);
+            acc_add(acc, 18 + 2 * c, w0[c], -q);
+        } else if (MU == 2) { // row2 = -sp i h0, row3 = sp i h1
+            acc_addi(acc, 12 + 2 * c, w0[c], -q);
+            acc_addi(acc, 18 + 2 * c, w1[c], q);
+        } else {              // row2 = sp h0, row3 = sp h1
+            acc_add(acc, 12 + 2 * c, w0[c], q);
+            acc_add(acc, 18 + 2 * c, w1[c], q);
+        }
+    }
+}
+
+template <int PREC, int NF, bool PRO, int MU, bool FWD, typename T>
+__device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const DslashArgs<T> &a, int nb, T sg)
+{
+    const T sp = FWD ? -a.sigma : a.sigma;
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;  // chunks per flavour
+    using SC = typename Traits<PREC>::schunk;
+    const SC *in = reinterpret_cast<const SC *>(a.in);
+    if (PRO) {
+        T v[NF][24];
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+            load_spinor<PREC>(in + f * fstride, a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr, nb, a.Vh, v[f]);
+        apply_twist<T, NF>(a.tw_pro, v);
+#pragma unroll
+        for (int f = 0; f < NF; f++) hop_one<MU, FWD>(acc[f], U, v[f], sp, sg);
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            T v[24];
+            load_spinor<PREC>(in + f * fstride, a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr, nb, a.Vh, v);
+            hop_one<MU, FWD>(acc[f], U, v, sp, sg);
+        }
+    }
+}
+
+template <int PREC, int NF, int RECON, bool PRO>
+__global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    using T = typename Traits<PREC>::real;
+    using LL = LinkLayout<PREC, RECON>;
+    using LC = typename LL::chunk;
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+
+    int r = cb;
+    const int xh = r % a.X1h;
+    r /= a.X1h;
+    const int y = r % a.Ly;
+    r /= a.Ly;
+    const int z = r % a.Lz;
+    const int t = r / a.Lz;
+    const int op = a.out_parity;
+    const int x = 2 * xh + ((op + y + z + t) & 1);
+    const int row = cb - xh;
+    const size_t gpar = (size_t)LL::N * a.Vh;  // chunks per (mu, parity)
+    const LC *G = reinterpret_cast<const LC *>(a.gauge);
+    const LC *Gout = G + (size_t)op * gpar;        // links at the output site: mu stride 2*gpar
+    const LC *Gin = G + (size_t)(1 - op) * gpar;   // links at the neighbour site
+
+    T acc[NF][24];
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+#pragma unroll
+        for (int k = 0; k < 24; k++) acc[f][k] = T(0);
+
+    Link<T> U;
+    const T one = T(1);
+    // ---- x
+    {
+        const int nf_ = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
+        LinkLoader<PREC, RECON>::load(Gout + 0 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, NF, PRO, 0, true>(acc, U, a, nf_, one);
+        const int nb_ = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
+        LinkLoader<PREC, RECON>::load(Gin + 0 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, NF, PRO, 0, false>(acc, U, a, nb_, one);
+    }
+    // ---- y
+    {
+        const int s = a.X1h;
+        const int nf_ = (y == a.Ly - 1) ? cb - (a.Ly - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 1 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, NF, PRO, 1, true>(acc, U, a, nf_, one);
+        const int nb_ = (y == 0) ? cb + (a.Ly - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 1 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, NF, PRO, 1, false>(acc, U, a, nb_, one);
+    }
+    // ---- z
+    {
+        const int s = a.X1h * a.Ly;
+        const int nf_ = (z == a.Lz - 1) ? cb - (a.Lz - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 2 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, NF, PRO, 2, true>(acc, U, a, nf_, one);
+        const int nb_ = (z == 0) ? cb + (a.Lz - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 2 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, NF, PRO, 2, false>(acc, U, a, nb_, one);
+    }
+    // ---- t (antiperiodic wrap when tbc)
+    {
+        const int s = a.X1h * a.Ly * a.Lz;
+        const bool wf = (t == a.Lt - 1), wb = (t == 0);
+        const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 3 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, NF, PRO, 3, true>(acc, U, a, nf_, (wf && a.tbc) ? -one : one);
+        const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, NF, PRO, 3, false>(acc, U, a, nb_, (wb && a.tbc) ? -one : one);
+    }
+
+    // ---- fused local epilogue
+    using SC = typename Traits<PREC>::schunk;
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    const int epi = a.epilogue;
+    if (epi == EPI_SCALE) {
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+#pragma unroll
+            for (int k = 0; k < 24; k++) acc[f][k] *= a.coef;
+    } else if (epi == EPI_TW) {
+        apply_twist<T, NF>(a.tw_epi, acc);
+    } else {
+        T xv[NF][24];
+        const SC *X = reinterpret_cast<const SC *>(a.x);
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+            load_spinor<PREC>(X + f * fstride, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv[f]);
+        if (epi == EPI_TWX_AXPY) {
+            apply_twist<T, NF>(a.tw_epi, xv);
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+#pragma unroll
+                for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+        } else if (epi == EPI_X_TWAXPY) {
+            apply_twist<T, NF>(a.tw_epi, acc);
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+#pragma unroll
+                for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+        } else {  // EPI_XPAY, EPI_TW_XPAY
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+#pragma unroll
+                for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+            if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+        }
+    }
+    SC *O = reinterpret_cast<SC *>(a.out);
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+        store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+}
+
+template <int PREC>
+cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro, int block,
+                               cudaStream_t s)
+{
+    const int grid = (a.Vh + block - 1) / block;
+#define TM_LAUNCH(NF, R, P) k_dslash<PREC, NF, R, P><<<grid, block, 0, s>>>(a)
+#define TM_RECON(NF, P)                  \
+    switch (recon) {                     \
+    case 18: TM_LAUNCH(NF, 18, P); break; \
+    case 12: TM_LAUNCH(NF, 12, P); break; \
+    case 8: TM_LAUNCH(NF, 8, P); break;   \
+    default: return cudaErrorInvalidValue; \
+    }
+    if (nf == 1) {
+        if (pro) { TM_RECON(1, true) } else { TM_RECON(1, false) }
+    } else {
+        if (pro) { TM_RECON(2, true) } else { TM_RECON(2, false) }
+    }
+#undef TM_RECON
+#undef TM_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace tmk

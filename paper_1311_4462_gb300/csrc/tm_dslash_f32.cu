@@ -1,0 +1,10 @@
+// Instantiations of the fused hopping kernel for FP32 storage (one translation unit per
+// precision so the three compile in parallel).
+#include "tm_dslash.cuh"
+
+namespace tmk {
+cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, int block, cudaStream_t s)
+{
+    return launch_dslash_impl<P32>(a, nf, recon, pro, block, s);
+}
+}  // namespace tmk

@@ -1,0 +1,44 @@
+// tm_internal.h -- declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/tm.h"
+
+namespace tmk {
+
+// kernel-level epilogue codes (see tm_dslash.cuh)
+enum Epilogue {
+    EPI_SCALE = 0,     // out = c acc
+    EPI_TW = 1,        // out = T acc
+    EPI_TWX_AXPY = 2,  // out = T x + c acc
+    EPI_X_TWAXPY = 3,  // out = x + c T acc
+    EPI_XPAY = 4,      // out = x + c acc
+    EPI_TW_XPAY = 5    // out = T (x + c acc)
+};
+
+// twist selector for host-built coefficient tables
+enum TwistKind { TW_R = 0, TW_RINV = 1 };
+
+}  // namespace tmk
+
+// The opaque handle behind tm_gauge*.
+struct tm_gauge {
+    tm_params p;
+    int nf;
+    int Vh, X1h;
+    int device;
+    int num_sms;
+    void *links[3];     // packed links, index 0: FP64, 1: FP32, 2: FP16
+    size_t link_bytes[3];
+    double *scratch;    // reduction partials + device scalars (library-owned)
+    size_t scratch_bytes;
+};
+
+namespace tmk {
+int prec_index(int prec);          // 0/1/2 for F64/F32/F16, -1 otherwise
+int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
+size_t chunk_bytes(int prec);      // always 16
+void set_error(const char *fmt, ...);
+tm_status cuda_check(cudaError_t e, const char *what);
+}  // namespace tmk

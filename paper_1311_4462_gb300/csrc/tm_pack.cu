@@ -1,0 +1,230 @@
+// tm_pack.cu -- conversion between the canonical full-lattice layout and the internal
+// parity-split structure-of-arrays fields, and the packed link codecs (sec. 2, sec. 3).
+#include <math.h>
+
+#include "tm_core.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+template <typename CT> struct CanonT;
+template <> struct CanonT<double2> { using real = double; };
+template <> struct CanonT<float2> { using real = float; };
+
+// lexicographic site of (parity, cb)
+__device__ __forceinline__ long lex_of(int cb, int parity, int X1h, int Lx, int Ly, int Lz)
+{
+    int r = cb;
+    const int xh = r % X1h;
+    r /= X1h;
+    const int y = r % Ly;
+    r /= Ly;
+    const int z = r % Lz;
+    const int t = r / Lz;
+    const int x = 2 * xh + ((parity + y + z + t) & 1);
+    return x + (long)Lx * (y + (long)Ly * (z + (long)Lz * t));
+}
+
+struct Geo {
+    int Vh, X1h, Lx, Ly, Lz, nf, nrhs;
+};
+
+// thread per (rhs, flavour, cb)
+template <int PREC, typename CT>
+__global__ void k_pack_spinor(void *out, float *norm, const CT *canon, int parity, Geo g)
+{
+    using T = typename Traits<PREC>::real;
+    using SC = typename Traits<PREC>::schunk;
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nsite = (long)g.Vh * g.nf * g.nrhs;
+    if (id >= nsite) return;
+    const int cb = (int)(id % g.Vh);
+    const int f = (int)((id / g.Vh) % g.nf);
+    const int rhs = (int)(id / ((long)g.Vh * g.nf));
+    const long lex = lex_of(cb, parity, g.X1h, g.Lx, g.Ly, g.Lz);
+    const long V = 2L * g.Vh;
+    const CT *src = canon + (((long)rhs * V + lex) * g.nf + f) * 12;
+    T v[24];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        CT c = src[k];
+        v[2 * k] = (T)c.x;
+        v[2 * k + 1] = (T)c.y;
+    }
+    const long blk = (long)rhs * g.nf + f;  // flavour block index
+    SC *o = reinterpret_cast<SC *>(out) + blk * Traits<PREC>::SCHUNKS * (long)g.Vh;
+    store_spinor<PREC>(o, norm ? norm + blk * g.Vh : nullptr, cb, g.Vh, v);
+}
+
+template <int PREC, typename CT>
+__global__ void k_unpack_spinor(CT *canon, const void *in, const float *norm, int parity, Geo g)
+{
+    using T = typename Traits<PREC>::real;
+    using SC = typename Traits<PREC>::schunk;
+    using R = typename CanonT<CT>::real;
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nsite = (long)g.Vh * g.nf * g.nrhs;
+    if (id >= nsite) return;
+    const int cb = (int)(id % g.Vh);
+    const int f = (int)((id / g.Vh) % g.nf);
+    const int rhs = (int)(id / ((long)g.Vh * g.nf));
+    const long lex = lex_of(cb, parity, g.X1h, g.Lx, g.Ly, g.Lz);
+    const long V = 2L * g.Vh;
+    const long blk = (long)rhs * g.nf + f;
+    const SC *p = reinterpret_cast<const SC *>(in) + blk * Traits<PREC>::SCHUNKS * (long)g.Vh;
+    T v[24];
+    load_spinor<PREC>(p, norm ? norm + blk * g.Vh : nullptr, cb, g.Vh, v);
+    CT *dst = canon + (((long)rhs * V + lex) * g.nf + f) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        CT c;
+        c.x = (R)v[2 * k];
+        c.y = (R)v[2 * k + 1];
+        dst[k] = c;
+    }
+}
+
+// ------------------------------------------------------------------------------------ links
+// Reals of one link in storage order for the given recon (see tm_core.cuh).
+__device__ __forceinline__ int encode_link(const double2 *u, int recon, double r[18])
+{
+    if (recon == 8) {
+        r[0] = u[1].x; r[1] = u[1].y;  // a2
+        r[2] = u[2].x; r[3] = u[2].y;  // a3
+        r[4] = u[3].x; r[5] = u[3].y;  // b1
+        r[6] = atan2(u[0].y, u[0].x);  // arg a1
+        r[7] = atan2(u[6].y, u[6].x);  // arg c1
+        return 8;
+    }
+    const int n = (recon == 18) ? 9 : 6;
+    for (int k = 0; k < n; k++) {
+        r[2 * k] = u[k].x;
+        r[2 * k + 1] = u[k].y;
+    }
+    return 2 * n;
+}
+
+// thread per (mu, parity, cb); writes chunk k of link (mu, parity, cb) at base + ((mu*2+par)*N + k)*Vh + cb
+template <int PREC>
+__global__ void k_pack_gauge(void *out, const double2 *canon, int recon, Geo g)
+{
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 8L * g.Vh) return;
+    const int cb = (int)(id % g.Vh);
+    const int par = (int)((id / g.Vh) % 2);
+    const int mu = (int)(id / (2L * g.Vh));
+    const long lex = lex_of(cb, par, g.X1h, g.Lx, g.Ly, g.Lz);
+    const long V = 2L * g.Vh;
+    const double2 *u = canon + ((long)mu * V + lex) * 9;
+    double r[18];
+    const int nr = encode_link(u, recon, r);
+    const long slot = (long)(mu * 2 + par);
+    if (PREC == P64) {
+        const int N = nr / 2;
+        double2 *o = reinterpret_cast<double2 *>(out) + slot * N * (long)g.Vh + cb;
+        for (int k = 0; k < N; k++) o[(long)k * g.Vh] = make_double2(r[2 * k], r[2 * k + 1]);
+    } else if (PREC == P32) {
+        if (recon == 18) {
+            float2 *o = reinterpret_cast<float2 *>(out) + slot * 9 * (long)g.Vh + cb;
+            for (int k = 0; k < 9; k++) o[(long)k * g.Vh] = make_float2((float)r[2 * k], (float)r[2 * k + 1]);
+        } else {
+            const int N = nr / 4;
+            float4 *o = reinterpret_cast<float4 *>(out) + slot * N * (long)g.Vh + cb;
+            for (int k = 0; k < N; k++)
+                o[(long)k * g.Vh] = make_float4((float)r[4 * k], (float)r[4 * k + 1], (float)r[4 * k + 2],
+                                                (float)r[4 * k + 3]);
+        }
+    } else {
+        if (recon == 8) {
+            r[6] /= 3.14159265358979323846;
+            r[7] /= 3.14159265358979323846;
+        }
+        if (recon == 18) {
+            uint32_t *o = reinterpret_cast<uint32_t *>(out) + slot * 9 * (long)g.Vh + cb;
+            for (int k = 0; k < 9; k++) o[(long)k * g.Vh] = f2h((float)r[2 * k], (float)r[2 * k + 1]);
+        } else if (recon == 12) {
+            uint2 *o = reinterpret_cast<uint2 *>(out) + slot * 3 * (long)g.Vh + cb;
+            for (int k = 0; k < 3; k++)
+                o[(long)k * g.Vh] = make_uint2(f2h((float)r[4 * k], (float)r[4 * k + 1]),
+                                               f2h((float)r[4 * k + 2], (float)r[4 * k + 3]));
+        } else {
+            uint4 *o = reinterpret_cast<uint4 *>(out) + slot * (long)g.Vh + cb;
+            uint4 c;
+            c.x = f2h((float)r[0], (float)r[1]);
+            c.y = f2h((float)r[2], (float)r[3]);
+            c.z = f2h((float)r[4], (float)r[5]);
+            c.w = f2h((float)r[6], (float)r[7]);
+            *o = c;
+        }
+    }
+}
+
+static Geo geo_of(const tm_gauge *g, int nrhs)
+{
+    Geo G;
+    G.Vh = g->Vh;
+    G.X1h = g->X1h;
+    G.Lx = g->p.L[0];
+    G.Ly = g->p.L[1];
+    G.Lz = g->p.L[2];
+    G.nf = g->nf;
+    G.nrhs = nrhs;
+    return G;
+}
+
+cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void *canon, int ctype, int parity,
+                               cudaStream_t s)
+{
+    Geo G = geo_of(g, f->nrhs);
+    const long n = (long)G.Vh * G.nf * G.nrhs;
+    const int block = 128;
+    const long grid = (n + block - 1) / block;
+#define TM_P(P, CT) k_pack_spinor<P, CT><<<grid, block, 0, s>>>(f->data, f->norm, (const CT *)canon, parity, G)
+    if (ctype == TM_C128) {
+        if (f->prec == TM_PREC_F64) TM_P(P64, double2);
+        else if (f->prec == TM_PREC_F32) TM_P(P32, double2);
+        else TM_P(P16, double2);
+    } else {
+        if (f->prec == TM_PREC_F64) TM_P(P64, float2);
+        else if (f->prec == TM_PREC_F32) TM_P(P32, float2);
+        else TM_P(P16, float2);
+    }
+#undef TM_P
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, const tm_field *f, int parity,
+                                 cudaStream_t s)
+{
+    Geo G = geo_of(g, f->nrhs);
+    const long n = (long)G.Vh * G.nf * G.nrhs;
+    const int block = 128;
+    const long grid = (n + block - 1) / block;
+#define TM_U(P, CT) k_unpack_spinor<P, CT><<<grid, block, 0, s>>>((CT *)canon, f->data, f->norm, parity, G)
+    if (ctype == TM_C128) {
+        if (f->prec == TM_PREC_F64) TM_U(P64, double2);
+        else if (f->prec == TM_PREC_F32) TM_U(P32, double2);
+        else TM_U(P16, double2);
+    } else {
+        if (f->prec == TM_PREC_F64) TM_U(P64, float2);
+        else if (f->prec == TM_PREC_F32) TM_U(P32, float2);
+        else TM_U(P16, float2);
+    }
+#undef TM_U
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void *canon, cudaStream_t s)
+{
+    Geo G = geo_of(g, 1);
+    const long n = 8L * G.Vh;
+    const int block = 128;
+    const long grid = (n + block - 1) / block;
+    const double2 *c = (const double2 *)canon;
+    if (pidx == 0) k_pack_gauge<P64><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    else if (pidx == 1) k_pack_gauge<P32><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    else k_pack_gauge<P16><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    return cudaGetLastError();
+}
+
+}  // namespace tmk

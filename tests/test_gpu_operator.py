@@ -1,0 +1,198 @@
+"""Parity of the CUDA operator (through the C ABI) against the FP64 CPU oracle.
+
+Element-by-element comparison of unpacked outputs with the oracle on the same seeded inputs.
+Tolerances (relative L2 over the output parity): FP64 1e-13, FP32 1e-6, FP16 with per-site
+norm 5e-3 per application.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1311_4462_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {8: 1e-13, 4: 1e-6, 2: 5e-3}
+
+# (name, L, flavor, kappa, mu, eps): covers L = 2 extents (x+mu == x-mu), ragged tails
+# (Vh not a multiple of the 128-thread block), non-cubic shapes, both flavour signs.
+CASES = [
+    ("cfg1_4^4_doublet_deg", (4, 4, 4, 4), 2, 0.16, 0.01, 0.0),
+    ("nd_6x4x2x10", (6, 4, 2, 10), 2, 0.1612, 0.135, 0.15),
+    ("plus_2x4x6x8", (2, 4, 6, 8), 1, 0.1612, 0.004, 0.0),
+    ("minus_8x6x4x10", (8, 6, 4, 10), -1, 0.1612, 0.004, 0.0),
+    ("nd_2^4", (2, 2, 2, 2), 2, 0.16, 0.135, 0.15),
+]
+PRECS = [8, 4, 2]
+RECONS = [18, 12, 8]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+_cache = {}
+
+
+def setup(case, recon):
+    import paper_1311_4462_gb300 as tmq
+    name, L, flavor, kappa, mu, eps = case
+    key = (name, recon)
+    if key not in _cache:
+        p = tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=recon)
+        po = orc.Params(L, kappa, mu, eps, flavor=flavor)
+        U = inputs.gauge_field(L, 1000 + len(name))
+        g = tmq.Gauge(p, torch.from_numpy(U))
+        psi = inputs.spinor_field(L, p.nf, 2000 + len(name))
+        chi = inputs.spinor_field(L, p.nf, 2100 + len(name))
+        _cache[key] = (tmq, p, po, U, g, psi, chi)
+    return _cache[key]
+
+
+def fields(tmq, g, prec, psi):
+    c = torch.from_numpy(psi)
+    return tmq.pack(g, c, 0, prec), tmq.pack(g, c, 1, prec)
+
+
+def get(tmq, g, f, parity):
+    return tmq.unpack(g, f, parity).cpu().numpy()
+
+
+def mask(po, v, parity):
+    return orc.project_parity(po, v, parity)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("recon", RECONS)
+def test_pack_unpack_roundtrip(case, prec, recon):
+    tmq, p, po, U, g, psi, chi = setup(case, recon)
+    e, o = fields(tmq, g, prec, psi)
+    back = get(tmq, g, e, 0) + get(tmq, g, o, 1)
+    tol = {8: 0.0, 4: 1e-7, 2: 6e-4}[prec]
+    assert rel(back, psi) <= tol
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("recon", RECONS)
+@pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
+@pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
+def test_precond_op(case, prec, recon, pc, dagger):
+    tmq, p, po, U, g, psi, chi = setup(case, recon)
+    xe, _ = fields(tmq, g, prec, psi)
+    out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+    tmq.precond_op(g, out, xe, tmp, pc, dagger)
+    got = get(tmq, g, out, 0)
+    ref = orc.apply_M_pc(po, U, mask(po, psi, 0), sym=bool(pc), dagger=dagger)
+    assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
+def test_full_operator(case, prec, dagger):
+    tmq, p, po, U, g, psi, chi = setup(case, 12)
+    xe, xo = fields(tmq, g, prec, psi)
+    oe, oo = tmq.Field(g, prec), tmq.Field(g, prec)
+    tmq.mat(g, oe, oo, xe, xo, dagger)
+    got = get(tmq, g, oe, 0) + get(tmq, g, oo, 1)
+    ref = orc.apply_M(po, U, psi, dagger=dagger)
+    assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_dslash_epilogues(case, prec, dagger, out_parity):
+    """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
+    tmq, p, po, U, g, psi, chi = setup(case, 12)
+    ip = 1 - out_parity
+    fin = fields(tmq, g, prec, psi)[ip]
+    fx = fields(tmq, g, prec, chi)[out_parity]
+    t_in = mask(po, psi, ip)
+    x = mask(po, chi, out_parity)
+    D = mask(po, orc.hop(po, U, t_in, dagger=dagger), out_parity)
+    k = p.kappa
+    tw = lambda v, inv: orc.twist(po, v, inverse=inv, dagger=dagger)
+    expect = {
+        tmq.TM_EPI_NONE: D,
+        tmq.TM_EPI_TWINV: tw(D, True),
+        tmq.TM_EPI_TWXPAY_ASYM: tw(x, False) - k * k * D,
+        tmq.TM_EPI_TWXPAY_SYM: x - k * k * tw(D, True),
+        tmq.TM_EPI_XPAY: x + k * D,
+        tmq.TM_EPI_TWINV_XPAY: tw(x + k * D, True),
+    }
+    fn = tmq.dslash_dagger if dagger else tmq.dslash
+    for epi, ref in expect.items():
+        out = tmq.Field(g, prec)
+        fn(g, out, fin, out_parity, epi, fx)
+        got = get(tmq, g, out, out_parity)
+        assert rel(got, ref) < TOL[prec], epi
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
+@pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
+def test_prepare_rhs_and_reconstruct(case, prec, pc, dagger):
+    tmq, p, po, U, g, psi, chi = setup(case, 12)
+    be, bo = fields(tmq, g, prec, chi)
+    bp = tmq.Field(g, prec)
+    tmq.prepare_rhs(g, bp, be, bo, pc, dagger)
+    ref = orc.prepare_rhs(po, U, chi, sym=bool(pc), dagger=dagger)
+    assert rel(get(tmq, g, bp, 0), ref) < TOL[prec]
+    xe, _ = fields(tmq, g, prec, psi)
+    xo = tmq.Field(g, prec)
+    tmq.reconstruct_odd(g, xo, bo, xe, dagger)
+    ref = orc.reconstruct_odd(po, U, mask(po, psi, 0), chi, dagger=dagger)
+    assert rel(get(tmq, g, xo, 1), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("prec", PRECS)
+def test_twist(case, prec):
+    tmq, p, po, U, g, psi, chi = setup(case, 12)
+    xe, _ = fields(tmq, g, prec, psi)
+    for inv in (False, True):
+        for dag in (False, True):
+            out = tmq.Field(g, prec)
+            tmq.twist(g, out, xe, inv, dag)
+            ref = orc.twist(po, mask(po, psi, 0), inverse=inv, dagger=dag)
+            assert rel(get(tmq, g, out, 0), ref) < TOL[prec]
+
+
+def test_fp16_matches_dequantized_inputs_closer():
+    """FP16 kernel arithmetic on its own inputs: compare with the oracle fed the FP16-rounded spinor."""
+    case = CASES[1]
+    tmq, p, po, U, g, psi, chi = setup(case, 18)
+    xe, _ = fields(tmq, g, 2, psi)
+    deq = get(tmq, g, xe, 0)
+    out, tmp = tmq.Field(g, 2), tmq.Field(g, 2)
+    tmq.precond_op(g, out, xe, tmp, 0, False)
+    ref_deq = orc.apply_M_pc(po, U, deq)
+    ref_orig = orc.apply_M_pc(po, U, mask(po, psi, 0))
+    got = get(tmq, g, out, 0)
+    assert rel(got, ref_deq) < rel(got, ref_orig) + 1e-12
+    assert rel(got, ref_deq) < 3e-3
+
+
+def test_argument_errors_are_reported():
+    import paper_1311_4462_gb300 as tmq
+    tmq_, p, po, U, g, psi, chi = setup(CASES[0], 12)
+    a, b = tmq.Field(g, 4), tmq.Field(g, 8)
+    with pytest.raises(tmq.TMError) as e:
+        tmq.dslash(g, a, b, 0)
+    assert e.value.status == -1
+    with pytest.raises(tmq.TMError):
+        tmq.dslash(g, a, a, 0)  # aliasing
+    with pytest.raises(tmq.TMError):
+        tmq.precond_op(g, a, a, a, 0)
+    bad = tmq.Params((3, 4, 4, 4), 0.16, 0.01, flavor=1)
+    with pytest.raises(tmq.TMError):
+        tmq.Gauge(bad, torch.zeros(bad.gauge_shape, dtype=torch.complex128))
+    sing = tmq.Params((4, 4, 4, 4), 0.125, 0.0, eps=4.0, flavor=2)
+    with pytest.raises(tmq.TMError):
+        tmq.Gauge(sing, torch.zeros(sing.gauge_shape, dtype=torch.complex128))
