@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd preconditioned twisted-mass operator on one GB300.
+
+Headline step: one application of the asymmetric even-even operator (eq. 2.2 LHS)
+    M_asym = R_ee - kappa^2 H_eo R_oo^-1 H_oe
+to a 32^3 x 64 non-degenerate doublet field (kappa = 0.1612, mu-bar = 0.135,
+eps-bar = 0.15, antiperiodic time), FP32 storage and arithmetic, 12-real links.  The
+step is the two fused launches tm_precond_op makes (tm_dslash with TM_EPI_TWINV, then
+TM_EPI_TWXPAY_ASYM), issued through the C ABI with CUDA events between them on the
+launching stream.  Flop convention: 1320 per hopping site and flavour, twist and xpay
+as counted in the design doc -> 5808 flops per even site for the doublet (2808 one flavour).
+
+Printed: one JSON line (rank 0).  Extra keys: per-precision / per-operator table,
+CG time-to-solution, roofline of the dominant kernel, oracle CPU baseline, clocks.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_FULL = (32, 32, 32, 64)
+KAPPA, MU_ND, EPS_ND, MU_DEG = 0.1612, 0.135, 0.15, 0.004
+FLOPS_PER_SITE = {1: 2808, 2: 5808}          # M_asym per even site (flop convention)
+FLOPS_SYM = {1: 2832, 2: 5856}               # M_sym per even site
+SPINOR_BYTES = {8: 192, 4: 96, 2: 52}        # per site and flavour, FP16 includes the 4-byte norm
+
+
+def asym_bytes(prec, nf, recon):
+    """Algorithmic bytes per even site of M_asym: 16 links + 5 spinor passes."""
+    return 16 * recon * prec + 5 * SPINOR_BYTES[prec] * nf
+
+
+def launch_bytes(prec, nf, recon):
+    """(kernel A, kernel B) bytes per output site: A reads 8 links + 1 spinor, writes 1; B also reads x."""
+    link = 8 * recon * prec
+    s = SPINOR_BYTES[prec] * nf
+    return link + 2 * s, link + 3 * s
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_4462_gb300", "csrc")
+    for f in ["tm_core.cuh", "tm_dslash.cuh", "tm_dslash_f32.cu"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel_key):
+    """Per-launch DRAM bytes of the dominant kernel from profiles/traffic.txt, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            key, srchash, nbytes = line.split()[:3]
+            if key == kernel_key and srchash == kernel_source_hash():
+                return float(nbytes)
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------------------- ours
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import inputs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    L = L_FULL
+    t0 = time.time()
+    U_np = inputs.gauge_field(L, 1002 + rank)
+    psi_np = inputs.spinor_field(L, 2, 2002 + rank)
+    gen_s = time.time() - t0
+    U = torch.from_numpy(U_np).to(dev)
+    p_nd = tmq.Params(L, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=12)
+    g = tmq.Gauge(p_nd, U)
+    psi = torch.from_numpy(psi_np).to(dev)
+    prec, nf, recon = tmq.TM_PREC_F32, 2, 12
+    xe = tmq.pack(g, psi, 0, prec)
+    tmp, out = tmq.Field(g, prec), tmq.Field(g, prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tmq.dslash(g, tmp, xe, 1, tmq.TM_EPI_TWINV)
+        tmq.dslash(g, out, tmp, 0, tmq.TM_EPI_TWXPAY_ASYM, xe)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clk = ClockSampler(dev.index)
+    clk.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for k in range(K):
+        evs[k][0].record(stream)
+        tmq.dslash(g, tmp, xe, 1, tmq.TM_EPI_TWINV)
+        evs[k][1].record(stream)
+        tmq.dslash(g, out, tmp, 0, tmq.TM_EPI_TWXPAY_ASYM, xe)
+        evs[k][2].record(stream)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    total_ms = e_start.elapsed_time(e_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ta = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
+    tb = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
+    Vh = p_nd.Vh
+    flops_step = FLOPS_PER_SITE[nf] * Vh
+    ms_per_step = total_ms / K
+    value = flops_step * K * world / (total_ms * 1e-3) / 1e9
+    la, lb = launch_bytes(prec, nf, recon)
+    avg_launch_ms = (sum(ta) + sum(tb)) / (2 * K)
+    achieved = ((la + lb) / 2 * Vh) / (avg_launch_ms * 1e-3) / 1e9
+    peak, peak_src = load_peaks()
+    traffic = read_traffic("k_dslash_f32_nd_r12_32x32x32x64")
+
+    result = {
+        "metric": "TM dslash GFLOPS & % HBM roofline per precision; CG time-to-1e-10 mixed vs FP64",
+        "value": round(value, 1), "unit": "GFLOPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded SU(3) links exp(0.3 i H), Gaussian spinors)",
+        "config": {"workload": "M_asym (eq. 2.2 LHS), non-degenerate doublet 32^3x64, kappa=0.1612, "
+                               "mu=0.135, eps=0.15, FP32 storage, recon-12",
+                   "lattice": list(L), "flavours": nf, "storage": "fp32", "recon": recon,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: links 403 MB, each spinor parity 201 MB, no flush",
+                   "flops_per_even_site": FLOPS_PER_SITE[nf], "bytes_per_even_site": asym_bytes(prec, nf, recon)},
+        "gpu_launches": 2 * K,
+        "roofline": {"bound": "hbm", "kernel": "k_dslash<FP32, doublet, recon-12> (both launches of M_asym)",
+                     "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "bytes_per_launch_algorithmic": (la + lb) / 2 * Vh,
+                     "launch_ms": {"twinv": round(statistics.mean(ta), 5), "twxpay": round(statistics.mean(tb), 5)}},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.quick:
+        result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
+        result["per_precision"] = per_precision(tmq, U, psi, dev, args)
+        result["cg"] = cg_section(tmq, g, U, psi, dev, args)
+        result["cpu_baseline"] = cpu_baseline(U_np, psi_np, args)
+    result["input_generation_s"] = round(gen_s, 2)
+    g.close()
+    return result
+
+
+def e2e_ours(args, tmq, g, psi_np, dev, flops_step):
+    """Same step end to end: pinned host canonical complex64 field -> device -> pack -> M_asym -> unpack -> host."""
+    import numpy as np
+    import torch
+
+    host_in = torch.from_numpy(psi_np.astype(np.complex64)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_in = torch.empty(host_in.shape, dtype=torch.complex64, device=dev)
+    dev_out = torch.zeros_like(dev_in)
+    prec = tmq.TM_PREC_F32
+    xe, tmp, out = tmq.Field(g, prec), tmq.Field(g, prec), tmq.Field(g, prec)
+
+    def step():
+        dev_in.copy_(host_in, non_blocking=True)
+        tmq.pack(g, dev_in, 0, prec, out=xe)
+        tmq.precond_op(g, out, xe, tmp, tmq.TM_PC_ASYM, False)
+        tmq.unpack(g, out, 0, canon=dev_out)
+        host_out.copy_(dev_out, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, min(20, args.steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    nbytes = host_in.numel() * 8
+    return {"value": round(flops_step / (ms * 1e-3) / 1e9, 1), "unit": "GFLOPS", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "path": "pinned host complex64 canonical field -> tm_pack -> tm_precond_op -> tm_unpack -> host"}
+
+
+def time_op(fn, reps, flush=None):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def per_precision(tmq, U, psi, dev, args):
+    """M_asym, M_sym and adjoints for both doublets, all precisions, recon 12 (and 18/8 for FP32/FP16)."""
+    import torch
+    peak, _ = load_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2, zeroed between reps
+    rows = []
+    L = L_FULL
+    for nf, mu, eps in [(2, MU_ND, EPS_ND), (1, MU_DEG, 0.0)]:
+        for recon in (12, 18, 8):
+            p = tmq.Params(L, KAPPA, mu, eps, flavor=(tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS),
+                           recon=recon)
+            g = tmq.Gauge(p, U)
+            src = psi if nf == 2 else psi[..., :1, :, :].contiguous()
+            for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16, tmq.TM_PREC_F64):
+                if recon != 12 and prec == tmq.TM_PREC_F64:
+                    continue
+                xe = tmq.pack(g, src, 0, prec)
+                out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+                for pc in (0, 1):
+                    for dag in (0, 1):
+                        if recon != 12 and (pc or dag):
+                            continue
+                        reps = 3 if prec == 8 else 10
+                        ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, pc, dag), reps, flush)
+                        fl = (FLOPS_SYM if pc else FLOPS_PER_SITE)[nf] * p.Vh
+                        by = asym_bytes(prec, nf, recon) * p.Vh
+                        row = {"op": ("M_sym" if pc else "M_asym") + ("^dag" if dag else ""),
+                               "flavours": nf, "prec": {8: "f64", 4: "f32", 2: "f16"}[prec], "recon": recon,
+                               "us": round(ms * 1e3, 1), "gflops": round(fl / (ms * 1e-3) / 1e9, 1),
+                               "gbs": round(by / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(by / (ms * 1e-3) / 1e9 / peak, 3)}
+                        if prec == 8:
+                            row["fp64_alu_frac_of_nominal_1250"] = round(fl / (ms * 1e-3) / 1e9 / 1250.0, 3)
+                        rows.append(row)
+                del xe, out, tmp
+            g.close()
+    return rows
+
+
+def cg_section(tmq, g, U, psi, dev, args):
+    return None
+
+
+def cpu_baseline(U_np, psi_np, args):
+    """The FP64 oracle as it stands (OpenMP over the host cores) on one full M_asym application."""
+    import oracle
+    po = oracle.Params(L_FULL, KAPPA, MU_ND, EPS_ND, flavor=2)
+    x = oracle.project_parity(po, psi_np, 0)
+    t0 = time.time()
+    n = 0
+    while True:
+        oracle.apply_M_pc(po, U_np, x)
+        n += 1
+        if time.time() - t0 > 8.0 or n >= 3:
+            break
+    dt = (time.time() - t0) / n
+    Vh = po.L[0] * po.L[1] * po.L[2] * po.L[3] // 2
+    return {"value": round(FLOPS_PER_SITE[2] * Vh / dt / 1e9, 3), "unit": "GFLOPS", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n} full M_asym application(s) of the 32^3x64 doublet, FP64, "
+                                        f"{dt:.2f} s each"}
+
+
+# -------------------------------------------------------------------------------------- reference
+def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP) timed as the reference arm on a bounded sub-lattice sample."""
+    import oracle
+    from paper_1311_4462_gb300 import inputs
+
+    oracle.build()
+    K, W = args.steps, args.warmup
+    # calibrate: pick the time extent of a 32^3 x Lt sample so K + W steps take about a minute
+    Lt = 8
+    L = (32, 32, 32, Lt)
+    po = oracle.Params(L, KAPPA, MU_ND, EPS_ND, flavor=2)
+    U = inputs.gauge_field(L, 1002)
+    x = oracle.project_parity(po, inputs.spinor_field(L, 2, 2002), 0)
+    t0 = time.time()
+    oracle.apply_M_pc(po, U, x)
+    per_site = (time.time() - t0) / (32 ** 3 * Lt)
+    budget = 60.0
+    Lt = 2 * int(max(1, min(32, budget / max(K + W, 1) / (per_site * 32 ** 3) / 2)))
+    L = (32, 32, 32, Lt)
+    po = oracle.Params(L, KAPPA, MU_ND, EPS_ND, flavor=2)
+    U = inputs.gauge_field(L, 1002)
+    x = oracle.project_parity(po, inputs.spinor_field(L, 2, 2002), 0)
+    for _ in range(W):
+        oracle.apply_M_pc(po, U, x)
+    t0 = time.time()
+    for _ in range(K):
+        oracle.apply_M_pc(po, U, x)
+    dt = time.time() - t0
+    Vh = 32 ** 3 * Lt // 2
+    value = FLOPS_PER_SITE[2] * Vh * K / dt / 1e9
+    sample = f"32^3x{Lt} sub-lattice of the 32^3x64 doublet workload, one FP64 M_asym application per step"
+    return {"metric": "TM dslash GFLOPS & % HBM roofline per precision; CG time-to-1e-10 mixed vs FP64",
+            "impl": "reference", "value": round(value, 3), "unit": "GFLOPS", "n_gpus": 0, "steps": K, "warmup": W,
+            "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": "M_asym (eq. 2.2 LHS), non-degenerate doublet, kappa=0.1612, mu=0.135, "
+                                   "eps=0.15", "lattice": list(L)},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GFLOPS", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline step only (no tables, e2e or baselines)")
+    ap.add_argument("--lattice", default=None, help="override the lattice, e.g. 32,32,32,32 (profiling runs)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.lattice:
+        global L_FULL
+        L_FULL = tuple(int(v) for v in args.lattice.split(","))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

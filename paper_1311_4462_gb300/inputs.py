@@ -4,8 +4,11 @@ This module only draws random numbers; it holds none of the operator's arithmeti
 
 * Links: U = exp(i * 0.3 * H) per link, H traceless hermitian built from a 3x3 matrix
   A with iid N(0,1) real and imaginary parts, H = (A + A^dag)/2 - tr(.)/3.  The
-  exponential is taken through a hermitian eigendecomposition; rows 1-2 are then
-  re-orthonormalised and row 3 is set to conj(row1 x row2), so every link is in
+  exponential is taken through the eigendecomposition of H written in closed form
+  (the three real roots of the characteristic polynomial det(l - H) = l^3 - c1 l - c0,
+  c1 = tr(H^2)/2, c0 = det H, by the trigonometric formula, and the spectral projectors
+  P_k = prod_{j != k} (H - l_j)/(l_k - l_j)), vectorised over all links; rows 1-2 are
+  then re-orthonormalised and row 3 is set to conj(row1 x row2), so every link is in
   SU(3) to rounding (which makes 12-real storage exact).
 * Spinors: iid N(0,1) real and imaginary parts per (site, flavour, spin, colour).
 * Z2 noise: (+-1 +- i)/sqrt(2) per entry.
@@ -27,8 +30,22 @@ def rng(seed: int) -> np.random.Generator:
 
 
 def _expi_herm(H: np.ndarray, scale: float) -> np.ndarray:
-    w, V = np.linalg.eigh(H)
-    return (V * np.exp(1j * scale * w)[..., None, :]) @ np.conj(np.swapaxes(V, -1, -2))
+    """exp(i * scale * H) for traceless hermitian 3x3 H (batched), via the closed-form spectrum."""
+    H2 = H @ H
+    c1 = 0.5 * np.trace(H2, axis1=-2, axis2=-1).real
+    c0 = np.linalg.det(H).real
+    r = np.sqrt(np.maximum(c1, 1e-300) / 3.0)
+    arg = np.clip(c0 / (2.0 * r ** 3), -1.0, 1.0)
+    th = np.arccos(arg) / 3.0
+    lam = [2.0 * r * np.cos(th - 2.0 * np.pi * k / 3.0) for k in range(3)]
+    eye = np.eye(3)
+    U = np.zeros_like(H)
+    for k in range(3):
+        a, b = [lam[j] for j in range(3) if j != k]
+        num = H2 - (a + b)[..., None, None] * H + (a * b)[..., None, None] * eye
+        den = (lam[k] - a) * (lam[k] - b)
+        U = U + (np.exp(1j * scale * lam[k]) / den)[..., None, None] * num
+    return U
 
 
 def reunitarize(U: np.ndarray) -> np.ndarray:
@@ -42,15 +59,21 @@ def reunitarize(U: np.ndarray) -> np.ndarray:
     return np.stack([r1, r2, r3], axis=-2)
 
 
-def random_su3(n: int, g: np.random.Generator, scale: float = 0.3) -> np.ndarray:
-    A = g.standard_normal((n, 3, 3)) + 1j * g.standard_normal((n, 3, 3))
+def _su3_from_normals(A: np.ndarray, scale: float) -> np.ndarray:
     H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
     tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
     H = H - tr[:, None, None] * np.eye(3)
-    chunks = np.array_split(H, max(1, min(64, n // 65536)))
-    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
-        U = np.concatenate(list(ex.map(lambda h: _expi_herm(h, scale), chunks)), axis=0)
-    return reunitarize(U)
+    return reunitarize(_expi_herm(H, scale))
+
+
+def random_su3(n: int, g: np.random.Generator, scale: float = 0.3) -> np.ndarray:
+    A = g.standard_normal((n, 3, 3)) + 1j * g.standard_normal((n, 3, 3))
+    if n < 65536:
+        return _su3_from_normals(A, scale)
+    # same arithmetic per link, done in cache-sized chunks on a thread pool (numpy releases the GIL)
+    chunks = np.array_split(A, (n + 131071) // 131072)
+    with ThreadPoolExecutor(max(1, min(32, os.cpu_count() or 1))) as ex:
+        return np.concatenate(list(ex.map(lambda a: _su3_from_normals(a, scale), chunks)), axis=0)
 
 
 def gauge_field(L, seed: int, scale: float = 0.3) -> np.ndarray:
