@@ -183,6 +183,68 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
 tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger,
                    void *stream);
 
+/* ------------------------------------------------------------------------------ solvers */
+/* CG on the normal equations (sec. 2.2: solve_type NORMOP on the even-odd preconditioned
+ * system), either all in FP64 or as the mixed-precision reliable-update CG the paper runs
+ * in production (double-single / double-half, sec. 3 and ref. [Clark:2009wm]). */
+typedef enum { TM_SOLVER_CG = 0, TM_SOLVER_MIXED_CG = 1 } tm_solver_type;
+/* solution_type (sec. 2.2): MAT solves A x = b, MATDAG_MAT solves A^dag A x = b, where
+ * A = M_pc of tm_precond_op (or its adjoint when dagger = 1). */
+typedef enum { TM_SOLUTION_MAT = 0, TM_SOLUTION_MATDAG_MAT = 1 } tm_solution_type;
+
+typedef struct {
+    int solver;      /* tm_solver_type */
+    int solution;    /* tm_solution_type */
+    int pc;          /* tm_pc */
+    int dagger;      /* 1: A = M_pc^dag */
+    double tol;      /* stop when |bhat - A^dag A x| / |bhat| <= tol (FP64 true residual);
+                        bhat = A^dag b (MAT) or b (MATDAG_MAT) */
+    int maxiter;     /* CG iterations (sloppy iterations for the mixed solver) */
+    double delta;    /* mixed: reliable update when |r_sloppy| < delta * max |r| since the last one */
+    int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
+    int use_x0;      /* 1: x_e holds the initial guess on entry; 0: start from zero */
+} tm_solver_params;
+
+typedef struct {
+    int iterations;
+    int reliable_updates; /* mixed: reliable updates; FP64 CG: restarts from the true residual */
+    double true_residual; /* |bhat - A^dag A x| / |bhat|, recomputed in FP64 at exit */
+    double pc_residual;   /* |A x - b| / |b| for MAT solutions (-1 for MATDAG_MAT) */
+    double seconds;       /* host wall time of the call */
+} tm_solver_stats;
+
+/* Device workspace tm_solve needs for these parameters (caller allocates, 256-byte aligned). */
+tm_status tm_solve_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp, size_t *bytes);
+
+/*
+ * Solve on the even sites.  x_e (in/out) and b_e are FP64 single-RHS fields.  Blocks until
+ * the solve ends (one scalar read per iteration).  Errors: TM_ERR_ARG, TM_ERR_NOMEM
+ * (workspace too small), TM_ERR_NOCONV (maxiter reached; x_e holds the last iterate and the
+ * stats are filled), TM_ERR_NAN (non-finite residual), TM_ERR_CUDA.
+ */
+tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
+                   tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/* FP64-accumulated reductions over one parity field (blocking): |x|^2 and Re<a, b>. */
+tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stream);
+tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, void *stream);
+
+/* ------------------------------------------------------------------------ differentiation */
+/*
+ * Link gradient of L(U) = Re <g, M(U) psi> for every link, in the convention
+ * dL = Re sum_ij conj(F_ij) dU_ij (the gradient torch's autograd propagates for complex U):
+ *   F_mu(x) = coef * (-kappa) * bc * sum_flavour [ sum_s ((1 - gamma_mu) g(x))_s psi(x+mu)_s^dag
+ *                                                 + sum_s psi(x)_s ((1 + gamma_mu) g(x+mu))_s^dag ]
+ * with bc = -1 on links across the antiperiodic time boundary (eq. 2.1 differentiated; R does
+ * not depend on U).  project = 1 returns the su(3) tangent-space part TA(F U^dag) U, TA(Z) =
+ * (Z - Z^dag)/2 - tr(Z - Z^dag)/6, which is what a gradient along SU(3) needs.  The pseudofermion
+ * force of S = phi^dag (M^dag M)^-1 phi is the case psi = X = (M^dag M)^-1 phi, g = Y = M X,
+ * coef = -2.  psi and g: FP64 or FP32 fields of both parities.  F_canon: device pointer to the
+ * canonical gauge layout, complex128 (canon_type TM_C128) or complex64.
+ */
+tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_field *psi_e, const tm_field *psi_o,
+                   const tm_field *g_e, const tm_field *g_o, double coef, int project, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

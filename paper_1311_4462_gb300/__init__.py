@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib as L
-from ._lib import (TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM,
+from ._lib import (TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT, TM_SOLVER_CG, TM_SOLVER_MIXED, TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM,
                    TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_NDEG_DOUBLET, TM_PC_ASYM, TM_PC_SYM, TM_PREC_F16, TM_PREC_F32,
                    TM_PREC_F64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
 
@@ -189,6 +189,66 @@ def reconstruct_odd(gauge, psi_o: Field, b_o: Field, psi_e: Field, dagger=False,
 
 def twist(gauge, out: Field, inp: Field, inverse=False, dagger=False, stream=None):
     L.check(L.load().tm_twist(gauge.h, out.ref(), inp.ref(), int(inverse), int(dagger), _stream(stream)))
+    return out
+
+
+def norm2(gauge, x: Field, stream=None) -> float:
+    """tm_norm2: |x|^2 with FP64 accumulation (blocking)."""
+    out = ctypes.c_double()
+    L.check(L.load().tm_norm2(gauge.h, x.ref(), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def dot(gauge, a: Field, b: Field, stream=None) -> float:
+    """tm_dot: Re<a, b> with FP64 accumulation (blocking)."""
+    out = ctypes.c_double()
+    L.check(L.load().tm_dot(gauge.h, a.ref(), b.ref(), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000,
+                  delta=0.1, sloppy_prec=TM_PREC_F32, use_x0=False):
+    sp = L.tm_solver_params()
+    sp.solver = TM_SOLVER_MIXED if solver == "mixed" else TM_SOLVER_CG
+    sp.solution, sp.pc, sp.dagger = int(solution), int(pc), int(dagger)
+    sp.tol, sp.maxiter, sp.delta = float(tol), int(maxiter), float(delta)
+    sp.sloppy_prec, sp.use_x0 = int(sloppy_prec), int(use_x0)
+    return sp
+
+
+def solve_workspace_bytes(gauge, sp) -> int:
+    n = ctypes.c_size_t()
+    L.check(L.load().tm_solve_workspace_bytes(gauge.h, ctypes.byref(sp), ctypes.byref(n)))
+    return n.value
+
+
+def solve(gauge, x_e: Field, b_e: Field, stream=None, workspace=None, check=True, **kw):
+    """tm_solve on the even sites (x_e, b_e: FP64 Fields).  Returns the stats as a dict
+    (with 'status'); raises TMError on failure unless check=False."""
+    torch = _torch()
+    sp = solver_params(**kw)
+    nbytes = solve_workspace_bytes(gauge, sp)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = L.tm_solver_stats()
+    status = L.load().tm_solve(gauge.h, x_e.ref(), b_e.ref(), ctypes.byref(sp), ctypes.byref(st),
+                               ctypes.c_void_p(workspace.data_ptr()), nbytes, _stream(stream))
+    out = {"status": status, "iterations": st.iterations, "reliable_updates": st.reliable_updates,
+           "true_residual": st.true_residual, "pc_residual": st.pc_residual, "seconds": st.seconds}
+    if check:
+        L.check(status)
+    return out
+
+
+def force(gauge, psi_e: Field, psi_o: Field, g_e: Field, g_o: Field, coef=1.0, project=True, out=None, stream=None):
+    """tm_force: link gradient of Re<g, M(U) psi> in the canonical gauge layout."""
+    torch = _torch()
+    dt = torch.complex128 if psi_e.prec == TM_PREC_F64 else torch.complex64
+    if out is None:
+        out = torch.empty(gauge.params.gauge_shape, dtype=dt, device="cuda")
+    ct = L.TM_C128 if out.dtype == torch.complex128 else L.TM_C64
+    L.check(L.load().tm_force(gauge.h, ctypes.c_void_p(out.data_ptr()), ct, psi_e.ref(), psi_o.ref(), g_e.ref(),
+                              g_o.ref(), float(coef), int(project), _stream(stream)))
     return out
 
 

@@ -29,6 +29,17 @@ class tm_field(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("prec", ctypes.c_int), ("nrhs", ctypes.c_int)]
 
 
+class tm_solver_params(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("solution", ctypes.c_int), ("pc", ctypes.c_int), ("dagger", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("delta", ctypes.c_double),
+                ("sloppy_prec", ctypes.c_int), ("use_x0", ctypes.c_int)]
+
+
+class tm_solver_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_residual", ctypes.c_double),
+                ("pc_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
 class TMError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -55,6 +66,12 @@ _SIGS = {
     "tm_prepare_rhs": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
     "tm_reconstruct_odd": [vp, FP, FP, FP, ctypes.c_int, vp],
     "tm_twist": [vp, FP, FP, ctypes.c_int, ctypes.c_int, vp],
+    "tm_solve_workspace_bytes": [vp, ctypes.POINTER(tm_solver_params), ctypes.POINTER(ctypes.c_size_t)],
+    "tm_solve": [vp, FP, FP, ctypes.POINTER(tm_solver_params), ctypes.POINTER(tm_solver_stats), vp, ctypes.c_size_t,
+                 vp],
+    "tm_norm2": [vp, FP, ctypes.POINTER(ctypes.c_double), vp],
+    "tm_dot": [vp, FP, FP, ctypes.POINTER(ctypes.c_double), vp],
+    "tm_force": [vp, vp, ctypes.c_int, FP, FP, FP, FP, ctypes.c_double, ctypes.c_int, vp],
 }
 
 

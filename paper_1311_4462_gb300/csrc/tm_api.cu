@@ -307,6 +307,10 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
             st = cuda_check(cudaMemsetAsync(g->scratch, 0, g->scratch_bytes, s), "scratch memset");
         }
     }
+    if (st == TM_OK && cudaHostAlloc((void **)&g->host_scalars, 4096, cudaHostAllocDefault) != cudaSuccess) {
+        set_error("tm_gauge_create: pinned host allocation failed");
+        st = TM_ERR_NOMEM;
+    }
     if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tm_gauge_create sync");
     if (st != TM_OK) {
         tm_gauge_destroy(g);
@@ -323,6 +327,7 @@ tm_status tm_gauge_destroy(tm_gauge *g)
     for (int i = 0; i < 3; i++)
         if (g->links[i]) cudaFree(g->links[i]);
     if (g->scratch) cudaFree(g->scratch);
+    if (g->host_scalars) cudaFreeHost(g->host_scalars);
     delete g;
     return TM_OK;
 }

@@ -1,10 +1,18 @@
-// tm_blas.cu -- site-wise kernels on parity fields: the standalone local twist.
-#include "tm_core.cuh"
+// tm_blas.cu -- site-wise kernels on parity fields: local twist, linear combinations,
+// precision conversion and FP64-accumulated reductions for the CG solvers.
+//
+// Every kernel walks "site blocks": one (rhs, flavour, site) triple = the 24 reals of a site,
+// so FP16 fields keep one norm per block.  Arithmetic is FP64 when any operand is stored in
+// FP64, else FP32; reductions add each site's FP32/FP64 partial into an FP64 thread sum,
+// reduce warps with shuffles, blocks through shared memory, and the last block to finish
+// (atomic ticket) sums the per-block partials in block order -- deterministic for a fixed
+// grid -- and applies a small scalar update (CG's alpha / beta) on the device.
+#include "tm_blas.cuh"
 #include "tm_internal.h"
 
 namespace tmk {
 
-// thread per (rhs, cb): both flavours of the site are twisted together (tau1 mixes them)
+// ---------------------------------------------------------------------------- twist
 template <int PREC, int NF>
 __global__ void k_twist(void *out, float *out_norm, const void *in, const float *in_norm, int Vh, int nrhs,
                         Twist<typename Traits<PREC>::real> tw)
@@ -61,6 +69,199 @@ cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field 
     }
 #undef TM_T
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- reductions
+// Block-level sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Write this block's partial for column `col` (one column per rhs = blockIdx.y); the last block
+// of the whole grid sums every column in block order and applies `fin` per column.
+__device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
+{
+    const int col = blockIdx.y;
+    if (threadIdx.x == 0) r.partials[(size_t)col * gridDim.x + blockIdx.x] = part;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y;
+        last = (atomicAdd(r.counter, 1u) == total - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = threadIdx.x; c < (int)gridDim.y; c += blockDim.x) {
+        double s = 0.0;
+        const volatile double *pp = r.partials + (size_t)c * gridDim.x;
+        for (unsigned b = 0; b < gridDim.x; b++) s += pp[b];
+        double *S = r.scalars;
+        const int R = TM_MAX_RHS;
+        const bool active = !r.active || r.active[c];
+        switch (r.fin) {
+        case FIN_STORE: S[r.slot * R + c] = s; break;
+        case FIN_ALPHA:  // pAp -> alpha = rr / pAp
+            S[SL_PAP * R + c] = s;
+            S[SL_ALPHA * R + c] = (active && s != 0.0) ? S[SL_RR * R + c] / s : 0.0;
+            break;
+        case FIN_BETA:  // |r|^2 new -> beta = rr_new / rr, rr = rr_new
+            S[SL_RRNEW * R + c] = s;
+            S[SL_BETA * R + c] = (active && S[SL_RR * R + c] != 0.0) ? s / S[SL_RR * R + c] : 0.0;
+            if (active) S[SL_RR * R + c] = s;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) *r.counter = 0u;  // ready for the next launch on this stream
+}
+
+// ------------------------------------------------------------------------- generic site op
+// One launch: for every site block, load operands a, b, c (any precision), compute
+//   out = ca * a + cb * b   (op AXPBY)      -- then optional reduction of |out|^2
+//   cg:  c += alpha * a ; b -= alpha * Ap  (op CG_UPDATE with a = p, d = Ap) -- reduction |b|^2
+//   dot: reduce Re<a, b>                    (op DOT)
+//   norm: reduce |a|^2                      (op NORM)
+//   copy: out = a                           (op COPY)
+// Coefficients come from SVal (host value or device scalar slot times a host multiplier).
+__device__ __forceinline__ double sval(const SVal &v, int rhs, const double *S)
+{
+    return v.slot >= 0 ? v.mult * S[v.slot * TM_MAX_RHS + rhs] : v.value;
+}
+
+template <int PA, int PB, int PC, int PD, typename T>
+__global__ void __launch_bounds__(256) k_site_op(SiteOpArgs a)
+{
+    const long nper = (long)a.Vh * a.nf;  // site blocks per rhs
+    const int rhs = blockIdx.y;
+    double acc = 0.0;
+    const bool active = !a.red.active || a.red.active[rhs];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nper && active; i += (long)gridDim.x * blockDim.x) {
+        const int cb = (int)(i % a.Vh);
+        const long blk = (long)rhs * a.nf + i / a.Vh;
+        T va[24], vb[24], vc[24], vd[24];
+        (void)vc;
+        T part = T(0);
+        switch (a.op) {
+        case OP_AXPBY: {
+            const T ca = (T)sval(a.ca, rhs, a.red.scalars), cbv = (T)sval(a.cb, rhs, a.red.scalars);
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            if (a.B.data) load_block<PB>(a.B, blk, cb, a.Vh, vb);
+#pragma unroll
+            for (int k = 0; k < 24; k++) {
+                const T o = a.B.data ? fma(ca, va[k], cbv * vb[k]) : ca * va[k];
+                va[k] = o;
+            }
+            store_block<PC>(a.C, blk, cb, a.Vh, va);  // va now holds the stored values
+            if (a.reduce) {
+#pragma unroll
+                for (int k = 0; k < 24; k++) part = fma(va[k], va[k], part);
+            }
+            break;
+        }
+        case OP_CG_UPDATE: {  // A = p, B = r, C = x, D = Ap
+            const T al = (T)sval(a.ca, rhs, a.red.scalars);
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            load_block<PC>(a.C, blk, cb, a.Vh, vc);
+#pragma unroll
+            for (int k = 0; k < 24; k++) vc[k] = fma(al, va[k], vc[k]);
+            store_block<PC>(a.C, blk, cb, a.Vh, vc);
+            load_block<PB>(a.B, blk, cb, a.Vh, vb);
+            load_block<PD>(a.D, blk, cb, a.Vh, vd);
+#pragma unroll
+            for (int k = 0; k < 24; k++) vb[k] = fma(-al, vd[k], vb[k]);
+            store_block<PB>(a.B, blk, cb, a.Vh, vb);  // vb now holds the stored values
+#pragma unroll
+            for (int k = 0; k < 24; k++) part = fma(vb[k], vb[k], part);
+            break;
+        }
+        case OP_DOT: {
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            load_block<PB>(a.B, blk, cb, a.Vh, vb);
+#pragma unroll
+            for (int k = 0; k < 24; k++) part = fma(va[k], vb[k], part);  // Re<a,b> = sum re*re + im*im
+            break;
+        }
+        case OP_NORM: {
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+#pragma unroll
+            for (int k = 0; k < 24; k++) part = fma(va[k], va[k], part);
+            break;
+        }
+        default: {  // OP_COPY
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            store_block<PC>(a.C, blk, cb, a.Vh, va);
+            break;
+        }
+        }
+        acc += (double)part;
+    }
+    if (a.reduce) {
+        const double s = block_sum(acc);
+        grid_finish(s, a.red);
+    }
+}
+
+template <int PA, int PB, int PC, int PD>
+static cudaError_t run_combo(const SiteOpArgs &a, dim3 grid, int block, cudaStream_t s)
+{
+    constexpr bool any64 = (PA == P64) || (PB == P64) || (PC == P64) || (PD == P64);
+    if (any64) k_site_op<PA, PB, PC, PD, double><<<grid, block, 0, s>>>(a);
+    else k_site_op<PA, PB, PC, PD, float><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// precision of a possibly-absent operand; an absent operand takes the first operand's
+static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
+
+// The operand precision combinations (A, B, C, D) the solvers use.
+#define TM_COMBOS(X)          \
+    X(P64, P64, P64, P64)     \
+    X(P32, P32, P32, P32)     \
+    X(P16, P16, P16, P16)     \
+    X(P16, P16, P32, P16)     \
+    X(P32, P64, P64, P32)     \
+    X(P64, P64, P32, P64)     \
+    X(P64, P64, P16, P64)     \
+    X(P32, P32, P64, P32)     \
+    X(P16, P16, P64, P16)     \
+    X(P32, P32, P16, P32)
+
+cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s)
+{
+    a.Vh = g->Vh;
+    a.nf = g->nf;
+    const int block = 256;
+    const long nper = (long)a.Vh * a.nf;
+    long gx = (nper + block - 1) / block;
+    const long cap = (long)g->num_sms * 4;
+    if (gx > cap) gx = cap;
+    const long maxcols = (long)((g->scratch_bytes - SCRATCH_PARTIALS_OFF) / sizeof(double)) / nrhs;
+    if (a.reduce && gx > maxcols) gx = maxcols;
+    dim3 grid((unsigned)gx, (unsigned)nrhs);
+    a.red.partials = reinterpret_cast<double *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_PARTIALS_OFF);
+    a.red.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_COUNTER_OFF);
+    if (!a.red.scalars) a.red.scalars = g->scratch;
+    const int pa = a.A.prec;
+    const int pb = pc_of(a.B, pa), pc = pc_of(a.C, pa), pd = pc_of(a.D, pa);
+#define TM_TRY_COMBO(A_, B_, C_, D_) \
+    if (pa == A_ && pb == B_ && pc == C_ && pd == D_) return run_combo<A_, B_, C_, D_>(a, grid, block, s);
+    TM_COMBOS(TM_TRY_COMBO)
+#undef TM_TRY_COMBO
+    return cudaErrorNotSupported;
 }
 
 }  // namespace tmk

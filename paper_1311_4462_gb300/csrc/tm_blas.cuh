@@ -1,0 +1,98 @@
+// tm_blas.cuh -- argument structs and block codecs for the site-wise kernels (tm_blas.cu)
+// and the solvers (tm_solver.cu).
+#pragma once
+#include "tm_core.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+constexpr int TM_MAX_RHS = 64;  // columns of the device scalar table
+
+// device scalar table: scalars[slot * TM_MAX_RHS + rhs]
+enum Slot { SL_RR = 0, SL_RRNEW = 1, SL_PAP = 2, SL_ALPHA = 3, SL_BETA = 4, SL_TMP0 = 5, SL_TMP1 = 6, SL_TMP2 = 7,
+            SL_COUNT = 16 };
+// scratch layout inside the gauge handle's scratch area
+constexpr size_t SCRATCH_SCALARS_OFF = 0;                                       // 16 x 64 doubles
+constexpr size_t SCRATCH_COUNTER_OFF = SL_COUNT * TM_MAX_RHS * sizeof(double);  // 8 KB: ticket counter
+constexpr size_t SCRATCH_PARTIALS_OFF = 16384;                                  // per-block partial sums
+
+enum SiteOpCode { OP_AXPBY = 0, OP_CG_UPDATE = 1, OP_DOT = 2, OP_NORM = 3, OP_COPY = 4 };
+enum FinCode { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+struct FieldRef {
+    void *data;
+    float *norm;
+    int prec;
+};
+
+// a coefficient: host value, or mult * scalars[slot][rhs] when slot >= 0
+struct SVal {
+    double value;
+    int slot;
+    double mult;
+};
+
+struct RedArgs {
+    double *partials;
+    unsigned *counter;
+    double *scalars;
+    const int *active;  // per-rhs mask (NULL: all active)
+    int fin;
+    int slot;
+};
+
+struct SiteOpArgs {
+    int op;
+    int reduce;
+    FieldRef A, B, C, D;
+    SVal ca, cb;
+    RedArgs red;
+    int Vh, nf;
+};
+
+// Load / store one site block (blk = rhs * nf + flavour) of a field given by FieldRef.
+template <int PREC, typename T>
+__device__ __forceinline__ void load_block(const FieldRef &f, long blk, int cb, int Vh, T v[24])
+{
+    using SC = typename Traits<PREC>::schunk;
+    using R = typename Traits<PREC>::real;
+    R tmp[24];
+    const SC *p = reinterpret_cast<const SC *>(f.data) + blk * Traits<PREC>::SCHUNKS * (long)Vh;
+    load_spinor<PREC>(p, f.norm ? f.norm + blk * Vh : nullptr, cb, Vh, tmp);
+#pragma unroll
+    for (int k = 0; k < 24; k++) v[k] = (T)tmp[k];
+}
+
+// Stores v and replaces it by the value as stored (rounded to the storage precision), so a
+// following reduction sees exactly what was written without reading memory back.
+template <int PREC, typename T>
+__device__ __forceinline__ void store_block(const FieldRef &f, long blk, int cb, int Vh, T v[24])
+{
+    using SC = typename Traits<PREC>::schunk;
+    using R = typename Traits<PREC>::real;
+    R tmp[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) tmp[k] = (R)v[k];
+    SC *p = reinterpret_cast<SC *>(f.data) + blk * Traits<PREC>::SCHUNKS * (long)Vh;
+    store_spinor<PREC>(p, f.norm ? f.norm + blk * Vh : nullptr, cb, Vh, tmp);
+    if (PREC == P16) {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; k++) m = fmaxf(m, fabsf((float)tmp[k]));
+        const float inv = (m > 0.f) ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; k++) v[k] = (T)(__half2float(__float2half_rn((float)tmp[k] * inv)) * m);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 24; k++) v[k] = (T)tmp[k];
+    }
+}
+
+cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s);
+
+inline FieldRef fref(const tm_field *f) { return FieldRef{f->data, f->norm, f->prec}; }
+inline FieldRef fnone() { return FieldRef{nullptr, nullptr, 0}; }
+inline SVal sv(double v) { return SVal{v, -1, 1.0}; }
+inline SVal sslot(int slot, double mult) { return SVal{0.0, slot, mult}; }
+
+}  // namespace tmk

@@ -1,0 +1,256 @@
+// tm_force.cu -- link gradient of the twisted-mass operator (eq. 2.1) for differentiation.
+//
+// For L = Re <g, M(U) psi> (inner product conjugate-linear in g) only the two hopping terms
+// holding U_mu(x) depend on it: the forward hop at x and the backward hop at x + mu.  With
+// dL = Re sum_ij conj(G_ij) dU_ij the gradient is
+//   G_mu(x) = -kappa * bc * sum_f [ sum_s ((1 - g_mu) g(x))_s  psi(x+mu)_s^dag
+//                                  + sum_s psi(x)_s ((1 + g_mu) g(x+mu))_s^dag ]
+// (bc = -1 on links across the antiperiodic time boundary), times a caller coefficient.
+// The twist R does not depend on U.  project = 1 returns the component in the tangent space
+// of SU(3) at U: P(G) = TA(G U^dag) U with TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6.
+// One thread per link; the colour outer products are summed over spin and flavour in
+// registers and the 3x3 result is written in the canonical gauge layout.
+#include "tm_blas.cuh"
+#include "tm_core.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+struct ForceArgs {
+    const void *psi[2];
+    const float *psi_norm[2];
+    const void *gv[2];
+    const float *gv_norm[2];
+    const void *gauge;
+    void *out;
+    int Vh, X1h, Lx, Ly, Lz, Lt, nf, tbc, project;
+    double coef;  // -kappa * caller coefficient
+};
+
+// (gamma_mu v)_s for the DeGrand-Rossi basis, returned as complex spin components
+template <typename T, int MU>
+__device__ __forceinline__ void gamma_apply(const C<T> v[4][3], C<T> o[4][3])
+{
+    const C<T> I1 = {T(0), T(1)};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (MU == 0) {
+            o[0][c] = cmul(I1, v[3][c]);
+            o[1][c] = cmul(I1, v[2][c]);
+            o[2][c] = cscale(T(-1), cmul(I1, v[1][c]));
+            o[3][c] = cscale(T(-1), cmul(I1, v[0][c]));
+        } else if (MU == 1) {
+            o[0][c] = cscale(T(-1), v[3][c]);
+            o[1][c] = v[2][c];
+            o[2][c] = v[1][c];
+            o[3][c] = cscale(T(-1), v[0][c]);
+        } else if (MU == 2) {
+            o[0][c] = cmul(I1, v[2][c]);
+            o[1][c] = cscale(T(-1), cmul(I1, v[3][c]));
+            o[2][c] = cscale(T(-1), cmul(I1, v[0][c]));
+            o[3][c] = cmul(I1, v[1][c]);
+        } else {
+            o[0][c] = v[2][c];
+            o[1][c] = v[3][c];
+            o[2][c] = v[0][c];
+            o[3][c] = v[1][c];
+        }
+    }
+}
+
+template <int PREC, typename T>
+__device__ __forceinline__ void load_sp(const void *base, const float *norm, int f, int cb, int Vh, C<T> v[4][3])
+{
+    using SC = typename Traits<PREC>::schunk;
+    using R = typename Traits<PREC>::real;
+    R r[24];
+    const SC *p = reinterpret_cast<const SC *>(base) + (long)f * Traits<PREC>::SCHUNKS * Vh;
+    load_spinor<PREC>(p, norm ? norm + (long)f * Vh : nullptr, cb, Vh, r);
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[s][c] = {(T)r[2 * (3 * s + c)], (T)r[2 * (3 * s + c) + 1]};
+}
+
+template <int PREC, int MU, typename T>
+__device__ __forceinline__ void accumulate_link(const ForceArgs &a, int par, int cb, int nb, C<T> m[3][3])
+{
+    for (int f = 0; f < a.nf; f++) {
+        C<T> gx[4][3], gy[4][3], px[4][3], py[4][3], t[4][3];
+        load_sp<PREC>(a.gv[par], a.gv_norm[par], f, cb, a.Vh, gx);
+        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, py);
+        // w1 = (1 - gamma) g(x): sum_s w1_s psi(x+mu)_s^dag
+        gamma_apply<T, MU>(gx, t);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) gx[s][c] = csub(gx[s][c], t[s][c]);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(gx[s][i], cconj(py[s][j])));
+        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, gy);
+        load_sp<PREC>(a.psi[par], a.psi_norm[par], f, cb, a.Vh, px);
+        // w2 = (1 + gamma) g(x+mu): sum_s psi(x)_s w2_s^dag
+        gamma_apply<T, MU>(gy, t);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) gy[s][c] = cadd(gy[s][c], t[s][c]);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(px[s][i], cconj(gy[s][j])));
+    }
+}
+
+template <int PREC, int RECON, typename CT>
+__global__ void k_force(const ForceArgs a)
+{
+    using T = typename Traits<PREC>::real;
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 8L * a.Vh) return;
+    const int cb = (int)(id % a.Vh);
+    const int par = (int)((id / a.Vh) % 2);
+    const int mu = (int)(id / (2L * a.Vh));
+    int r = cb;
+    const int xh = r % a.X1h;
+    r /= a.X1h;
+    const int y = r % a.Ly;
+    r /= a.Ly;
+    const int z = r % a.Lz;
+    const int t = r / a.Lz;
+    const int x = 2 * xh + ((par + y + z + t) & 1);
+    int nb;
+    T bc = T(1);
+    if (mu == 0) nb = (cb - xh) + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
+    else if (mu == 1) nb = (y == a.Ly - 1) ? cb - (a.Ly - 1) * a.X1h : cb + a.X1h;
+    else if (mu == 2) nb = (z == a.Lz - 1) ? cb - (a.Lz - 1) * a.X1h * a.Ly : cb + a.X1h * a.Ly;
+    else {
+        const int s = a.X1h * a.Ly * a.Lz;
+        nb = (t == a.Lt - 1) ? cb - (a.Lt - 1) * s : cb + s;
+        if (t == a.Lt - 1 && a.tbc) bc = T(-1);
+    }
+    C<T> m[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) m[i][j] = {T(0), T(0)};
+    if (mu == 0) accumulate_link<PREC, 0>(a, par, cb, nb, m);
+    else if (mu == 1) accumulate_link<PREC, 1>(a, par, cb, nb, m);
+    else if (mu == 2) accumulate_link<PREC, 2>(a, par, cb, nb, m);
+    else accumulate_link<PREC, 3>(a, par, cb, nb, m);
+    const T sc = (T)a.coef * bc;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) m[i][j] = cscale(sc, m[i][j]);
+    if (a.project) {
+        using LL = LinkLayout<PREC, RECON>;
+        const typename LL::chunk *G = reinterpret_cast<const typename LL::chunk *>(a.gauge);
+        Link<T> U;
+        LinkLoader<PREC, RECON>::load(G + (size_t)(mu * 2 + par) * LL::N * a.Vh, cb, a.Vh, U);
+        C<T> zz[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                C<T> s = {T(0), T(0)};
+#pragma unroll
+                for (int k = 0; k < 3; k++) s = cadd(s, cmul(m[i][k], cconj(U.u[j][k])));
+                zz[i][j] = s;
+            }
+        // TA(Z) = (Z - Z^dag)/2 - i Im tr(Z)/3 (the trace of (Z - Z^dag)/2 is i Im tr Z)
+        const T imtr = (zz[0][0].i + zz[1][1].i + zz[2][2].i) / T(3);
+        C<T> ta[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                ta[i][j] = {T(0.5) * (zz[i][j].r - zz[j][i].r), T(0.5) * (zz[i][j].i + zz[j][i].i)};
+                if (i == j) ta[i][j].i -= imtr;
+            }
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                C<T> s = {T(0), T(0)};
+#pragma unroll
+                for (int k = 0; k < 3; k++) s = cadd(s, cmul(ta[i][k], U.u[k][j]));
+                m[i][j] = s;
+            }
+    }
+    const long lex = x + (long)a.Lx * (y + (long)a.Ly * (z + (long)a.Lz * t));
+    const long V = 2L * a.Vh;
+    CT *o = reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex) * 9;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            CT v;
+            v.x = m[i][j].r;
+            v.y = m[i][j].i;
+            o[3 * i + j] = v;
+        }
+}
+
+}  // namespace tmk
+
+using namespace tmk;
+
+extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_field *psi_e,
+                              const tm_field *psi_o, const tm_field *g_e, const tm_field *g_o, double coef,
+                              int project, void *stream)
+{
+    if (!g || !F_canon || !psi_e || !psi_o || !g_e || !g_o) { set_error("tm_force: null argument"); return TM_ERR_ARG; }
+    const tm_field *fs[4] = {psi_e, psi_o, g_e, g_o};
+    for (auto f : fs) {
+        if (!f->data || f->prec != psi_e->prec || f->nrhs != 1 || (f->prec == TM_PREC_F16 && !f->norm)) {
+            set_error("tm_force: fields must be single-RHS and share one precision");
+            return TM_ERR_ARG;
+        }
+    }
+    if (psi_e->prec == TM_PREC_F16) { set_error("tm_force: FP64 or FP32 fields only"); return TM_ERR_ARG; }
+    if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("tm_force: unknown canon_type"); return TM_ERR_ARG; }
+    ForceArgs a;
+    a.psi[0] = psi_e->data;
+    a.psi[1] = psi_o->data;
+    a.gv[0] = g_e->data;
+    a.gv[1] = g_o->data;
+    a.psi_norm[0] = a.psi_norm[1] = a.gv_norm[0] = a.gv_norm[1] = nullptr;
+    a.Vh = g->Vh;
+    a.X1h = g->X1h;
+    a.Lx = g->p.L[0];
+    a.Ly = g->p.L[1];
+    a.Lz = g->p.L[2];
+    a.Lt = g->p.L[3];
+    a.nf = g->nf;
+    a.tbc = g->p.t_antiperiodic ? 1 : 0;
+    a.project = project ? 1 : 0;
+    a.coef = -g->p.kappa * coef;
+    const int pidx = prec_index(psi_e->prec);
+    a.gauge = g->links[pidx];
+    a.out = F_canon;
+    const long n = 8L * g->Vh;
+    const int block = 128;
+    const long grid = (n + block - 1) / block;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int recon = g->p.recon;
+#define TM_F(P, R, CT) k_force<P, R, CT><<<grid, block, 0, s>>>(a)
+#define TM_FR(P, CT)                         \
+    if (recon == 18) TM_F(P, 18, CT);         \
+    else if (recon == 12) TM_F(P, 12, CT);    \
+    else TM_F(P, 8, CT);
+    if (pidx == 0) {
+        if (canon_type == TM_C128) { TM_FR(P64, double2) } else { TM_FR(P64, float2) }
+    } else {
+        if (canon_type == TM_C128) { TM_FR(P32, double2) } else { TM_FR(P32, float2) }
+    }
+#undef TM_FR
+#undef TM_F
+    return cuda_check(cudaGetLastError(), "tm_force launch");
+}

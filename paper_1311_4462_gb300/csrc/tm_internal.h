@@ -32,6 +32,7 @@ struct tm_gauge {
     void *links[3];     // packed links, index 0: FP64, 1: FP32, 2: FP16
     size_t link_bytes[3];
     double *scratch;    // reduction partials + device scalars (library-owned)
+    double *host_scalars;  // pinned mirror for scalar readback
     size_t scratch_bytes;
 };
 

@@ -1,0 +1,367 @@
+// tm_solver.cu -- CG on the normal equations of the even-even operator (sec. 2.2:
+// DIRECT_PC solve with NORMOP CG), in FP64, and the mixed-precision reliable-update CG
+// (the double-single / double-half solver of sec. 3): the sloppy iteration runs the fused
+// operator and BLAS in FP32 or FP16 storage; the solution accumulation, the true residual
+// and the stopping test run in FP64.
+//
+// Scalars (alpha, beta, |r|^2) live in the handle's device scalar table and are produced by
+// the reductions' last block, so an iteration enqueues without host round trips; the host
+// reads |r|^2 once per iteration to decide convergence and reliable updates.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "tm_blas.cuh"
+#include "tm_internal.h"
+
+namespace tmk {
+
+__global__ void k_scalar_beta(double *S, int nrhs, const int *active)
+{
+    const int c = threadIdx.x;
+    if (c >= nrhs) return;
+    if (active && !active[c]) return;
+    const double rr = S[SL_RR * TM_MAX_RHS + c], rn = S[SL_RRNEW * TM_MAX_RHS + c];
+    S[SL_BETA * TM_MAX_RHS + c] = rr != 0.0 ? rn / rr : 0.0;
+    S[SL_RR * TM_MAX_RHS + c] = rn;
+}
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+struct Carve {
+    char *base;
+    size_t off, cap;
+    bool ok = true;
+    tm_field take(const tm_gauge *g, int prec)
+    {
+        tm_field f;
+        memset(&f, 0, sizeof(f));
+        size_t d, n;
+        tm_field_bytes(g, prec, 1, &d, &n);
+        f.prec = prec;
+        f.nrhs = 1;
+        f.data = base ? base + off : nullptr;
+        off += align256(d);
+        if (n) {
+            f.norm = base ? reinterpret_cast<float *>(base + off) : nullptr;
+            off += align256(n);
+        }
+        if (off > cap) ok = false;
+        return f;
+    }
+};
+
+static size_t workspace_need(const tm_gauge *g, const tm_solver_params *sp)
+{
+    Carve c{nullptr, 0, (size_t)-1};
+    for (int i = 0; i < 6; i++) c.take(g, TM_PREC_F64);
+    if (sp->solver == TM_SOLVER_MIXED_CG) {
+        for (int i = 0; i < 5; i++) c.take(g, sp->sloppy_prec);
+        c.take(g, TM_PREC_F32);
+    }
+    return c.off;
+}
+
+class Solver {
+  public:
+    const tm_gauge *g;
+    const tm_solver_params *sp;
+    cudaStream_t s;
+    double *S;  // device scalar table
+    double *H;  // pinned host mirror
+
+    tm_status site(int op, FieldRef A, FieldRef B, FieldRef C, FieldRef D, SVal ca, SVal cb, int reduce, int fin,
+                   int slot)
+    {
+        SiteOpArgs a;
+        memset(&a, 0, sizeof(a));
+        a.op = op;
+        a.reduce = reduce;
+        a.A = A;
+        a.B = B;
+        a.C = C;
+        a.D = D;
+        a.ca = ca;
+        a.cb = cb;
+        a.red.scalars = S;
+        a.red.fin = fin;
+        a.red.slot = slot;
+        return cuda_check(launch_site_op(g, a, 1, s), "site op");
+    }
+    tm_status norm2(const tm_field *x, int slot)
+    {
+        return site(OP_NORM, fref(x), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, slot);
+    }
+    tm_status copy(const tm_field *dst, const tm_field *src)
+    {
+        return site(OP_COPY, fref(src), fnone(), fref(dst), fnone(), sv(1), sv(0), 0, 0, 0);
+    }
+    // C = ca A + cb B
+    tm_status axpby(const tm_field *C, SVal ca, const tm_field *A, SVal cb, const tm_field *B, int reduce = 0,
+                    int fin = FIN_STORE, int slot = SL_TMP0)
+    {
+        return site(OP_AXPBY, fref(A), B ? fref(B) : fnone(), fref(C), fnone(), ca, cb, reduce, fin, slot);
+    }
+    tm_status read(int slot, double *v)
+    {
+        tm_status st = cuda_check(cudaMemcpyAsync(H, S + slot * TM_MAX_RHS, sizeof(double), cudaMemcpyDeviceToHost, s),
+                                  "scalar readback");
+        if (st != TM_OK) return st;
+        st = cuda_check(cudaStreamSynchronize(s), "solver sync");
+        *v = H[0];
+        return st;
+    }
+    tm_status zero(const tm_field *f)
+    {
+        size_t d, n;
+        tm_field_bytes(g, f->prec, 1, &d, &n);
+        tm_status st = cuda_check(cudaMemsetAsync(f->data, 0, d, s), "memset");
+        if (st == TM_OK && n) st = cuda_check(cudaMemsetAsync(f->norm, 0, n, s), "memset");
+        return st;
+    }
+    // out = A^dag A in with A = M_pc (or M_pc^dag when dagger)
+    tm_status normal_op(const tm_field *out, const tm_field *in, const tm_field *te, const tm_field *to)
+    {
+        tm_status st = tm_precond_op(g, te, in, to, sp->pc, sp->dagger, s);
+        if (st != TM_OK) return st;
+        return tm_precond_op(g, out, te, to, sp->pc, !sp->dagger, s);
+    }
+};
+
+static tm_status check_solver_params(const tm_gauge *g, const tm_solver_params *sp)
+{
+    if (!g || !sp) { set_error("tm_solve: null handle or params"); return TM_ERR_ARG; }
+    if (sp->solver != TM_SOLVER_CG && sp->solver != TM_SOLVER_MIXED_CG) { set_error("unknown solver"); return TM_ERR_ARG; }
+    if (sp->solution != TM_SOLUTION_MAT && sp->solution != TM_SOLUTION_MATDAG_MAT) {
+        set_error("unknown solution type");
+        return TM_ERR_ARG;
+    }
+    if (sp->pc != TM_PC_ASYM && sp->pc != TM_PC_SYM) { set_error("unknown pc"); return TM_ERR_ARG; }
+    if (!(sp->tol > 0.0) || sp->maxiter < 1) { set_error("tol must be > 0 and maxiter >= 1"); return TM_ERR_ARG; }
+    if (sp->solver == TM_SOLVER_MIXED_CG) {
+        if (sp->sloppy_prec != TM_PREC_F32 && sp->sloppy_prec != TM_PREC_F16) {
+            set_error("sloppy_prec must be TM_PREC_F32 or TM_PREC_F16");
+            return TM_ERR_ARG;
+        }
+        if (!(sp->delta > 0.0 && sp->delta < 1.0)) { set_error("delta must be in (0, 1)"); return TM_ERR_ARG; }
+    }
+    return TM_OK;
+}
+
+#define TRY(x)                      \
+    do {                            \
+        st = (x);                   \
+        if (st != TM_OK) goto done; \
+    } while (0)
+
+static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, const tm_solver_params *sp,
+                       tm_solver_stats *stats, void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    tm_status st = TM_OK;
+    Solver sv_;
+    sv_.g = g;
+    sv_.sp = sp;
+    sv_.s = s;
+    sv_.S = g->scratch;
+    sv_.H = g->host_scalars;
+    Solver &V = sv_;
+    Carve c{reinterpret_cast<char *>(ws), 0, ws_bytes};
+    tm_field r = c.take(g, TM_PREC_F64), p = c.take(g, TM_PREC_F64), Ap = c.take(g, TM_PREC_F64);
+    tm_field te = c.take(g, TM_PREC_F64), to = c.take(g, TM_PREC_F64), bh = c.take(g, TM_PREC_F64);
+    const bool mixed = sp->solver == TM_SOLVER_MIXED_CG;
+    tm_field rs{}, ps{}, Aps{}, tes{}, tos{}, xs{};
+    if (mixed) {
+        rs = c.take(g, sp->sloppy_prec);
+        ps = c.take(g, sp->sloppy_prec);
+        Aps = c.take(g, sp->sloppy_prec);
+        tes = c.take(g, sp->sloppy_prec);
+        tos = c.take(g, sp->sloppy_prec);
+        xs = c.take(g, TM_PREC_F32);
+    }
+    if (!c.ok) {
+        set_error("tm_solve: workspace of %zu bytes is smaller than the %zu needed", ws_bytes, c.off);
+        return TM_ERR_NOMEM;
+    }
+    double bb = 0, rr = 0, r2 = 0;
+    int it = 0, nrel = 0;
+    const double tol2 = sp->tol * sp->tol;
+    const tm_field *bhat = b;
+    // right-hand side of the normal equations
+    if (sp->solution == TM_SOLUTION_MAT) {
+        TRY(tm_precond_op(g, &bh, b, &to, sp->pc, !sp->dagger, s));  // bhat = A^dag b
+        bhat = &bh;
+    }
+    TRY(V.norm2(bhat, SL_TMP0));
+    TRY(V.read(SL_TMP0, &bb));
+    if (!isfinite(bb)) { set_error("tm_solve: non-finite source"); st = TM_ERR_NAN; goto done; }
+    if (bb == 0.0) {
+        TRY(V.zero(x));
+        goto done;
+    }
+    // r = bhat - A^dag A x
+    if (sp->use_x0) {
+        TRY(V.normal_op(&Ap, x, &te, &to));
+        TRY(V.axpby(&r, sv(1.0), bhat, sv(-1.0), &Ap, 1, FIN_STORE, SL_RR));
+    } else {
+        TRY(V.zero(x));
+        TRY(V.copy(&r, bhat));
+        TRY(V.norm2(&r, SL_RR));
+    }
+    TRY(V.read(SL_RR, &r2));
+
+    if (!mixed) {
+        // CG on the recursively updated residual; when it reaches tol the true residual is
+        // recomputed, and CG restarts from it (at most 4 times) if rounding left it above tol.
+        for (int restart = 0; restart < 5 && r2 > tol2 * bb && it < sp->maxiter; restart++) {
+            if (restart > 0) nrel++;
+            TRY(V.copy(&p, &r));
+            rr = r2;
+            while (rr > tol2 * bb && it < sp->maxiter) {
+                TRY(V.normal_op(&Ap, &p, &te, &to));
+                TRY(V.site(OP_DOT, fref(&p), fref(&Ap), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0));
+                TRY(V.site(OP_CG_UPDATE, fref(&p), fref(&r), fref(x), fref(&Ap), sslot(SL_ALPHA, 1.0), sv(0), 1,
+                           FIN_BETA, 0));
+                TRY(V.read(SL_RRNEW, &rr));
+                it++;
+                if (!isfinite(rr)) {
+                    set_error("tm_solve: non-finite residual at iteration %d", it);
+                    st = TM_ERR_NAN;
+                    goto done;
+                }
+                if (rr <= tol2 * bb) break;
+                TRY(V.axpby(&p, sv(1.0), &r, sslot(SL_BETA, 1.0), &p));  // p = r + beta p
+            }
+            // true residual r = bhat - A^dag A x, FP64; SL_RR = |r|^2 for the next restart
+            TRY(V.normal_op(&Ap, x, &te, &to));
+            TRY(V.axpby(&r, sv(1.0), bhat, sv(-1.0), &Ap, 1, FIN_STORE, SL_RR));
+            TRY(V.read(SL_RR, &r2));
+        }
+    } else {
+        // sloppy copies: rs = r, p = rs, xs = 0; SL_RR = |rs|^2
+        TRY(V.copy(&rs, &r));
+        TRY(V.copy(&ps, &rs));
+        TRY(V.zero(&xs));
+        TRY(V.norm2(&rs, SL_RR));
+        double maxr = sqrt(r2);
+        bool converged = r2 <= tol2 * bb;
+        while (!converged && it < sp->maxiter) {
+            TRY(V.normal_op(&Aps, &ps, &tes, &tos));
+            TRY(V.site(OP_DOT, fref(&ps), fref(&Aps), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0));
+            TRY(V.site(OP_CG_UPDATE, fref(&ps), fref(&rs), fref(&xs), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
+                       FIN_STORE, SL_RRNEW));
+            TRY(V.read(SL_RRNEW, &rr));
+            it++;
+            if (!isfinite(rr)) { set_error("tm_solve: non-finite residual at iteration %d", it); st = TM_ERR_NAN; goto done; }
+            const double rn = sqrt(rr);
+            if (rn > maxr) maxr = rn;
+            if (rn < sp->delta * maxr || rr <= tol2 * bb || it == sp->maxiter) {
+                // reliable update: fold the sloppy solution into x, recompute the true residual in FP64
+                TRY(V.axpby(x, sv(1.0), &xs, sv(1.0), x));
+                TRY(V.zero(&xs));
+                TRY(V.normal_op(&Ap, x, &te, &to));
+                TRY(V.axpby(&r, sv(1.0), bhat, sv(-1.0), &Ap, 1, FIN_STORE, SL_TMP0));
+                TRY(V.read(SL_TMP0, &r2));
+                nrel++;
+                if (!isfinite(r2)) { set_error("tm_solve: non-finite true residual"); st = TM_ERR_NAN; goto done; }
+                if (r2 <= tol2 * bb) { converged = true; break; }
+                TRY(V.copy(&rs, &r));
+                TRY(V.norm2(&rs, SL_RRNEW));
+                maxr = sqrt(r2);
+            }
+            k_scalar_beta<<<1, 32, 0, s>>>(V.S, 1, nullptr);
+            TRY(cuda_check(cudaGetLastError(), "beta"));
+            TRY(V.axpby(&ps, sv(1.0), &rs, sslot(SL_BETA, 1.0), &ps));  // p = rs + beta p
+        }
+    }
+    // final true residual of the normal equations, in FP64
+    TRY(V.normal_op(&Ap, x, &te, &to));
+    TRY(V.axpby(&r, sv(1.0), bhat, sv(-1.0), &Ap, 1, FIN_STORE, SL_TMP0));
+    TRY(V.read(SL_TMP0, &r2));
+    if (stats) {
+        stats->true_residual = sqrt(r2 / bb);
+        stats->pc_residual = -1.0;
+    }
+    if (stats && sp->solution == TM_SOLUTION_MAT) {
+        double b2, e2;
+        TRY(tm_precond_op(g, &te, x, &to, sp->pc, sp->dagger, s));  // M_pc x
+        TRY(V.axpby(&te, sv(1.0), b, sv(-1.0), &te, 1, FIN_STORE, SL_TMP0));
+        TRY(V.read(SL_TMP0, &e2));
+        TRY(V.norm2(b, SL_TMP1));
+        TRY(V.read(SL_TMP1, &b2));
+        stats->pc_residual = sqrt(e2 / b2);
+    }
+    if (r2 > tol2 * bb) {
+        set_error("tm_solve: no convergence after %d iterations (true residual %.3e)", it, sqrt(r2 / bb));
+        st = TM_ERR_NOCONV;
+    }
+done:
+    if (stats) {
+        stats->iterations = it;
+        stats->reliable_updates = nrel;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return st;
+}
+
+}  // namespace tmk
+
+using namespace tmk;
+
+extern "C" {
+
+tm_status tm_solve_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp, size_t *bytes)
+{
+    tm_status st = check_solver_params(g, sp);
+    if (st != TM_OK) return st;
+    if (!bytes) { set_error("null output"); return TM_ERR_ARG; }
+    *bytes = workspace_need(g, sp);
+    return TM_OK;
+}
+
+tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
+                   tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream)
+{
+    tm_status st = check_solver_params(g, sp);
+    if (st != TM_OK) return st;
+    if (!x_e || !b_e || !workspace) { set_error("tm_solve: null field or workspace"); return TM_ERR_ARG; }
+    if (x_e->prec != TM_PREC_F64 || b_e->prec != TM_PREC_F64 || x_e->nrhs != 1 || b_e->nrhs != 1) {
+        set_error("tm_solve: x and b must be single-RHS FP64 fields");
+        return TM_ERR_ARG;
+    }
+    if (x_e->data == b_e->data) { set_error("tm_solve: x must not alias b"); return TM_ERR_ARG; }
+    if (((uintptr_t)workspace & 255) != 0) { set_error("tm_solve: workspace must be 256-byte aligned"); return TM_ERR_ARG; }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return solve(g, x_e, b_e, sp, stats, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stream)
+{
+    if (!g || !x || !x->data || !out) { set_error("tm_norm2: null argument"); return TM_ERR_ARG; }
+    Solver V;
+    V.g = g;
+    V.sp = nullptr;
+    V.s = (cudaStream_t)stream;
+    V.S = g->scratch;
+    V.H = g->host_scalars;
+    tm_status st = V.site(OP_NORM, fref(x), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP2);
+    if (st != TM_OK) return st;
+    return V.read(SL_TMP2, out);
+}
+
+tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, void *stream)
+{
+    if (!g || !a || !b || !a->data || !b->data || !re_out) { set_error("tm_dot: null argument"); return TM_ERR_ARG; }
+    Solver V;
+    V.g = g;
+    V.sp = nullptr;
+    V.s = (cudaStream_t)stream;
+    V.S = g->scratch;
+    V.H = g->host_scalars;
+    tm_status st = V.site(OP_DOT, fref(a), fref(b), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP2);
+    if (st != TM_OK) return st;
+    return V.read(SL_TMP2, re_out);
+}
+
+}  // extern "C"
