@@ -245,6 +245,24 @@ tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double
 tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_field *psi_e, const tm_field *psi_o,
                    const tm_field *g_e, const tm_field *g_o, double coef, int project, void *stream);
 
+/* --------------------------------------------------------------------- allocation-free variant */
+/*
+ * |x|^2 of each right-hand side of a parity field (the tm_norm2 reduction), for callers that
+ * cannot allocate device memory: it needs no tm_gauge handle (creating one allocates) and calls
+ * no allocating routine.  The paper has no counterpart; this is a library-usage addition.
+ *   x:          field to reduce (any precision); Vh sites per parity, nf flavours (1 or 2),
+ *               x->nrhs right-hand sides, at most 64.
+ *   result_dev: device pointer to x->nrhs doubles, written with |x_rhs|^2 (FP64 accumulation).
+ * The reduction's scratch (256 x 64 partial sums and a completion ticket, about 128 KB) is one
+ * static device array per loaded copy of the library, kept on every GPU that uses it until the
+ * process exits.  The first call on a device (with that device current) looks up the array's
+ * device address and caches it; make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (different streams, or different host threads
+ * without ordering) race and give wrong results; calls ordered on one stream are safe.
+ * Errors: TM_ERR_ARG (null pointers, nrhs > 64, nf not 1 or 2, bad Vh), TM_ERR_CUDA.
+ */
+tm_status tm_norm2_noalloc(const tm_field *x, int Vh, int nf, double *result_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ _SIGS = {
     "tm_norm2": [vp, FP, ctypes.POINTER(ctypes.c_double), vp],
     "tm_dot": [vp, FP, FP, ctypes.POINTER(ctypes.c_double), vp],
     "tm_force": [vp, vp, ctypes.c_int, FP, FP, FP, FP, ctypes.c_double, ctypes.c_int, vp],
+    "tm_norm2_noalloc": [FP, ctypes.c_int, ctypes.c_int, vp, vp],
 }
 
 

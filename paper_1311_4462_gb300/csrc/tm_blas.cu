@@ -265,3 +265,24 @@ cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream
 }
 
 }  // namespace tmk
+
+namespace tmk {
+
+// Launch of k_site_op with caller-supplied reduction scratch and geometry (no gauge handle):
+// grid.x blocks per rhs column, 256 threads, partials/counter taken from a.red as given.
+cudaError_t launch_site_op_explicit(SiteOpArgs a, int Vh, int nf, int grid_x, int nrhs, cudaStream_t s)
+{
+    a.Vh = Vh;
+    a.nf = nf;
+    const int block = 256;
+    dim3 grid((unsigned)grid_x, (unsigned)nrhs);
+    const int pa = a.A.prec;
+    const int pb = pc_of(a.B, pa), pc = pc_of(a.C, pa), pd = pc_of(a.D, pa);
+#define TM_TRY_COMBO(A_, B_, C_, D_) \
+    if (pa == A_ && pb == B_ && pc == C_ && pd == D_) return run_combo<A_, B_, C_, D_>(a, grid, block, s);
+    TM_COMBOS(TM_TRY_COMBO)
+#undef TM_TRY_COMBO
+    return cudaErrorNotSupported;
+}
+
+}  // namespace tmk
