@@ -203,13 +203,14 @@ typedef struct {
     double delta;    /* mixed: reliable update when |r_sloppy| < delta * max |r| since the last one */
     int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
     int use_x0;      /* 1: x_e holds the initial guess on entry; 0: start from zero */
+    int want_pc_residual; /* 1: also compute stats->pc_residual (one more FP64 operator application) */
 } tm_solver_params;
 
 typedef struct {
     int iterations;
     int reliable_updates; /* mixed: reliable updates; FP64 CG: restarts from the true residual */
     double true_residual; /* |bhat - A^dag A x| / |bhat|, recomputed in FP64 at exit */
-    double pc_residual;   /* |A x - b| / |b| for MAT solutions (-1 for MATDAG_MAT) */
+    double pc_residual;   /* |A x - b| / |b| for MAT solutions when want_pc_residual, else -1 */
     double seconds;       /* host wall time of the call */
 } tm_solver_stats;
 
@@ -244,6 +245,19 @@ tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double
  */
 tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_field *psi_e, const tm_field *psi_o,
                    const tm_field *g_e, const tm_field *g_o, double coef, int project, void *stream);
+
+/* ---------------------------------------------------------------------------- autotuning */
+/*
+ * Time every launch choice of the hopping kernel (thread-per-site or, for the doublet,
+ * thread-per-site-and-flavour; 64-256 threads per block) for each precision, with and without
+ * the input-twist prologue, on this handle's lattice, and keep the fastest.  Allocates three
+ * scratch fields for the duration of the call and synchronises `stream`; do not call it while
+ * capturing a graph.  Until it runs (or a table is imported) the handle uses defaults.
+ */
+tm_status tm_autotune(tm_gauge *g, void *stream);
+/* The tuned table as text ("f32:0:1:128 ..." = precision:prologue:variant:block), and back. */
+tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n);
+tm_status tm_tune_import(tm_gauge *g, const char *text);
 
 /* --------------------------------------------------------------------- allocation-free variant */
 /*

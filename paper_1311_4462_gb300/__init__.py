@@ -206,13 +206,19 @@ def dot(gauge, a: Field, b: Field, stream=None) -> float:
     return out.value
 
 
+# reliable-update thresholds: the sloppy residual may fall by this factor between FP64 updates
+# (FP16 storage keeps about 3 digits, FP32 about 7; chosen from a sweep on the 32^3x64 doublet)
+DEFAULT_DELTA = {TM_PREC_F16: 1e-2, TM_PREC_F32: 1e-3}
+
+
 def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000,
-                  delta=0.1, sloppy_prec=TM_PREC_F32, use_x0=False):
+                  delta=None, sloppy_prec=TM_PREC_F32, use_x0=False, want_pc_residual=False):
     sp = L.tm_solver_params()
     sp.solver = TM_SOLVER_MIXED if solver == "mixed" else TM_SOLVER_CG
     sp.solution, sp.pc, sp.dagger = int(solution), int(pc), int(dagger)
-    sp.tol, sp.maxiter, sp.delta = float(tol), int(maxiter), float(delta)
-    sp.sloppy_prec, sp.use_x0 = int(sloppy_prec), int(use_x0)
+    sp.tol, sp.maxiter = float(tol), int(maxiter)
+    sp.delta = float(delta if delta is not None else DEFAULT_DELTA.get(int(sloppy_prec), 0.1))
+    sp.sloppy_prec, sp.use_x0, sp.want_pc_residual = int(sloppy_prec), int(use_x0), int(want_pc_residual)
     return sp
 
 
@@ -250,6 +256,37 @@ def force(gauge, psi_e: Field, psi_o: Field, g_e: Field, g_o: Field, coef=1.0, p
     L.check(L.load().tm_force(gauge.h, ctypes.c_void_p(out.data_ptr()), ct, psi_e.ref(), psi_o.ref(), g_e.ref(),
                               g_o.ref(), float(coef), int(project), _stream(stream)))
     return out
+
+
+def autotune(gauge, cache_path=None, stream=None):
+    """tm_autotune, with an optional JSON cache keyed by lattice, flavours and recon."""
+    import json
+    import os
+    key = "L%s_nf%d_recon%d" % ("x".join(map(str, gauge.params.L)), gauge.params.nf, gauge.params.recon)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        tune_import(gauge, cache[key])
+        return cache[key]
+    L.check(L.load().tm_autotune(gauge.h, _stream(stream)))
+    table = tune_export(gauge)
+    if cache_path:
+        cache[key] = table
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return table
+
+
+def tune_export(gauge) -> str:
+    buf = ctypes.create_string_buffer(512)
+    L.check(L.load().tm_tune_export(gauge.h, buf, 512))
+    return buf.value.decode()
+
+
+def tune_import(gauge, text: str):
+    L.check(L.load().tm_tune_import(gauge.h, text.encode()))
 
 
 def version() -> str:

@@ -10,9 +10,12 @@
 
 namespace tmk {
 
-cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
-cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
-cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, int block, cudaStream_t s);
+cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, int variant, int block,
+                              cudaStream_t s);
+cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, int variant, int block,
+                              cudaStream_t s);
+cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, int variant, int block,
+                              cudaStream_t s);
 cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void *canon, int ctype, int parity,
                                cudaStream_t s);
 cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, const tm_field *f, int parity,
@@ -186,7 +189,7 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
     Twist<double> z;
     memset(&z, 0, sizeof(z));
     const Twist<double> &te = tw_epi ? *tw_epi : z, &tp = tw_pro ? *tw_pro : z;
-    const int block = 128;
+    const tm_tune_entry tu = g->tune[pidx][pro ? 1 : 0];
     cudaError_t e;
     if (pidx == 0) {
         DslashArgs<double> a;
@@ -196,7 +199,7 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
         a.coef = coef;
         a.tw_epi = te;
         a.tw_pro = tp;
-        e = launch_dslash_p64(a, g->nf, g->p.recon, pro, block, s);
+        e = launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     } else {
         DslashArgs<float> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -205,8 +208,8 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
         a.coef = (float)coef;
         a.tw_epi = to_float(te);
         a.tw_pro = to_float(tp);
-        e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, block, s)
-                        : launch_dslash_p16(a, g->nf, g->p.recon, pro, block, s);
+        e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s)
+                        : launch_dslash_p16(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     }
     return cuda_check(e, "dslash launch");
 }
@@ -281,6 +284,8 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     const long V = (long)p->L[0] * p->L[1] * p->L[2] * p->L[3];
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(g->nf == 2 && j == 0) ? 1 : 0, 128};
     cudaStream_t s = (cudaStream_t)stream;
     tm_status st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
     if (st == TM_OK) st = cuda_check(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
@@ -464,6 +469,110 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
     if (psi_o->data == psi_e->data) { set_error("tm_reconstruct_odd: psi_o must not alias psi_e"); return TM_ERR_ARG; }
     const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
     return dslash_launch(g, psi_o, psi_e, b_o, 1, dagger, EPI_TW_XPAY, g->p.kappa, &Ri, nullptr, (cudaStream_t)stream);
+}
+
+tm_status tm_autotune(tm_gauge *g, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int precs[3] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16};
+    const int blocks[4] = {64, 128, 192, 256};
+    tm_status st = TM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void *buf = nullptr;
+    size_t d, n;
+    tm_field_bytes(g, TM_PREC_F64, 1, &d, &n);
+    const size_t fb = (d + 255) & ~(size_t)255;
+    if (cudaMalloc(&buf, 3 * fb) != cudaSuccess) { set_error("tm_autotune: allocation failed"); return TM_ERR_NOMEM; }
+    st = cuda_check(cudaMemsetAsync(buf, 0, 3 * fb, s), "tm_autotune memset");
+    if (st == TM_OK) st = cuda_check(cudaEventCreate(&e0), "event");
+    if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
+    for (int pi = 0; pi < 3 && st == TM_OK; pi++) {
+        // one FP64-sized buffer per field holds any precision; FP16 norms sit in the tail
+        tm_field_bytes(g, precs[pi], 1, &d, &n);
+        tm_field f[3];
+        for (int k = 0; k < 3; k++) {
+            f[k].data = (char *)buf + k * fb;
+            f[k].norm = n ? (float *)((char *)buf + k * fb + ((d + 255) & ~(size_t)255)) : nullptr;
+            f[k].prec = precs[pi];
+            f[k].nrhs = 1;
+        }
+        const Twist<double> Ri = make_twist(g, TW_RINV, 0);
+        for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
+            float best = 1e30f;
+            tm_tune_entry bestc = g->tune[pi][pro];
+            for (int variant = 0; variant < ((g->nf == 2 && !pro) ? 2 : 1); variant++) {
+                for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
+                    g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
+                    float ms = 0;
+                    for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
+                        st = cuda_check(cudaEventRecord(e0, s), "event");
+                        if (st == TM_OK)
+                            st = dslash_launch(g, &f[0], &f[1], &f[2], 0, 0, EPI_TWX_AXPY, -0.01, &Ri, pro ? &Ri : nullptr, s);
+                        if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+                        if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+                        float t = 0;
+                        if (st == TM_OK) cudaEventElapsedTime(&t, e0, e1);
+                        if (rep > 0) ms += t;  // first repetition warms up
+                    }
+                    if (st == TM_OK && ms < best) {
+                        best = ms;
+                        bestc = g->tune[pi][pro];
+                    }
+                }
+            }
+            g->tune[pi][pro] = bestc;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    return st;
+}
+
+tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n)
+{
+    if (!g || !buf || n == 0) { set_error("tm_tune_export: null argument"); return TM_ERR_ARG; }
+    const char *names[3] = {"f64", "f32", "f16"};
+    size_t off = 0;
+    buf[0] = 0;
+    for (int pi = 0; pi < 3; pi++)
+        for (int pro = 0; pro < 2; pro++) {
+            int w = snprintf(buf + off, n - off, "%s%s:%d:%d:%d", off ? " " : "", names[pi], pro,
+                             g->tune[pi][pro].variant, g->tune[pi][pro].block);
+            if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
+            off += (size_t)w;
+        }
+    return TM_OK;
+}
+
+tm_status tm_tune_import(tm_gauge *g, const char *text)
+{
+    if (!g || !text) { set_error("tm_tune_import: null argument"); return TM_ERR_ARG; }
+    tm_tune_entry t[3][2];
+    memcpy(t, g->tune, sizeof(t));
+    const char *p = text;
+    while (*p) {
+        while (*p == ' ') p++;
+        if (!*p) break;
+        char name[8] = {0};
+        int pro, variant, block, used = 0;
+        if (sscanf(p, "%3[a-z0-9]:%d:%d:%d%n", name, &pro, &variant, &block, &used) != 4 || used == 0) {
+            set_error("tm_tune_import: cannot parse '%.32s'", p);
+            return TM_ERR_ARG;
+        }
+        const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
+        if (pi < 0 || (pro != 0 && pro != 1) || (variant != 0 && variant != 1) || block < 32 || block > 256 ||
+            block % 32) {
+            set_error("tm_tune_import: invalid entry '%.32s'", p);
+            return TM_ERR_ARG;
+        }
+        t[pi][pro] = tm_tune_entry{variant, block};
+        p += used;
+    }
+    memcpy(g->tune, t, sizeof(t));
+    return TM_OK;
 }
 
 tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger, void *stream)

@@ -137,6 +137,25 @@ __device__ __forceinline__ void load_spinor<P16>(const void *base, const float *
     }
 }
 
+// FP16 only: the stored halves of a site without the norm factor, and the norm itself, so a
+// linear consumer can apply the norm once to its result instead of to all 24 inputs.
+__device__ __forceinline__ float load_spinor_f16_unscaled(const void *base, const float *norm, int cb, int Vh,
+                                                          float v[24])
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + cb;
+    const float n = __ldg(norm + cb);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        uint4 c = ldg(p + (size_t)k * Vh);
+        float2 a = h2f(c.x), b = h2f(c.y), d = h2f(c.z), e = h2f(c.w);
+        v[8 * k + 0] = a.x; v[8 * k + 1] = a.y;
+        v[8 * k + 2] = b.x; v[8 * k + 3] = b.y;
+        v[8 * k + 4] = d.x; v[8 * k + 5] = d.y;
+        v[8 * k + 6] = e.x; v[8 * k + 7] = e.y;
+    }
+    return n;
+}
+
 template <int PREC>
 __device__ __forceinline__ void store_spinor(void *base, float *norm, int cb, int Vh,
                                              const typename Traits<PREC>::real v[24]);

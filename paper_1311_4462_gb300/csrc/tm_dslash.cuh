@@ -142,8 +142,43 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
 #pragma unroll
         for (int f = 0; f < NF; f++) {
             T v[24];
-            load_spinor<PREC>(in + f * fstride, a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr, nb, a.Vh, v);
-            hop_one<MU, FWD>(acc[f], U, v, sp, sg);
+            if constexpr (PREC == P16) {
+                // the hop is linear in the input: fold the site norm into the accumulation sign
+                const T n = load_spinor_f16_unscaled(in + f * fstride, a.in_norm + (size_t)f * a.Vh, nb, a.Vh, v);
+                hop_one<MU, FWD>(acc[f], U, v, sp, sg * n);
+            } else {
+                load_spinor<PREC>(in + f * fstride, nullptr, nb, a.Vh, v);
+                hop_one<MU, FWD>(acc[f], U, v, sp, sg);
+            }
+        }
+    }
+}
+
+// One flavour of the doublet per thread (flavour = lane & 1): the 8 hops use this flavour's
+// spinor only; the link loads of the two lanes of a pair hit the same addresses and are served
+// by one request.  Flavour mixing in the epilogue takes the partner lane's values by shuffle.
+template <typename T>
+__device__ __forceinline__ void partner(const T v[24], T p[24])
+{
+#pragma unroll
+    for (int k = 0; k < 24; k++) p[k] = __shfl_xor_sync(0xffffffffu, v[k], 1);
+}
+
+// out_f = m[g][f][f] own + m[g][f][1-f] other, per spin block g
+template <typename T>
+__device__ __forceinline__ void twist_split(const Twist<T> &tw, int f, T own[24], const T other[24])
+{
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const int gi = s >> 1;
+        const C<T> d = tw.m[gi][f][f], o = tw.m[gi][f][1 - f];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int k = 2 * (3 * s + c);
+            const C<T> a = {own[k], own[k + 1]}, b = {other[k], other[k + 1]};
+            const C<T> r = cadd(cmul(d, a), cmul(o, b));
+            own[k] = r.r;
+            own[k + 1] = r.i;
         }
     }
 }
@@ -264,10 +299,135 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
-template <int PREC>
-cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro, int block,
-                               cudaStream_t s)
+template <int PREC, int RECON>
+__global__ void __launch_bounds__(256) k_dslash_fsplit(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
+    using T = typename Traits<PREC>::real;
+    using LL = LinkLayout<PREC, RECON>;
+    using LC = typename LL::chunk;
+    using SC = typename Traits<PREC>::schunk;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = (int)(tid & 1);
+    const bool live = (tid >> 1) < a.Vh;
+    // lanes past the end compute the last site again (shuffles need the whole warp) and do not store
+    const int cb = live ? (int)(tid >> 1) : a.Vh - 1;
+
+    int r = cb;
+    const int xh = r % a.X1h;
+    r /= a.X1h;
+    const int y = r % a.Ly;
+    r /= a.Ly;
+    const int z = r % a.Lz;
+    const int t = r / a.Lz;
+    const int op = a.out_parity;
+    const int x = 2 * xh + ((op + y + z + t) & 1);
+    const int row = cb - xh;
+    const size_t gpar = (size_t)LL::N * a.Vh;
+    const LC *G = reinterpret_cast<const LC *>(a.gauge);
+    const LC *Gout = G + (size_t)op * gpar;
+    const LC *Gin = G + (size_t)(1 - op) * gpar;
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    DslashArgs<T> af = a;  // this lane's flavour block as a one-flavour field
+    af.in = reinterpret_cast<const SC *>(a.in) + f * fstride;
+    af.in_norm = a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr;
+
+    T acc[1][24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) acc[0][k] = T(0);
+    Link<T> U;
+    const T one = T(1);
+    {
+        const int nf_ = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
+        LinkLoader<PREC, RECON>::load(Gout + 0 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, 1, false, 0, true>(acc, U, af, nf_, one);
+        const int nb_ = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
+        LinkLoader<PREC, RECON>::load(Gin + 0 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, 1, false, 0, false>(acc, U, af, nb_, one);
+    }
+    {
+        const int s = a.X1h;
+        const int nf_ = (y == a.Ly - 1) ? cb - (a.Ly - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 1 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, 1, false, 1, true>(acc, U, af, nf_, one);
+        const int nb_ = (y == 0) ? cb + (a.Ly - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 1 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, 1, false, 1, false>(acc, U, af, nb_, one);
+    }
+    {
+        const int s = a.X1h * a.Ly;
+        const int nf_ = (z == a.Lz - 1) ? cb - (a.Lz - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 2 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, 1, false, 2, true>(acc, U, af, nf_, one);
+        const int nb_ = (z == 0) ? cb + (a.Lz - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 2 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, 1, false, 2, false>(acc, U, af, nb_, one);
+    }
+    {
+        const int s = a.X1h * a.Ly * a.Lz;
+        const bool wf = (t == a.Lt - 1), wb = (t == 0);
+        const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
+        LinkLoader<PREC, RECON>::load(Gout + 3 * 2 * gpar, cb, a.Vh, U);
+        hop<PREC, 1, false, 3, true>(acc, U, af, nf_, (wf && a.tbc) ? -one : one);
+        const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
+        LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
+        hop<PREC, 1, false, 3, false>(acc, U, af, nb_, (wb && a.tbc) ? -one : one);
+    }
+
+    T *v = acc[0];
+    T other[24];
+    const int epi = a.epilogue;
+    if (epi == EPI_SCALE) {
+#pragma unroll
+        for (int k = 0; k < 24; k++) v[k] *= a.coef;
+    } else if (epi == EPI_TW) {
+        partner(v, other);
+        twist_split(a.tw_epi, f, v, other);
+    } else {
+        T xv[24];
+        const SC *X = reinterpret_cast<const SC *>(a.x) + f * fstride;
+        load_spinor<PREC>(X, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv);
+        if (epi == EPI_TWX_AXPY) {
+            partner(xv, other);
+            twist_split(a.tw_epi, f, xv, other);
+#pragma unroll
+            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
+        } else if (epi == EPI_X_TWAXPY) {
+            partner(v, other);
+            twist_split(a.tw_epi, f, v, other);
+#pragma unroll
+            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
+            if (epi == EPI_TW_XPAY) {
+                partner(v, other);
+                twist_split(a.tw_epi, f, v, other);
+            }
+        }
+    }
+    if (live) {
+        SC *O = reinterpret_cast<SC *>(a.out) + f * fstride;
+        store_spinor<PREC>(O, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, v);
+    }
+}
+
+// variant 0: one thread per site (both flavours); variant 1: one thread per site and flavour
+// (doublet without prologue only).  block: threads per block (multiple of 32, <= 256).
+template <int PREC>
+cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
+                               int variant, int block, cudaStream_t s)
+{
+    if (nf == 2 && !pro && variant == 1) {
+        const long threads = 2L * a.Vh;
+        const int grid = (int)((threads + block - 1) / block);
+        switch (recon) {
+        case 18: k_dslash_fsplit<PREC, 18><<<grid, block, 0, s>>>(a); break;
+        case 12: k_dslash_fsplit<PREC, 12><<<grid, block, 0, s>>>(a); break;
+        case 8: k_dslash_fsplit<PREC, 8><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int grid = (a.Vh + block - 1) / block;
 #define TM_LAUNCH(NF, R, P) k_dslash<PREC, NF, R, P><<<grid, block, 0, s>>>(a)
 #define TM_RECON(NF, P)                  \

@@ -3,8 +3,9 @@
 #include "tm_dslash.cuh"
 
 namespace tmk {
-cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, int block, cudaStream_t s)
+cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, int variant, int block,
+                              cudaStream_t s)
 {
-    return launch_dslash_impl<P64>(a, nf, recon, pro, block, s);
+    return launch_dslash_impl<P64>(a, nf, recon, pro, variant, block, s);
 }
 }  // namespace tmk

@@ -22,6 +22,12 @@ enum TwistKind { TW_R = 0, TW_RINV = 1 };
 
 }  // namespace tmk
 
+// Launch choice of the hopping kernel for one (precision, prologue) pair.
+struct tm_tune_entry {
+    int variant;  // 0: one thread per site; 1: one thread per site and flavour (doublet)
+    int block;    // threads per block
+};
+
 // The opaque handle behind tm_gauge*.
 struct tm_gauge {
     tm_params p;
@@ -33,6 +39,7 @@ struct tm_gauge {
     size_t link_bytes[3];
     double *scratch;    // reduction partials + device scalars (library-owned)
     double *host_scalars;  // pinned mirror for scalar readback
+    tm_tune_entry tune[3][2];  // [precision index][prologue]
     size_t scratch_bytes;
 };
 

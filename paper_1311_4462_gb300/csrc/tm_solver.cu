@@ -275,15 +275,13 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
             TRY(V.axpby(&ps, sv(1.0), &rs, sslot(SL_BETA, 1.0), &ps));  // p = rs + beta p
         }
     }
-    // final true residual of the normal equations, in FP64
-    TRY(V.normal_op(&Ap, x, &te, &to));
-    TRY(V.axpby(&r, sv(1.0), bhat, sv(-1.0), &Ap, 1, FIN_STORE, SL_TMP0));
-    TRY(V.read(SL_TMP0, &r2));
+    // r2 is the FP64 true residual of the final x on every path above (the FP64 loop ends with a
+    // recomputation, the mixed loop with a reliable update), so it is not recomputed here.
     if (stats) {
         stats->true_residual = sqrt(r2 / bb);
         stats->pc_residual = -1.0;
     }
-    if (stats && sp->solution == TM_SOLUTION_MAT) {
+    if (stats && sp->want_pc_residual && sp->solution == TM_SOLUTION_MAT) {
         double b2, e2;
         TRY(tm_precond_op(g, &te, x, &to, sp->pc, sp->dagger, s));  // M_pc x
         TRY(V.axpby(&te, sv(1.0), b, sv(-1.0), &te, 1, FIN_STORE, SL_TMP0));

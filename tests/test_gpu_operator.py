@@ -50,6 +50,11 @@ def setup(case, recon):
     return _cache[key]
 
 
+def use_variant(tmq, g, variant, block=128):
+    """Force the hopping-kernel launch choice (variant 1 = thread per site and flavour, doublet only)."""
+    tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:0:{block}" for p in ("f64", "f32", "f16")))
+
+
 def fields(tmq, g, prec, psi):
     c = torch.from_numpy(psi)
     return tmq.pack(g, c, 0, prec), tmq.pack(g, c, 1, prec)
@@ -79,8 +84,12 @@ def test_pack_unpack_roundtrip(case, prec, recon):
 @pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
-def test_precond_op(case, prec, recon, pc, dagger):
+@pytest.mark.parametrize("variant", [0, 1], ids=["site", "split"])
+def test_precond_op(case, prec, recon, pc, dagger, variant):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
+    if variant and p.nf == 1:
+        pytest.skip("flavour split applies to the doublet")
+    use_variant(tmq, g, variant, block=64 if variant else 128)
     xe, _ = fields(tmq, g, prec, psi)
     out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
     tmq.precond_op(g, out, xe, tmp, pc, dagger)
@@ -94,6 +103,7 @@ def test_precond_op(case, prec, recon, pc, dagger):
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 def test_full_operator(case, prec, dagger):
     tmq, p, po, U, g, psi, chi = setup(case, 12)
+    use_variant(tmq, g, 1 if p.nf == 2 else 0, block=256)
     xe, xo = fields(tmq, g, prec, psi)
     oe, oo = tmq.Field(g, prec), tmq.Field(g, prec)
     tmq.mat(g, oe, oo, xe, xo, dagger)
@@ -106,9 +116,13 @@ def test_full_operator(case, prec, dagger):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 @pytest.mark.parametrize("out_parity", [0, 1])
-def test_dslash_epilogues(case, prec, dagger, out_parity):
+@pytest.mark.parametrize("variant", [0, 1], ids=["site", "split"])
+def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
     """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
     tmq, p, po, U, g, psi, chi = setup(case, 12)
+    if variant and p.nf == 1:
+        pytest.skip("flavour split applies to the doublet")
+    use_variant(tmq, g, variant, block=96 if variant else 128)
     ip = 1 - out_parity
     fin = fields(tmq, g, prec, psi)[ip]
     fx = fields(tmq, g, prec, chi)[out_parity]
@@ -196,3 +210,21 @@ def test_argument_errors_are_reported():
     sing = tmq.Params((4, 4, 4, 4), 0.125, 0.0, eps=4.0, flavor=2)
     with pytest.raises(tmq.TMError):
         tmq.Gauge(sing, torch.zeros(sing.gauge_shape, dtype=torch.complex128))
+
+
+def test_autotune_roundtrip_and_parity():
+    import paper_1311_4462_gb300 as tmq
+    case = CASES[1]
+    tmq_, p, po, U, g, psi, chi = setup(case, 12)
+    table = tmq.autotune(g)
+    entries = table.split()
+    assert len(entries) == 6 and all(len(e.split(":")) == 4 for e in entries)
+    tmq.tune_import(g, table)
+    assert tmq.tune_export(g) == table
+    with pytest.raises(tmq.TMError):
+        tmq.tune_import(g, "f32:0:1:100")  # block not a multiple of 32
+    xe, _ = fields(tmq, g, 4, psi)
+    out, tmp = tmq.Field(g, 4), tmq.Field(g, 4)
+    tmq.precond_op(g, out, xe, tmp, 0, False)
+    ref = orc.apply_M_pc(po, U, mask(po, psi, 0))
+    assert rel(get(tmq, g, out, 0), ref) < TOL[4]
