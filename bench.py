@@ -139,10 +139,14 @@ def run_ours(args, rank, world):
     psi_np = inputs.spinor_field(L, 2, 2002 + rank)
     gen_s = time.time() - t0
     U = torch.from_numpy(U_np).to(dev)
-    p_nd = tmq.Params(L, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=12)
+    prec, nf, recon = tmq.PRECS[args.prec], args.nf, args.recon
+    if nf == 2:
+        p_nd = tmq.Params(L, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=recon)
+    else:
+        p_nd = tmq.Params(L, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=recon)
     g = tmq.Gauge(p_nd, U)
-    psi = torch.from_numpy(psi_np).to(dev)
-    prec, nf, recon = tmq.TM_PREC_F32, 2, 12
+    tune_table = tmq.autotune(g)
+    psi = torch.from_numpy(psi_np if nf == 2 else psi_np[..., :1, :, :].copy()).to(dev)
     xe = tmq.pack(g, psi, 0, prec)
     tmp, out = tmq.Field(g, prec), tmq.Field(g, prec)
     stream = torch.cuda.current_stream()
@@ -189,27 +193,34 @@ def run_ours(args, rank, world):
     avg_launch_ms = (sum(ta) + sum(tb)) / (2 * K)
     achieved = ((la + lb) / 2 * Vh) / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_src = load_peaks()
-    traffic = read_traffic("k_dslash_f32_nd_r12_32x32x32x64")
+    traffic = read_traffic("k_dslash_%s_%s_r%d_%s" % (args.prec, "nd" if nf == 2 else "deg", recon,
+                                                      "x".join(map(str, L))))
 
     result = {
         "metric": "TM dslash GFLOPS & % HBM roofline per precision; CG time-to-1e-10 mixed vs FP64",
         "value": round(value, 1), "unit": "GFLOPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded SU(3) links exp(0.3 i H), Gaussian spinors)",
-        "config": {"workload": "M_asym (eq. 2.2 LHS), non-degenerate doublet 32^3x64, kappa=0.1612, "
-                               "mu=0.135, eps=0.15, FP32 storage, recon-12",
-                   "lattice": list(L), "flavours": nf, "storage": "fp32", "recon": recon,
+        "dtype": args.prec, "data": "synthetic (seeded SU(3) links exp(0.3 i H), Gaussian spinors)",
+        "config": {"workload": ("M_asym (eq. 2.2 LHS), non-degenerate doublet %s, kappa=0.1612, mu=0.135, eps=0.15"
+                                % "x".join(map(str, L)) if nf == 2 else
+                                "M_asym (eq. 2.2 LHS), one flavour %s, kappa=0.1612, mu=0.004"
+                                % "x".join(map(str, L))) + ", %s storage, recon-%d" % (args.prec.upper(), recon),
+                   "lattice": list(L), "flavours": nf, "storage": args.prec, "recon": recon,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: links 403 MB, each spinor parity 201 MB, no flush",
                    "flops_per_even_site": FLOPS_PER_SITE[nf], "bytes_per_even_site": asym_bytes(prec, nf, recon)},
         "gpu_launches": 2 * K,
-        "roofline": {"bound": "hbm", "kernel": "k_dslash<FP32, doublet, recon-12> (both launches of M_asym)",
+        "roofline": {"bound": "hbm", "kernel": "k_dslash<%s, %s, recon-%d> (both launches of M_asym)"
+                     % (args.prec.upper(), "doublet" if nf == 2 else "one flavour", recon),
                      "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "bytes_per_launch_algorithmic": (la + lb) / 2 * Vh,
                      "launch_ms": {"twinv": round(statistics.mean(ta), 5), "twxpay": round(statistics.mean(tb), 5)}},
         "clocks": clocks,
+        "launch_table": tune_table,
     }
+    if rank == 0 and not args.quick and (args.prec, nf, recon, L) != ("f32", 2, 12, (32, 32, 32, 64)):
+        args.quick = True  # the extra sections describe the default workload only
     if rank == 0 and not args.quick:
         result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
         result["per_precision"] = per_precision(tmq, U, psi, dev, args)
@@ -286,6 +297,7 @@ def per_precision(tmq, U, psi, dev, args):
             p = tmq.Params(L, KAPPA, mu, eps, flavor=(tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS),
                            recon=recon)
             g = tmq.Gauge(p, U)
+            tmq.autotune(g)
             src = psi if nf == 2 else psi[..., :1, :, :].contiguous()
             for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16, tmq.TM_PREC_F64):
                 if recon != 12 and prec == tmq.TM_PREC_F64:
@@ -445,6 +457,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline step only (no tables, e2e or baselines)")
     ap.add_argument("--lattice", default=None, help="override the lattice, e.g. 32,32,32,32 (profiling runs)")
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline storage (profiling runs)")
+    ap.add_argument("--nf", type=int, default=2, choices=[1, 2], help="flavours of the headline step (profiling runs)")
+    ap.add_argument("--recon", type=int, default=12, choices=[18, 12, 8], help="link storage (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -285,7 +285,7 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
     for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(g->nf == 2 && j == 0) ? 1 : 0, 128};
+        for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
     cudaStream_t s = (cudaStream_t)stream;
     tm_status st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
     if (st == TM_OK) st = cuda_check(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
@@ -501,8 +501,11 @@ tm_status tm_autotune(tm_gauge *g, void *stream)
         for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
             float best = 1e30f;
             tm_tune_entry bestc = g->tune[pi][pro];
-            for (int variant = 0; variant < ((g->nf == 2 && !pro) ? 2 : 1); variant++) {
+            for (int variant = 0; variant < 7; variant++) {
+                if (pro && (variant == 1 || variant == 2)) continue;  // split and pipeline: no prologue
+                if (variant == 1 && g->nf != 2) continue;  // flavour split needs the doublet
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
+                    if (variant >= 3 && blocks[bi] != 128) continue;  // register-capped forms use 128
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
                     float ms = 0;
                     for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -563,7 +566,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || (variant != 0 && variant != 1) || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant > 6 || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

@@ -337,6 +337,94 @@ struct LinkLoader<P16, RECON> {
     }
 };
 
+
+// Convert the raw chunks of one site (as loaded) to reals; FP16 values stay unscaled (the norm
+// is applied by the caller).
+template <int PREC>
+__device__ __forceinline__ void spinor_from_chunks(const typename Traits<PREC>::schunk *c,
+                                                   typename Traits<PREC>::real v[24])
+{
+    if constexpr (PREC == P64) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) { v[2 * k] = c[k].x; v[2 * k + 1] = c[k].y; }
+    } else if constexpr (PREC == P32) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            v[4 * k] = c[k].x; v[4 * k + 1] = c[k].y; v[4 * k + 2] = c[k].z; v[4 * k + 3] = c[k].w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float2 a = h2f(c[k].x), b = h2f(c[k].y), d = h2f(c[k].z), e = h2f(c[k].w);
+            v[8 * k + 0] = a.x; v[8 * k + 1] = a.y; v[8 * k + 2] = b.x; v[8 * k + 3] = b.y;
+            v[8 * k + 4] = d.x; v[8 * k + 5] = d.y; v[8 * k + 6] = e.x; v[8 * k + 7] = e.y;
+        }
+    }
+}
+
+// Decode a link from its raw chunks held in registers (same formats as LinkLoader).
+template <int PREC, int RECON> struct LinkRegLoader;
+template <int RECON> struct LinkRegLoader<P64, RECON> {
+    __device__ static __forceinline__ void load(const double2 *c, Link<double> &U)
+    {
+        if (RECON == 8) {
+            double r[8];
+#pragma unroll
+            for (int k = 0; k < 4; k++) { r[2 * k] = c[k].x; r[2 * k + 1] = c[k].y; }
+            decode_link8(r, U);
+            return;
+        }
+        constexpr int NROW = (RECON == 18) ? 3 : 2;
+#pragma unroll
+        for (int k = 0; k < 3 * NROW; k++) U.u[k / 3][k % 3] = {c[k].x, c[k].y};
+        if (RECON == 12) complete_row3(U);
+    }
+};
+template <int RECON> struct LinkRegLoader<P32, RECON> {
+    template <typename CH>
+    __device__ static __forceinline__ void load(const CH *c, Link<float> &U)
+    {
+        if constexpr (RECON == 18) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) U.u[k / 3][k % 3] = {c[k].x, c[k].y};
+        } else {
+            constexpr int NC = RECON / 4;
+            float r[RECON];
+#pragma unroll
+            for (int k = 0; k < NC; k++) { r[4 * k] = c[k].x; r[4 * k + 1] = c[k].y; r[4 * k + 2] = c[k].z; r[4 * k + 3] = c[k].w; }
+            if constexpr (RECON == 12) {
+#pragma unroll
+                for (int k = 0; k < 6; k++) U.u[k / 3][k % 3] = {r[2 * k], r[2 * k + 1]};
+                complete_row3(U);
+            } else {
+                decode_link8(r, U);
+            }
+        }
+    }
+};
+template <int RECON> struct LinkRegLoader<P16, RECON> {
+    template <typename CH>
+    __device__ static __forceinline__ void load(const CH *c, Link<float> &U)
+    {
+        if constexpr (RECON == 18) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) { float2 v = h2f(c[k]); U.u[k / 3][k % 3] = {v.x, v.y}; }
+        } else if constexpr (RECON == 12) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float2 a = h2f(c[k].x), b = h2f(c[k].y);
+                U.u[(2 * k) / 3][(2 * k) % 3] = {a.x, a.y};
+                U.u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {b.x, b.y};
+            }
+            complete_row3(U);
+        } else {
+            float2 a = h2f(c[0].x), b = h2f(c[0].y), d = h2f(c[0].z), e = h2f(c[0].w);
+            float r[8] = {a.x, a.y, b.x, b.y, d.x, d.y, e.x * 3.14159265358979f, e.y * 3.14159265358979f};
+            decode_link8(r, U);
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------------- local twist
 // A general (flavour x flavour) matrix per gamma5 block: m[g][f][f'], g = 0 for spins 0,1
 // (gamma5 = +1 in the DeGrand-Rossi basis) and g = 1 for spins 2,3 (gamma5 = -1).  For one

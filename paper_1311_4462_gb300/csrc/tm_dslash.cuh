@@ -184,7 +184,7 @@ __device__ __forceinline__ void twist_split(const Twist<T> &tw, int f, T own[24]
 }
 
 template <int PREC, int NF, int RECON, bool PRO>
-__global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+__device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
@@ -299,6 +299,20 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
+template <int PREC, int NF, int RECON, bool PRO>
+__global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    dslash_body<PREC, NF, RECON, PRO>(a);
+}
+
+// The same kernel with a register cap: 128-thread blocks, at least MINB resident per SM
+// (65536 / (128 MINB) registers per thread), traded against spills by the autotuner.
+template <int PREC, int NF, int RECON, bool PRO, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    dslash_body<PREC, NF, RECON, PRO>(a);
+}
+
 template <int PREC, int RECON>
 __global__ void __launch_bounds__(256) k_dslash_fsplit(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
@@ -411,8 +425,154 @@ __global__ void __launch_bounds__(256) k_dslash_fsplit(const __grid_constant__ D
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Variant 2: the same computation as k_dslash with an explicit two-stage software pipeline:
+// the raw 16-byte chunks of hop h+1 (link and neighbour spinors, not yet converted) are
+// loaded into registers before hop h is computed, so every warp keeps two hops of global
+// loads in flight instead of one.
+template <int PREC, int RECON, int NF>
+struct HopRaw {
+    typename LinkLayout<PREC, RECON>::chunk l[LinkLayout<PREC, RECON>::N];
+    typename Traits<PREC>::schunk s[NF][Traits<PREC>::SCHUNKS];
+    float n[NF];
+};
+
+template <int PREC, int RECON, int NF>
+__device__ __forceinline__ void fetch_hop(HopRaw<PREC, RECON, NF> &r, const typename LinkLayout<PREC, RECON>::chunk *g,
+                                          int lcb, const typename Traits<PREC>::schunk *in, const float *in_norm, int nb,
+                                          int Vh)
+{
+#pragma unroll
+    for (int k = 0; k < LinkLayout<PREC, RECON>::N; k++) r.l[k] = ldg(g + (size_t)k * Vh + lcb);
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+#pragma unroll
+        for (int k = 0; k < Traits<PREC>::SCHUNKS; k++)
+            r.s[f][k] = ldg(in + ((size_t)f * Traits<PREC>::SCHUNKS + k) * Vh + nb);
+        if constexpr (PREC == P16) r.n[f] = __ldg(in_norm + (size_t)f * Vh + nb);
+    }
+}
+
+// decode the raw link of a HopRaw (same arithmetic as LinkLoader on registers)
+template <int PREC, int RECON, int NF, typename T>
+__device__ __forceinline__ void decode_link_raw(const HopRaw<PREC, RECON, NF> &r, Link<T> &U)
+{
+    using LC = typename LinkLayout<PREC, RECON>::chunk;
+    constexpr int N = LinkLayout<PREC, RECON>::N;
+    // reuse LinkLoader by pointing it at a register copy laid out as [k][1]
+    LC tmp[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) tmp[k] = r.l[k];
+    LinkRegLoader<PREC, RECON>::load(tmp, U);
+}
+
+template <int PREC, int RECON, int NF, int MU, bool FWD, typename T>
+__device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC, RECON, NF> &r, T sp, T sg)
+{
+    Link<T> U;
+    decode_link_raw<PREC, RECON, NF>(r, U);
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        T v[24];
+        T scale = sg;
+        spinor_from_chunks<PREC>(r.s[f], v);
+        if constexpr (PREC == P16) scale = sg * r.n[f];
+        hop_one<MU, FWD>(acc[f], U, v, sp, scale);
+    }
+}
+
+template <int PREC, int NF, int RECON>
+__global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    using T = typename Traits<PREC>::real;
+    using LL = LinkLayout<PREC, RECON>;
+    using LC = typename LL::chunk;
+    using SC = typename Traits<PREC>::schunk;
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+    int r = cb;
+    const int xh = r % a.X1h;
+    r /= a.X1h;
+    const int y = r % a.Ly;
+    r /= a.Ly;
+    const int z = r % a.Lz;
+    const int t = r / a.Lz;
+    const int op = a.out_parity;
+    const int x = 2 * xh + ((op + y + z + t) & 1);
+    const int row = cb - xh;
+    const size_t gpar = (size_t)LL::N * a.Vh;
+    const LC *G = reinterpret_cast<const LC *>(a.gauge);
+    const LC *Gout = G + (size_t)op * gpar, *Gin = G + (size_t)(1 - op) * gpar;
+    const SC *in = reinterpret_cast<const SC *>(a.in);
+    // neighbour indices of the 8 hops (forward, backward for mu = x, y, z, t)
+    const int sy = a.X1h, sz = a.X1h * a.Ly, st = a.X1h * a.Ly * a.Lz;
+    const int n0 = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1), n1 = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
+    const int n2 = (y == a.Ly - 1) ? cb - (a.Ly - 1) * sy : cb + sy, n3 = (y == 0) ? cb + (a.Ly - 1) * sy : cb - sy;
+    const int n4 = (z == a.Lz - 1) ? cb - (a.Lz - 1) * sz : cb + sz, n5 = (z == 0) ? cb + (a.Lz - 1) * sz : cb - sz;
+    const int n6 = (t == a.Lt - 1) ? cb - (a.Lt - 1) * st : cb + st, n7 = (t == 0) ? cb + (a.Lt - 1) * st : cb - st;
+    const T one = T(1);
+    const T sgf = (t == a.Lt - 1 && a.tbc) ? -one : one, sgb = (t == 0 && a.tbc) ? -one : one;
+    const T spf = -a.sigma, spb = a.sigma;
+
+    T acc[NF][24];
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+#pragma unroll
+        for (int k = 0; k < 24; k++) acc[f][k] = T(0);
+    HopRaw<PREC, RECON, NF> ra, rb;
+    const size_t m2 = 2 * gpar;
+    fetch_hop(ra, Gout + 0 * m2, cb, in, a.in_norm, n0, a.Vh);
+    fetch_hop(rb, Gin + 0 * m2, n1, in, a.in_norm, n1, a.Vh);
+    compute_hop<PREC, RECON, NF, 0, true>(acc, ra, spf, one);
+    fetch_hop(ra, Gout + 1 * m2, cb, in, a.in_norm, n2, a.Vh);
+    compute_hop<PREC, RECON, NF, 0, false>(acc, rb, spb, one);
+    fetch_hop(rb, Gin + 1 * m2, n3, in, a.in_norm, n3, a.Vh);
+    compute_hop<PREC, RECON, NF, 1, true>(acc, ra, spf, one);
+    fetch_hop(ra, Gout + 2 * m2, cb, in, a.in_norm, n4, a.Vh);
+    compute_hop<PREC, RECON, NF, 1, false>(acc, rb, spb, one);
+    fetch_hop(rb, Gin + 2 * m2, n5, in, a.in_norm, n5, a.Vh);
+    compute_hop<PREC, RECON, NF, 2, true>(acc, ra, spf, one);
+    fetch_hop(ra, Gout + 3 * m2, cb, in, a.in_norm, n6, a.Vh);
+    compute_hop<PREC, RECON, NF, 2, false>(acc, rb, spb, one);
+    fetch_hop(rb, Gin + 3 * m2, n7, in, a.in_norm, n7, a.Vh);
+    compute_hop<PREC, RECON, NF, 3, true>(acc, ra, spf, sgf);
+    compute_hop<PREC, RECON, NF, 3, false>(acc, rb, spb, sgb);
+
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    const int epi = a.epilogue;
+    if (epi == EPI_SCALE) {
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+#pragma unroll
+            for (int k = 0; k < 24; k++) acc[f][k] *= a.coef;
+    } else if (epi == EPI_TW) {
+        apply_twist<T, NF>(a.tw_epi, acc);
+    } else {
+        T xv[NF][24];
+        const SC *X = reinterpret_cast<const SC *>(a.x);
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+            load_spinor<PREC>(X + f * fstride, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv[f]);
+        if (epi == EPI_TWX_AXPY) {
+            apply_twist<T, NF>(a.tw_epi, xv);
+        } else if (epi == EPI_X_TWAXPY) {
+            apply_twist<T, NF>(a.tw_epi, acc);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+#pragma unroll
+            for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+        if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+    }
+    SC *O = reinterpret_cast<SC *>(a.out);
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+        store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+}
+
 // variant 0: one thread per site (both flavours); variant 1: one thread per site and flavour
-// (doublet without prologue only).  block: threads per block (multiple of 32, <= 256).
+// (doublet without prologue only); variant 2: variant 0 with the two-stage load pipeline (no prologue);
+// variants 3-6: variant 0 with a register cap for 4, 5, 6, 8 resident 128-thread blocks.  block: threads per block (multiple of 32, <= 256).
 template <int PREC>
 cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                int variant, int block, cudaStream_t s)
@@ -428,7 +588,45 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
         }
         return cudaGetLastError();
     }
+    if (variant >= 3) {
+        // register-capped launches, 128 threads per block
+        const int g128 = (a.Vh + 127) / 128;
+#define TM_LB(NF, R, P)                                                           \
+    switch (variant) {                                                            \
+    case 3: k_dslash_lb<PREC, NF, R, P, 4><<<g128, 128, 0, s>>>(a); break;        \
+    case 4: k_dslash_lb<PREC, NF, R, P, 5><<<g128, 128, 0, s>>>(a); break;        \
+    case 5: k_dslash_lb<PREC, NF, R, P, 6><<<g128, 128, 0, s>>>(a); break;        \
+    default: k_dslash_lb<PREC, NF, R, P, 8><<<g128, 128, 0, s>>>(a); break;       \
+    }
+#define TM_LBR(NF, P)                   \
+    switch (recon) {                    \
+    case 18: TM_LB(NF, 18, P) break;     \
+    case 12: TM_LB(NF, 12, P) break;     \
+    case 8: TM_LB(NF, 8, P) break;       \
+    default: return cudaErrorInvalidValue; \
+    }
+        if (nf == 1) {
+            if (pro) { TM_LBR(1, true) } else { TM_LBR(1, false) }
+        } else {
+            if (pro) { TM_LBR(2, true) } else { TM_LBR(2, false) }
+        }
+#undef TM_LBR
+#undef TM_LB
+        return cudaGetLastError();
+    }
     const int grid = (a.Vh + block - 1) / block;
+    if (variant == 2 && !pro) {
+#define TM_PIPE(NF)                                                                 \
+    switch (recon) {                                                                \
+    case 18: k_dslash_pipe<PREC, NF, 18><<<grid, block, 0, s>>>(a); break;          \
+    case 12: k_dslash_pipe<PREC, NF, 12><<<grid, block, 0, s>>>(a); break;          \
+    case 8: k_dslash_pipe<PREC, NF, 8><<<grid, block, 0, s>>>(a); break;            \
+    default: return cudaErrorInvalidValue;                                          \
+    }
+        if (nf == 1) { TM_PIPE(1) } else { TM_PIPE(2) }
+#undef TM_PIPE
+        return cudaGetLastError();
+    }
 #define TM_LAUNCH(NF, R, P) k_dslash<PREC, NF, R, P><<<grid, block, 0, s>>>(a)
 #define TM_RECON(NF, P)                  \
     switch (recon) {                     \

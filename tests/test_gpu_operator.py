@@ -52,7 +52,8 @@ def setup(case, recon):
 
 def use_variant(tmq, g, variant, block=128):
     """Force the hopping-kernel launch choice (variant 1 = thread per site and flavour, doublet only)."""
-    tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:0:{block}" for p in ("f64", "f32", "f16")))
+    pro_variant = variant if variant >= 3 else 0
+    tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
 
 def fields(tmq, g, prec, psi):
@@ -84,12 +85,12 @@ def test_pack_unpack_roundtrip(case, prec, recon):
 @pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
-@pytest.mark.parametrize("variant", [0, 1], ids=["site", "split"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 4, 6], ids=["site", "split", "pipe", "cap5", "cap8"])
 def test_precond_op(case, prec, recon, pc, dagger, variant):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
-    if variant and p.nf == 1:
+    if variant == 1 and p.nf == 1:
         pytest.skip("flavour split applies to the doublet")
-    use_variant(tmq, g, variant, block=64 if variant else 128)
+    use_variant(tmq, g, variant, block=64 if variant in (1, 2) else 128)
     xe, _ = fields(tmq, g, prec, psi)
     out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
     tmq.precond_op(g, out, xe, tmp, pc, dagger)
@@ -103,7 +104,7 @@ def test_precond_op(case, prec, recon, pc, dagger, variant):
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 def test_full_operator(case, prec, dagger):
     tmq, p, po, U, g, psi, chi = setup(case, 12)
-    use_variant(tmq, g, 1 if p.nf == 2 else 0, block=256)
+    use_variant(tmq, g, 2, block=256)
     xe, xo = fields(tmq, g, prec, psi)
     oe, oo = tmq.Field(g, prec), tmq.Field(g, prec)
     tmq.mat(g, oe, oo, xe, xo, dagger)
@@ -116,13 +117,13 @@ def test_full_operator(case, prec, dagger):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 @pytest.mark.parametrize("out_parity", [0, 1])
-@pytest.mark.parametrize("variant", [0, 1], ids=["site", "split"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 5], ids=["site", "split", "pipe", "cap4", "cap6"])
 def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
     """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
     tmq, p, po, U, g, psi, chi = setup(case, 12)
-    if variant and p.nf == 1:
+    if variant == 1 and p.nf == 1:
         pytest.skip("flavour split applies to the doublet")
-    use_variant(tmq, g, variant, block=96 if variant else 128)
+    use_variant(tmq, g, variant, block=96 if variant in (1, 2) else 128)
     ip = 1 - out_parity
     fin = fields(tmq, g, prec, psi)[ip]
     fx = fields(tmq, g, prec, chi)[out_parity]
