@@ -13,6 +13,9 @@
  * as H_eo, which makes the left-hand sides of eq. 2.2 and 2.3 the exact Schur complements.
  *
  * Conventions shared by every call:
+ *  - Operator calls (tm_dslash*, tm_precond_op, tm_mat, tm_prepare_rhs, tm_reconstruct_odd,
+ *    tm_twist) accept fields with nrhs >= 1 (all operands sharing nrhs): every right-hand side
+ *    is processed in one launch that reads each link once per site for all of them.
  *  - All pointers to field or gauge data are DEVICE pointers (cudaMalloc'd or from an
  *    allocator such as torch).  The caller owns every field; the library never frees one.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call except
@@ -130,6 +133,15 @@ tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_fie
                     void *stream);
 
 /*
+ * Z2 noise sources (+-1 +- i)/sqrt 2 for the stochastic estimator of disconnected loops (the
+ * paper's production use, sec. 1 and 4), written straight into one parity of a field: element i
+ * (flat canonical index) of right-hand side r takes bits 0 / 1 (real / imaginary sign) of
+ * SplitMix64's output function at the counter state (seed + r + 1) G + (i + 1) G,
+ * G = 0x9E3779B97F4A7C15 (Steele, Lea & Flood 2014).
+ */
+tm_status tm_noise_z2(const tm_gauge *g, const tm_field *out, int parity, unsigned long long seed, void *stream);
+
+/*
  * One fused hopping kernel (sec. 2.1):  out(out_parity) = epilogue(H_{p,1-p} in), with
  * H^dag and daggered twists in tm_dslash_dagger.  `x` has the output parity and is used by
  * the XPAY epilogues (NULL otherwise).  out, in and x must share a precision; out must not
@@ -150,6 +162,15 @@ tm_status tm_dslash_dagger(const tm_gauge *g, const tm_field *out, const tm_fiel
  */
 tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
                         int pc, int dagger, void *stream);
+
+/*
+ * tm_precond_op restricted to the right-hand sides listed in active_dev (device array of
+ * nactive indices into the fields' nrhs), for solvers that stop iterating converged sources;
+ * the other right-hand sides of out_e and tmp_o are left untouched.  Listed indices outside
+ * [0, nrhs) are skipped by the kernels.
+ */
+tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
+                               int pc, int dagger, const int *active_dev, int nactive, void *stream);
 
 /*
  * Full unpreconditioned operator (eq. 2.1) on both parities: out = M in (dagger = 0) or
@@ -204,6 +225,7 @@ typedef struct {
     int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
     int use_x0;      /* 1: x_e holds the initial guess on entry; 0: start from zero */
     int want_pc_residual; /* 1: also compute stats->pc_residual (one more FP64 operator application) */
+    int use_graph;   /* tm_solve_multi: capture the sloppy iteration as a CUDA graph and replay it */
 } tm_solver_params;
 
 typedef struct {
@@ -225,6 +247,31 @@ tm_status tm_solve_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp
  */
 tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
                    tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Multi-RHS solve (batched stochastic sources): x_e and b_e hold nrhs <= 64 right-hand sides
+ * (FP64).  All sources iterate together: every operator factor is one multi-RHS launch that
+ * reads each link once per site for all active sources, and every BLAS step is one launch with
+ * per-source alpha, beta and |r|^2.  The mixed solver takes its FP64 reliable updates for all
+ * active sources at once when any of them asks for one; a source whose FP64 true residual meets
+ * tol is dropped (later launches skip it) and its iteration count recorded.  use_graph captures
+ * the sloppy iteration (two operator applications, the alpha reduction and the fused update)
+ * as a CUDA graph, re-captured when the number of active sources changes.  The solve runs on an
+ * internal stream ordered after `stream` and blocks until it ends.  stats: array of nrhs
+ * entries.  Errors as tm_solve (TM_ERR_NOCONV when any source misses tol within maxiter).
+ */
+tm_status tm_solve_multi_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp, int nrhs, size_t *bytes);
+tm_status tm_solve_multi(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
+                         tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * <a_r, gamma5 b_r> for every right-hand side r (complex, FP64 accumulation, blocking): the
+ * per-source term of the stochastic estimator Tr[gamma5 M^-1] ~ (1/N) sum_n eta_n^dag gamma5 s_n
+ * (s_n = M^-1 eta_n), evaluated per parity and summed by the caller.  re_out, im_out: host
+ * arrays of nrhs doubles.  Operand precisions as for the solver's combinations (FP64 pairs).
+ */
+tm_status tm_g5dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, double *im_out,
+                   void *stream);
 
 /* FP64-accumulated reductions over one parity field (blocking): |x|^2 and Re<a, b>. */
 tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stream);

@@ -212,13 +212,14 @@ DEFAULT_DELTA = {TM_PREC_F16: 1e-2, TM_PREC_F32: 1e-3}
 
 
 def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000,
-                  delta=None, sloppy_prec=TM_PREC_F32, use_x0=False, want_pc_residual=False):
+                  delta=None, sloppy_prec=TM_PREC_F32, use_x0=False, want_pc_residual=False, use_graph=False):
     sp = L.tm_solver_params()
     sp.solver = TM_SOLVER_MIXED if solver == "mixed" else TM_SOLVER_CG
     sp.solution, sp.pc, sp.dagger = int(solution), int(pc), int(dagger)
     sp.tol, sp.maxiter = float(tol), int(maxiter)
     sp.delta = float(delta if delta is not None else DEFAULT_DELTA.get(int(sloppy_prec), 0.1))
     sp.sloppy_prec, sp.use_x0, sp.want_pc_residual = int(sloppy_prec), int(use_x0), int(want_pc_residual)
+    sp.use_graph = int(use_graph)
     return sp
 
 
@@ -287,6 +288,50 @@ def tune_export(gauge) -> str:
 
 def tune_import(gauge, text: str):
     L.check(L.load().tm_tune_import(gauge.h, text.encode()))
+
+
+def precond_op_active(gauge, out_e: Field, in_e: Field, tmp_o: Field, active, pc=TM_PC_ASYM, dagger=False,
+                      stream=None):
+    """tm_precond_op_active: only the right-hand sides listed in `active` (ints)."""
+    torch = _torch()
+    lst = torch.tensor(list(active), dtype=torch.int32, device="cuda")
+    L.check(L.load().tm_precond_op_active(gauge.h, out_e.ref(), in_e.ref(), tmp_o.ref(), int(pc), int(dagger),
+                                          ctypes.c_void_p(lst.data_ptr()), int(lst.numel()), _stream(stream)))
+    torch.cuda.current_stream().synchronize()
+    return out_e
+
+
+def solve_multi(gauge, x_e: Field, b_e: Field, stream=None, workspace=None, check=True, **kw):
+    """tm_solve_multi: all nrhs sources of b_e at once.  Returns (status, list of per-source stats)."""
+    torch = _torch()
+    sp = solver_params(**kw)
+    n = ctypes.c_size_t()
+    L.check(L.load().tm_solve_multi_workspace_bytes(gauge.h, ctypes.byref(sp), int(x_e.nrhs), ctypes.byref(n)))
+    if workspace is None or workspace.numel() < n.value:
+        workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+    stats = (L.tm_solver_stats * x_e.nrhs)()
+    status = L.load().tm_solve_multi(gauge.h, x_e.ref(), b_e.ref(), ctypes.byref(sp), stats,
+                                     ctypes.c_void_p(workspace.data_ptr()), n.value, _stream(stream))
+    out = [{"iterations": s.iterations, "reliable_updates": s.reliable_updates, "true_residual": s.true_residual,
+            "seconds": s.seconds} for s in stats]
+    if check:
+        L.check(status)
+    return status, out
+
+
+def noise_z2(gauge, field: Field, parity: int, seed: int, stream=None) -> Field:
+    """tm_noise_z2: counter-based Z2 noise (right-hand side r uses seed + r)."""
+    L.check(L.load().tm_noise_z2(gauge.h, field.ref(), int(parity), ctypes.c_ulonglong(int(seed)), _stream(stream)))
+    return field
+
+
+def g5dot(gauge, a: Field, b: Field, stream=None):
+    """tm_g5dot: <a_r, gamma5 b_r> per right-hand side, as a complex numpy array."""
+    import numpy as np
+    n = a.nrhs
+    re, im = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    L.check(L.load().tm_g5dot(gauge.h, a.ref(), b.ref(), re, im, _stream(stream)))
+    return np.array(list(re)) + 1j * np.array(list(im))
 
 
 def version() -> str:

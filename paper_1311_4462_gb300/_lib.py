@@ -32,7 +32,8 @@ class tm_field(ctypes.Structure):
 class tm_solver_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("solution", ctypes.c_int), ("pc", ctypes.c_int), ("dagger", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("delta", ctypes.c_double),
-                ("sloppy_prec", ctypes.c_int), ("use_x0", ctypes.c_int), ("want_pc_residual", ctypes.c_int)]
+                ("sloppy_prec", ctypes.c_int), ("use_x0", ctypes.c_int), ("want_pc_residual", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
 
 
 class tm_solver_stats(ctypes.Structure):
@@ -74,6 +75,13 @@ _SIGS = {
     "tm_force": [vp, vp, ctypes.c_int, FP, FP, FP, FP, ctypes.c_double, ctypes.c_int, vp],
     "tm_norm2_noalloc": [FP, ctypes.c_int, ctypes.c_int, vp, vp],
     "tm_autotune": [vp, vp],
+    "tm_precond_op_active": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp],
+    "tm_solve_multi_workspace_bytes": [vp, ctypes.POINTER(tm_solver_params), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_size_t)],
+    "tm_solve_multi": [vp, FP, FP, ctypes.POINTER(tm_solver_params), ctypes.POINTER(tm_solver_stats), vp,
+                       ctypes.c_size_t, vp],
+    "tm_noise_z2": [vp, FP, ctypes.c_int, ctypes.c_ulonglong, vp],
+    "tm_g5dot": [vp, FP, FP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp],
     "tm_tune_export": [vp, ctypes.c_char_p, ctypes.c_size_t],
     "tm_tune_import": [vp, ctypes.c_char_p],
 }

@@ -16,15 +16,23 @@ cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, boo
                               cudaStream_t s);
 cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, int variant, int block,
                               cudaStream_t s);
+cudaError_t launch_dslash_multi_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, cudaStream_t s);
+cudaError_t launch_dslash_multi_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, cudaStream_t s);
+cudaError_t launch_dslash_multi_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, cudaStream_t s);
 cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void *canon, int ctype, int parity,
                                cudaStream_t s);
 cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, const tm_field *f, int parity,
                                  cudaStream_t s);
 cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void *canon, cudaStream_t s);
+cudaError_t launch_noise_z2(const tm_gauge *g, const tm_field *f, int parity, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
                          cudaStream_t s);
 
 static thread_local char g_err[512];
+constexpr int TM_MAX_RHS_API = 64;
 
 void set_error(const char *fmt, ...)
 {
@@ -179,10 +187,11 @@ static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out
     a.tbc = g->p.t_antiperiodic ? 1 : 0;
 }
 
-// Generic fused hopping launch: out = epi(H or H^dag (pro(in))).
-static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x,
-                               int out_parity, int dagger, int epi, double coef, const Twist<double> *tw_epi,
-                               const Twist<double> *tw_pro, cudaStream_t s)
+// Generic fused hopping launch: out = epi(H or H^dag (pro(in))).  With nact > 1 (or a list act of
+// right-hand-side indices) the multi-RHS kernel processes those right-hand sides of the fields.
+tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x, int out_parity,
+                        int dagger, int epi, double coef, const Twist<double> *tw_epi, const Twist<double> *tw_pro,
+                        cudaStream_t s, const int *act, int nact)
 {
     const int pidx = prec_index(in->prec);
     const bool pro = tw_pro != nullptr;
@@ -190,6 +199,7 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
     memset(&z, 0, sizeof(z));
     const Twist<double> &te = tw_epi ? *tw_epi : z, &tp = tw_pro ? *tw_pro : z;
     const tm_tune_entry tu = g->tune[pidx][pro ? 1 : 0];
+    const bool multi = act != nullptr || nact > 1;
     cudaError_t e;
     if (pidx == 0) {
         DslashArgs<double> a;
@@ -199,7 +209,8 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
         a.coef = coef;
         a.tw_epi = te;
         a.tw_pro = tp;
-        e = launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
+        e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s)
+                  : launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     } else {
         DslashArgs<float> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -208,10 +219,22 @@ static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_
         a.coef = (float)coef;
         a.tw_epi = to_float(te);
         a.tw_pro = to_float(tp);
-        e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s)
-                        : launch_dslash_p16(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
+        if (multi)
+            e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s)
+                            : launch_dslash_multi_p16(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s);
+        else
+            e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s)
+                            : launch_dslash_p16(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     }
     return cuda_check(e, "dslash launch");
+}
+
+static tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x,
+                               int out_parity, int dagger, int epi, double coef, const Twist<double> *tw_epi,
+                               const Twist<double> *tw_pro, cudaStream_t s)
+{
+    // every right-hand side of the fields (nrhs = 1: the single-RHS kernels)
+    return dslash_launch(g, out, in, x, out_parity, dagger, epi, coef, tw_epi, tw_pro, s, nullptr, out->nrhs);
 }
 
 static tm_status same_prec(const tm_field *a, const tm_field *b, const char *what)
@@ -234,7 +257,6 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
     TM_TRY(check_field(g, out, "out"));
     TM_TRY(check_field(g, in, "in"));
     TM_TRY(same_prec(out, in, "tm_dslash"));
-    if (out->nrhs != 1) { set_error("tm_dslash: single-RHS fields only"); return TM_ERR_ARG; }
     if (out_parity != 0 && out_parity != 1) { set_error("out_parity must be 0 or 1"); return TM_ERR_ARG; }
     if (out->data == in->data) { set_error("tm_dslash: out must not alias in"); return TM_ERR_ARG; }
     const double k = g->p.kappa;
@@ -254,6 +276,26 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
     case TM_EPI_XPAY: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_XPAY, k, nullptr, nullptr, s);
     default: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_TW_XPAY, k, &Ri, nullptr, s);
     }
+}
+
+tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                       int dagger, cudaStream_t s, const int *act, int nact)
+{
+    const double k2 = g->p.kappa * g->p.kappa;
+    const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
+    if (pc == TM_PC_ASYM) {
+        // tmp = R^-1_oo H_oe in ;  out = R_ee in - kappa^2 H_eo tmp
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, dagger, EPI_TWX_AXPY, -k2, &R, nullptr, s, act, nact);
+    }
+    if (!dagger) {
+        // tmp = R^-1_oo H_oe in ;  out = in - kappa^2 R^-1_ee H_eo tmp
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, 0, EPI_X_TWAXPY, -k2, &Ri, nullptr, s, act, nact);
+    }
+    // adjoint of the symmetric operator: tmp = R^-dag_oo H^dag_oe R^-dag_ee in ; out = in - kappa^2 H^dag_eo tmp
+    TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s, act, nact));
+    return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
 }
 
 }  // namespace tmk
@@ -365,6 +407,14 @@ tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_fie
     return cuda_check(launch_unpack_spinor(g, canon, canon_type, in, parity, (cudaStream_t)stream), "tm_unpack");
 }
 
+tm_status tm_noise_z2(const tm_gauge *g, const tm_field *out, int parity, unsigned long long seed, void *stream)
+{
+    if (!g) { set_error("tm_noise_z2: null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
+    return cuda_check(launch_noise_z2(g, out, parity, seed, (cudaStream_t)stream), "tm_noise_z2");
+}
+
 tm_status tm_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
                     const tm_field *x, void *stream)
 {
@@ -386,28 +436,34 @@ tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field
     TM_TRY(check_field(g, tmp_o, "tmp_o"));
     TM_TRY(same_prec(out_e, in_e, "tm_precond_op"));
     TM_TRY(same_prec(out_e, tmp_o, "tm_precond_op"));
-    if (out_e->nrhs != 1) { set_error("tm_precond_op: single-RHS fields only"); return TM_ERR_ARG; }
+    if (out_e->nrhs > TM_MAX_RHS_API) { set_error("tm_precond_op: at most %d right-hand sides", TM_MAX_RHS_API); return TM_ERR_ARG; }
     if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
     if (out_e->data == in_e->data || tmp_o->data == in_e->data || tmp_o->data == out_e->data) {
         set_error("tm_precond_op: out_e, in_e and tmp_o must be distinct");
         return TM_ERR_ARG;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    const double k2 = g->p.kappa * g->p.kappa;
-    const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
-    if (pc == TM_PC_ASYM) {
-        // tmp = R^-1_oo H_oe in ;  out = R_ee in - kappa^2 H_eo tmp
-        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, &Ri, nullptr, s));
-        return dslash_launch(g, out_e, tmp_o, in_e, 0, dagger, EPI_TWX_AXPY, -k2, &R, nullptr, s);
+    return precond_core(g, out_e, in_e, tmp_o, pc, dagger, (cudaStream_t)stream, nullptr, out_e->nrhs);
+}
+
+tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
+                               int pc, int dagger, const int *active_dev, int nactive, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out_e, "out_e"));
+    TM_TRY(check_field(g, in_e, "in_e"));
+    TM_TRY(check_field(g, tmp_o, "tmp_o"));
+    TM_TRY(same_prec(out_e, in_e, "tm_precond_op_active"));
+    TM_TRY(same_prec(out_e, tmp_o, "tm_precond_op_active"));
+    if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
+    if (!active_dev || nactive < 1 || nactive > out_e->nrhs) {
+        set_error("tm_precond_op_active: need 1 <= nactive <= nrhs (%d) and a device index list", out_e->nrhs);
+        return TM_ERR_ARG;
     }
-    if (!dagger) {
-        // tmp = R^-1_oo H_oe in ;  out = in - kappa^2 R^-1_ee H_eo tmp
-        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s));
-        return dslash_launch(g, out_e, tmp_o, in_e, 0, 0, EPI_X_TWAXPY, -k2, &Ri, nullptr, s);
+    if (out_e->data == in_e->data || tmp_o->data == in_e->data || tmp_o->data == out_e->data) {
+        set_error("tm_precond_op_active: out_e, in_e and tmp_o must be distinct");
+        return TM_ERR_ARG;
     }
-    // adjoint of the symmetric operator: tmp = R^-dag_oo H^dag_oe R^-dag_ee in ; out = in - kappa^2 H^dag_eo tmp
-    TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s));
-    return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s);
+    return precond_core(g, out_e, in_e, tmp_o, pc, dagger, (cudaStream_t)stream, active_dev, nactive);
 }
 
 tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,
@@ -421,7 +477,6 @@ tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o
     TM_TRY(same_prec(out_e, in_e, "tm_mat"));
     TM_TRY(same_prec(out_o, in_o, "tm_mat"));
     TM_TRY(same_prec(out_e, out_o, "tm_mat"));
-    if (out_e->nrhs != 1) { set_error("tm_mat: single-RHS fields only"); return TM_ERR_ARG; }
     if (out_e->data == in_e->data || out_e->data == in_o->data || out_o->data == in_e->data ||
         out_o->data == in_o->data) {
         set_error("tm_mat: outputs must not alias inputs");
@@ -444,7 +499,6 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
     TM_TRY(check_field(g, b_o, "b_o"));
     TM_TRY(same_prec(bprime_e, b_e, "tm_prepare_rhs"));
     TM_TRY(same_prec(bprime_e, b_o, "tm_prepare_rhs"));
-    if (bprime_e->nrhs != 1) { set_error("tm_prepare_rhs: single-RHS fields only"); return TM_ERR_ARG; }
     if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
     if (bprime_e->data == b_o->data) { set_error("tm_prepare_rhs: bprime_e must not alias b_o"); return TM_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
@@ -465,7 +519,6 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
     TM_TRY(check_field(g, psi_e, "psi_e"));
     TM_TRY(same_prec(psi_o, b_o, "tm_reconstruct_odd"));
     TM_TRY(same_prec(psi_o, psi_e, "tm_reconstruct_odd"));
-    if (psi_o->nrhs != 1) { set_error("tm_reconstruct_odd: single-RHS fields only"); return TM_ERR_ARG; }
     if (psi_o->data == psi_e->data) { set_error("tm_reconstruct_odd: psi_o must not alias psi_e"); return TM_ERR_ARG; }
     const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
     return dslash_launch(g, psi_o, psi_e, b_o, 1, dagger, EPI_TW_XPAY, g->p.kappa, &Ri, nullptr, (cudaStream_t)stream);

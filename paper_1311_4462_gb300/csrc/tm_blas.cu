@@ -136,6 +136,7 @@ __device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
 //   dot: reduce Re<a, b>                    (op DOT)
 //   norm: reduce |a|^2                      (op NORM)
 //   copy: out = a                           (op COPY)
+//   g5dot: reduce Re / Im <a, gamma5 b>     (ops G5DOT_RE, G5DOT_IM)
 // Coefficients come from SVal (host value or device scalar slot times a host multiplier).
 __device__ __forceinline__ double sval(const SVal &v, int rhs, const double *S)
 {
@@ -193,6 +194,20 @@ __global__ void __launch_bounds__(256) k_site_op(SiteOpArgs a)
             load_block<PB>(a.B, blk, cb, a.Vh, vb);
 #pragma unroll
             for (int k = 0; k < 24; k++) part = fma(va[k], vb[k], part);  // Re<a,b> = sum re*re + im*im
+            break;
+        }
+        case OP_G5DOT_RE:    // Re <a, gamma5 b>: gamma5 = +1 on spins 0, 1 and -1 on spins 2, 3
+        case OP_G5DOT_IM: {  // Im <a, gamma5 b>
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            load_block<PB>(a.B, blk, cb, a.Vh, vb);
+            const bool re = a.op == OP_G5DOT_RE;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                const T sg = (j < 6) ? T(1) : T(-1);
+                const T v = re ? fma(va[2 * j], vb[2 * j], va[2 * j + 1] * vb[2 * j + 1])
+                               : fma(va[2 * j], vb[2 * j + 1], -va[2 * j + 1] * vb[2 * j]);
+                part = fma(sg, v, part);
+            }
             break;
         }
         case OP_NORM: {

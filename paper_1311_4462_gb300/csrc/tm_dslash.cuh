@@ -184,13 +184,23 @@ __device__ __forceinline__ void twist_split(const Twist<T> &tw, int f, T own[24]
 }
 
 template <int PREC, int NF, int RECON, bool PRO>
-__device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a)
+__device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
     using LC = typename LL::chunk;
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= a.Vh) return;
+    // right-hand side `rhs` of a field with nrhs > 1: its flavour blocks start at rhs * NF
+    DslashArgs<T> a = a0;
+    if (rhs) {
+        using SC0 = typename Traits<PREC>::schunk;
+        const size_t boff = (size_t)rhs * NF * Traits<PREC>::SCHUNKS * a0.Vh, noff = (size_t)rhs * NF * a0.Vh;
+        a.in = reinterpret_cast<const SC0 *>(a0.in) + boff;
+        a.out = reinterpret_cast<SC0 *>(a0.out) + boff;
+        if (a0.x) a.x = reinterpret_cast<const SC0 *>(a0.x) + boff;
+        if (a0.in_norm) a.in_norm = a0.in_norm + noff;
+        if (a0.out_norm) a.out_norm = a0.out_norm + noff;
+        if (a0.x_norm) a.x_norm = a0.x_norm + noff;
+    }
 
     int r = cb;
     const int xh = r % a.X1h;
@@ -302,7 +312,9 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
 template <int PREC, int NF, int RECON, bool PRO>
 __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
-    dslash_body<PREC, NF, RECON, PRO>(a);
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+    dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
 }
 
 // The same kernel with a register cap: 128-thread blocks, at least MINB resident per SM
@@ -310,7 +322,51 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
 template <int PREC, int NF, int RECON, bool PRO, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
-    dslash_body<PREC, NF, RECON, PRO>(a);
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+    dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
+}
+
+// Several right-hand sides in one launch (multi-RHS, sources share the gauge field): thread
+// t handles site t / nact of right-hand side act[t % nact] (act = NULL: rhs = t % nact).  The
+// right-hand sides of a site sit in consecutive lanes, so their identical link loads are one
+// request per warp: each link leaves memory once per site for all nact sources.
+template <int PREC, int NF, int RECON, bool PRO>
+__global__ void __launch_bounds__(128, 4)
+    k_dslash_multi(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act, int nact,
+                   int nrhs)
+{
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long cb = tid / nact;
+    if (cb >= a.Vh) return;
+    const int slot = (int)(tid - cb * nact);
+    const int rhs = act ? __ldg(act + slot) : slot;
+    if (rhs < 0 || rhs >= nrhs) return;  // an index outside the fields is skipped, never dereferenced
+    dslash_body<PREC, NF, RECON, PRO>(a, (int)cb, rhs);
+}
+
+template <int PREC>
+cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
+                                     const int *act, int nact, int nrhs, cudaStream_t s)
+{
+    const long threads = (long)a.Vh * nact;
+    const unsigned grid = (unsigned)((threads + 127) / 128);
+#define TM_M(NF, R, P) k_dslash_multi<PREC, NF, R, P><<<grid, 128, 0, s>>>(a, act, nact, nrhs)
+#define TM_MR(NF, P)                        \
+    switch (recon) {                        \
+    case 18: TM_M(NF, 18, P); break;        \
+    case 12: TM_M(NF, 12, P); break;        \
+    case 8: TM_M(NF, 8, P); break;          \
+    default: return cudaErrorInvalidValue;  \
+    }
+    if (nf == 1) {
+        if (pro) { TM_MR(1, true) } else { TM_MR(1, false) }
+    } else {
+        if (pro) { TM_MR(2, true) } else { TM_MR(2, false) }
+    }
+#undef TM_MR
+#undef TM_M
+    return cudaGetLastError();
 }
 
 template <int PREC, int RECON>

@@ -8,4 +8,9 @@ cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, boo
 {
     return launch_dslash_impl<P16>(a, nf, recon, pro, variant, block, s);
 }
+cudaError_t launch_dslash_multi_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, cudaStream_t s)
+{
+    return launch_dslash_multi_impl<P16>(a, nf, recon, pro, act, nact, nrhs, s);
+}
 }  // namespace tmk

@@ -8,4 +8,9 @@ cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bo
 {
     return launch_dslash_impl<P64>(a, nf, recon, pro, variant, block, s);
 }
+cudaError_t launch_dslash_multi_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, cudaStream_t s)
+{
+    return launch_dslash_multi_impl<P64>(a, nf, recon, pro, act, nact, nrhs, s);
+}
 }  // namespace tmk

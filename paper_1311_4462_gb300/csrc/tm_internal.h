@@ -20,6 +20,9 @@ enum Epilogue {
 // twist selector for host-built coefficient tables
 enum TwistKind { TW_R = 0, TW_RINV = 1 };
 
+// operator composition shared by the API and the solvers (tm_api.cu)
+tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                       int dagger, cudaStream_t s, const int *act, int nact);
 }  // namespace tmk
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
@@ -49,4 +52,7 @@ int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
 size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);
 tm_status cuda_check(cudaError_t e, const char *what);
+// operator composition shared by the API and the solvers (tm_api.cu)
+tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                       int dagger, cudaStream_t s, const int *act, int nact);
 }  // namespace tmk

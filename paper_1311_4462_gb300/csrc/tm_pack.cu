@@ -159,6 +159,45 @@ __global__ void k_pack_gauge(void *out, const double2 *canon, int recon, Geo g)
     }
 }
 
+// ------------------------------------------------------------------------------ Z2 noise
+// Element i of source `seed` (flat index into the canonical layout [Lt][Lz][Ly][Lx][nf][4][3]):
+// sign bits of SplitMix64's output function (Steele, Lea & Flood, OOPSLA 2014) at the counter
+// state (seed + 1) G + (i + 1) G, G = 0x9E3779B97F4A7C15: bit 0 -> real, bit 1 -> imaginary,
+// value (+-1 +- i)/sqrt(2).  Right-hand side r of the field uses seed + r.
+__device__ __forceinline__ unsigned long long splitmix64_out(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <int PREC>
+__global__ void k_noise_z2(void *out, float *norm, int parity, unsigned long long seed, Geo g)
+{
+    using T = typename Traits<PREC>::real;
+    using SC = typename Traits<PREC>::schunk;
+    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long)g.Vh * g.nf * g.nrhs) return;
+    const int cb = (int)(id % g.Vh);
+    const int f = (int)((id / g.Vh) % g.nf);
+    const int rhs = (int)(id / ((long)g.Vh * g.nf));
+    const long lex = lex_of(cb, parity, g.X1h, g.Lx, g.Ly, g.Lz);
+    const unsigned long long G = 0x9E3779B97F4A7C15ull;
+    const unsigned long long base = (seed + rhs + 1ull) * G;
+    const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+    T v[24];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const unsigned long long i = (unsigned long long)((lex * g.nf + f) * 12 + k);
+        const unsigned long long z = splitmix64_out(base + (i + 1ull) * G);
+        v[2 * k] = (z & 1ull) ? -h : h;
+        v[2 * k + 1] = (z & 2ull) ? -h : h;
+    }
+    const long blk = (long)rhs * g.nf + f;
+    SC *o = reinterpret_cast<SC *>(out) + blk * Traits<PREC>::SCHUNKS * (long)g.Vh;
+    store_spinor<PREC>(o, norm ? norm + blk * g.Vh : nullptr, cb, g.Vh, v);
+}
+
 static Geo geo_of(const tm_gauge *g, int nrhs)
 {
     Geo G;
@@ -211,6 +250,18 @@ cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, cons
         else TM_U(P16, float2);
     }
 #undef TM_U
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise_z2(const tm_gauge *g, const tm_field *f, int parity, unsigned long long seed, cudaStream_t s)
+{
+    Geo G = geo_of(g, f->nrhs);
+    const long n = (long)G.Vh * G.nf * G.nrhs;
+    const int block = 128;
+    const long grid = (n + block - 1) / block;
+    if (f->prec == TM_PREC_F64) k_noise_z2<P64><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
+    else if (f->prec == TM_PREC_F32) k_noise_z2<P32><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
+    else k_noise_z2<P16><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
     return cudaGetLastError();
 }
 

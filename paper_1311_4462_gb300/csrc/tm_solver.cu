@@ -363,3 +363,377 @@ tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double
 }
 
 }  // extern "C"
+
+// ============================================================================ multi-RHS CG
+// All right-hand sides iterate together (one multi-RHS operator launch per factor, one BLAS
+// launch per step with one column per source, per-source alpha/beta/|r|^2 in the scalar
+// table).  Reliable updates are taken for all active sources at once when any source asks
+// for one; a source whose FP64 true residual meets the tolerance is dropped from the active
+// list, so later launches skip it.  With use_graph the sloppy iteration is captured once per
+// active-set size as a CUDA graph on an internal stream and replayed.
+namespace tmk {
+
+static size_t multi_workspace_need(const tm_gauge *g, const tm_solver_params *sp, int nrhs)
+{
+    size_t need = 0, d, n;
+    const int ps = sp->solver == TM_SOLVER_MIXED_CG ? sp->sloppy_prec : TM_PREC_F64;
+    const int px = sp->solver == TM_SOLVER_MIXED_CG ? TM_PREC_F32 : TM_PREC_F64;
+    tm_field_bytes(g, TM_PREC_F64, nrhs, &d, &n);
+    need += 5 * align256(d);
+    tm_field_bytes(g, ps, nrhs, &d, &n);
+    need += 5 * (align256(d) + align256(n));
+    tm_field_bytes(g, px, nrhs, &d, &n);
+    need += align256(d) + align256(n);
+    need += 2 * align256(TM_MAX_RHS * sizeof(int));
+    return need;
+}
+
+struct MultiCarve {
+    char *base;
+    size_t off;
+    tm_field take(const tm_gauge *g, int prec, int nrhs)
+    {
+        tm_field f;
+        memset(&f, 0, sizeof(f));
+        size_t d, n;
+        tm_field_bytes(g, prec, nrhs, &d, &n);
+        f.prec = prec;
+        f.nrhs = nrhs;
+        f.data = base + off;
+        off += align256(d);
+        if (n) {
+            f.norm = reinterpret_cast<float *>(base + off);
+            off += align256(n);
+        }
+        return f;
+    }
+    int *ints()
+    {
+        int *p = reinterpret_cast<int *>(base + off);
+        off += align256(TM_MAX_RHS * sizeof(int));
+        return p;
+    }
+};
+
+class MultiSolver {
+  public:
+    const tm_gauge *g;
+    const tm_solver_params *sp;
+    cudaStream_t s;
+    int nrhs;
+    double *S, *H;
+    int *d_list, *d_mask, *h_ints;  // device active list / mask, pinned host staging
+
+    tm_status site(int op, FieldRef A, FieldRef B, FieldRef C, FieldRef D, SVal ca, SVal cb, int reduce, int fin,
+                   int slot, bool masked = true)
+    {
+        SiteOpArgs a;
+        memset(&a, 0, sizeof(a));
+        a.op = op;
+        a.reduce = reduce;
+        a.A = A;
+        a.B = B;
+        a.C = C;
+        a.D = D;
+        a.ca = ca;
+        a.cb = cb;
+        a.red.scalars = S;
+        a.red.fin = fin;
+        a.red.slot = slot;
+        a.red.active = masked ? d_mask : nullptr;
+        return cuda_check(launch_site_op(g, a, nrhs, s), "site op");
+    }
+    tm_status read_col(int slot, double *out)
+    {
+        tm_status st = cuda_check(
+            cudaMemcpyAsync(H, S + slot * TM_MAX_RHS, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s), "readback");
+        if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "sync");
+        if (st == TM_OK) memcpy(out, H, nrhs * sizeof(double));
+        return st;
+    }
+    // upload the active set: list of indices and a 0/1 mask
+    tm_status set_active(const bool *act, int *nact)
+    {
+        int k = 0;
+        for (int r = 0; r < nrhs; r++)
+            if (act[r]) h_ints[k++] = r;
+        for (int r = 0; r < nrhs; r++) h_ints[TM_MAX_RHS + r] = act[r] ? 1 : 0;
+        *nact = k;
+        tm_status st = cuda_check(cudaMemcpyAsync(d_list, h_ints, TM_MAX_RHS * sizeof(int), cudaMemcpyHostToDevice, s),
+                                  "active list");
+        if (st == TM_OK)
+            st = cuda_check(cudaMemcpyAsync(d_mask, h_ints + TM_MAX_RHS, TM_MAX_RHS * sizeof(int),
+                                            cudaMemcpyHostToDevice, s), "active mask");
+        // the staging buffer is reused: wait until both copies have read it
+        if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "sync");
+        return st;
+    }
+    tm_status normal_op(const tm_field *out, const tm_field *in, const tm_field *te, const tm_field *to, int nact)
+    {
+        tm_status st = precond_core(g, te, in, to, sp->pc, sp->dagger, s, d_list, nact);
+        if (st != TM_OK) return st;
+        return precond_core(g, out, te, to, sp->pc, !sp->dagger, s, d_list, nact);
+    }
+};
+
+#define MTRY(x)                      \
+    do {                             \
+        st = (x);                    \
+        if (st != TM_OK) goto mdone; \
+    } while (0)
+
+static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_field *b, const tm_solver_params *sp,
+                             tm_solver_stats *stats, void *ws, cudaStream_t user_stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = x->nrhs;
+    const bool mixed = sp->solver == TM_SOLVER_MIXED_CG;
+    const int ps = mixed ? sp->sloppy_prec : TM_PREC_F64;
+    const int px = mixed ? TM_PREC_F32 : TM_PREC_F64;
+    MultiCarve c{reinterpret_cast<char *>(ws), 0};
+    tm_field r = c.take(g, TM_PREC_F64, nrhs), Ap = c.take(g, TM_PREC_F64, nrhs), te = c.take(g, TM_PREC_F64, nrhs);
+    tm_field to = c.take(g, TM_PREC_F64, nrhs), bh = c.take(g, TM_PREC_F64, nrhs);
+    tm_field rs = c.take(g, ps, nrhs), pp = c.take(g, ps, nrhs), Aps = c.take(g, ps, nrhs);
+    tm_field tes = c.take(g, ps, nrhs), tos = c.take(g, ps, nrhs), xs = c.take(g, px, nrhs);
+    MultiSolver V;
+    V.g = g;
+    V.sp = sp;
+    V.nrhs = nrhs;
+    V.S = g->scratch;
+    V.H = g->host_scalars;
+    V.h_ints = reinterpret_cast<int *>(g->host_scalars + 256);
+    V.d_list = c.ints();
+    V.d_mask = c.ints();
+    // work on a private stream (graph capture needs one), ordered after the caller's work
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_nact = -1;
+    tm_status st = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+    if (st != TM_OK) return st;
+    V.s = s;
+    double bb[TM_MAX_RHS], r2[TM_MAX_RHS], rr[TM_MAX_RHS], maxr[TM_MAX_RHS];
+    bool act[TM_MAX_RHS];
+    int conv_it[TM_MAX_RHS], nact = 0, it = 0, nrel = 0;
+    const double tol2 = sp->tol * sp->tol;
+    const double delta = mixed ? sp->delta : 0.0;
+    const tm_field *bhat = b;
+    for (int k = 0; k < nrhs; k++) {
+        act[k] = true;
+        conv_it[k] = -1;
+    }
+    MTRY(cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event"));
+    MTRY(cuda_check(cudaEventRecord(ev, user_stream), "event"));
+    MTRY(cuda_check(cudaStreamWaitEvent(s, ev, 0), "event wait"));
+    MTRY(V.set_active(act, &nact));
+    if (sp->solution == TM_SOLUTION_MAT) {
+        MTRY(precond_core(g, &bh, b, &to, sp->pc, !sp->dagger, s, V.d_list, nact));  // bhat = A^dag b
+        bhat = &bh;
+    }
+    MTRY(V.site(OP_NORM, fref(bhat), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP0, false));
+    MTRY(V.read_col(SL_TMP0, bb));
+    for (int k = 0; k < nrhs; k++) {
+        if (!isfinite(bb[k])) { set_error("tm_solve_multi: non-finite source %d", k); st = TM_ERR_NAN; goto mdone; }
+        act[k] = bb[k] > 0.0;
+    }
+    // x = 0 (or the given guess), r = bhat - A^dag A x
+    if (sp->use_x0) {
+        MTRY(V.set_active(act, &nact));
+        if (nact) MTRY(V.normal_op(&Ap, x, &te, &to, nact));
+        MTRY(V.site(OP_AXPBY, fref(bhat), fref(&Ap), fref(&r), fnone(), sv(1.0), sv(-1.0), 1, FIN_STORE, SL_TMP0,
+                    false));
+    } else {
+        size_t d, n;
+        tm_field_bytes(g, TM_PREC_F64, nrhs, &d, &n);
+        MTRY(cuda_check(cudaMemsetAsync(x->data, 0, d, s), "memset"));
+        MTRY(V.site(OP_COPY, fref(bhat), fnone(), fref(&r), fnone(), sv(1), sv(0), 0, 0, 0, false));
+        MTRY(V.site(OP_NORM, fref(&r), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP0, false));
+    }
+    MTRY(V.read_col(SL_TMP0, r2));
+    for (int k = 0; k < nrhs; k++) {
+        if (act[k] && r2[k] <= tol2 * bb[k]) {
+            act[k] = false;
+            conv_it[k] = 0;
+        }
+        maxr[k] = sqrt(r2[k]);
+    }
+    MTRY(V.set_active(act, &nact));
+    if (nact) {
+        {
+            size_t d, n;
+            tm_field_bytes(g, px, nrhs, &d, &n);
+            MTRY(cuda_check(cudaMemsetAsync(xs.data, 0, d, s), "memset"));
+        }
+        MTRY(V.site(OP_COPY, fref(&r), fnone(), fref(&rs), fnone(), sv(1), sv(0), 0, 0, 0));
+        MTRY(V.site(OP_COPY, fref(&rs), fnone(), fref(&pp), fnone(), sv(1), sv(0), 0, 0, 0));
+        MTRY(V.site(OP_NORM, fref(&rs), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_RR));
+    }
+    while (nact > 0 && it < sp->maxiter) {
+        // ---- sloppy iteration (optionally one replayed graph): Ap = A p, alpha, x += a p, r -= a Ap, |r|^2
+        if (sp->use_graph) {
+            if (graph_nact != nact) {
+                if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+                if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+                MTRY(cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture"));
+                tm_status cst = V.normal_op(&Aps, &pp, &tes, &tos, nact);
+                if (cst == TM_OK)
+                    cst = V.site(OP_DOT, fref(&pp), fref(&Aps), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0);
+                if (cst == TM_OK)
+                    cst = V.site(OP_CG_UPDATE, fref(&pp), fref(&rs), fref(&xs), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0),
+                                 1, FIN_STORE, SL_RRNEW);
+                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                MTRY(cst);
+                MTRY(cuda_check(ce, "end capture"));
+                MTRY(cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "graph instantiate"));
+                graph_nact = nact;
+            }
+            MTRY(cuda_check(cudaGraphLaunch(gexec, s), "graph launch"));
+        } else {
+            MTRY(V.normal_op(&Aps, &pp, &tes, &tos, nact));
+            MTRY(V.site(OP_DOT, fref(&pp), fref(&Aps), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0));
+            MTRY(V.site(OP_CG_UPDATE, fref(&pp), fref(&rs), fref(&xs), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
+                        FIN_STORE, SL_RRNEW));
+        }
+        MTRY(V.read_col(SL_RRNEW, rr));
+        it++;
+        bool update = (it == sp->maxiter);
+        for (int k = 0; k < nrhs; k++) {
+            if (!act[k]) continue;
+            if (!isfinite(rr[k])) {
+                set_error("tm_solve_multi: non-finite residual for source %d at iteration %d", k, it);
+                st = TM_ERR_NAN;
+                goto mdone;
+            }
+            const double rn = sqrt(rr[k]);
+            if (rn > maxr[k]) maxr[k] = rn;
+            if (rn < delta * maxr[k] || rr[k] <= tol2 * bb[k]) update = true;
+        }
+        if (update) {
+            // fold the sloppy solutions of every active source into x, true residual in FP64
+            MTRY(V.site(OP_AXPBY, fref(&xs), fref(x), fref(x), fnone(), sv(1.0), sv(1.0), 0, 0, 0));
+            MTRY(V.site(OP_AXPBY, fref(&xs), fnone(), fref(&xs), fnone(), sv(0.0), sv(0.0), 0, 0, 0));
+            MTRY(V.normal_op(&Ap, x, &te, &to, nact));
+            MTRY(V.site(OP_AXPBY, fref(bhat), fref(&Ap), fref(&r), fnone(), sv(1.0), sv(-1.0), 1, FIN_STORE,
+                        SL_TMP0));
+            MTRY(V.read_col(SL_TMP0, r2));
+            nrel++;
+            bool changed = false;
+            for (int k = 0; k < nrhs; k++) {
+                if (!act[k]) continue;
+                if (r2[k] <= tol2 * bb[k]) {
+                    act[k] = false;
+                    conv_it[k] = it;
+                    changed = true;
+                }
+                maxr[k] = sqrt(r2[k]);
+            }
+            if (changed) MTRY(V.set_active(act, &nact));
+            if (nact == 0) break;
+            MTRY(V.site(OP_COPY, fref(&r), fnone(), fref(&rs), fnone(), sv(1), sv(0), 0, 0, 0));
+            MTRY(V.site(OP_NORM, fref(&rs), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_RRNEW));
+        }
+        k_scalar_beta<<<1, TM_MAX_RHS, 0, s>>>(V.S, nrhs, V.d_mask);
+        MTRY(cuda_check(cudaGetLastError(), "beta"));
+        MTRY(V.site(OP_AXPBY, fref(&rs), fref(&pp), fref(&pp), fnone(), sv(1.0), sslot(SL_BETA, 1.0), 0, 0, 0));
+    }
+    if (nact > 0) {
+        set_error("tm_solve_multi: %d source(s) not converged after %d iterations", nact, it);
+        st = TM_ERR_NOCONV;
+    }
+mdone:
+    if (stats) {
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int k = 0; k < nrhs; k++) {
+            stats[k].iterations = conv_it[k] >= 0 ? conv_it[k] : it;
+            stats[k].reliable_updates = nrel;
+            stats[k].true_residual = bb[k] > 0 ? sqrt(r2[k] / bb[k]) : 0.0;
+            stats[k].pc_residual = -1.0;
+            stats[k].seconds = secs;
+        }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (s) {
+        cudaEvent_t done = nullptr;
+        if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(done, s);
+            cudaStreamWaitEvent(user_stream, done, 0);
+            cudaEventDestroy(done);
+        }
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    if (ev) cudaEventDestroy(ev);
+    return st;
+}
+
+}  // namespace tmk
+
+extern "C" {
+
+tm_status tm_g5dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, double *im_out,
+                   void *stream)
+{
+    if (!g || !a || !b || !a->data || !b->data || !re_out || !im_out) { set_error("tm_g5dot: null argument"); return TM_ERR_ARG; }
+    if (a->nrhs != b->nrhs || a->nrhs < 1 || a->nrhs > TM_MAX_RHS) {
+        set_error("tm_g5dot: fields must share nrhs in [1, %d]", TM_MAX_RHS);
+        return TM_ERR_ARG;
+    }
+    if ((a->prec == TM_PREC_F16 && !a->norm) || (b->prec == TM_PREC_F16 && !b->norm)) {
+        set_error("tm_g5dot: FP16 field needs its norm array");
+        return TM_ERR_ARG;
+    }
+    MultiSolver V;
+    V.g = g;
+    V.sp = nullptr;
+    V.s = (cudaStream_t)stream;
+    V.nrhs = a->nrhs;
+    V.S = g->scratch;
+    V.H = g->host_scalars;
+    V.d_mask = nullptr;
+    tm_status st = V.site(OP_G5DOT_RE, fref(a), fref(b), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP0, false);
+    if (st == TM_OK) st = V.read_col(SL_TMP0, re_out);
+    if (st == TM_OK) st = V.site(OP_G5DOT_IM, fref(a), fref(b), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP0, false);
+    if (st == TM_OK) st = V.read_col(SL_TMP0, im_out);
+    return st;
+}
+
+tm_status tm_solve_multi_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp, int nrhs, size_t *bytes)
+{
+    tm_status st = check_solver_params(g, sp);
+    if (st != TM_OK) return st;
+    if (!bytes || nrhs < 1 || nrhs > TM_MAX_RHS) {
+        set_error("tm_solve_multi_workspace_bytes: need 1 <= nrhs <= %d", TM_MAX_RHS);
+        return TM_ERR_ARG;
+    }
+    *bytes = multi_workspace_need(g, sp, nrhs);
+    return TM_OK;
+}
+
+tm_status tm_solve_multi(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
+                         tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream)
+{
+    tm_status st = check_solver_params(g, sp);
+    if (st != TM_OK) return st;
+    if (!x_e || !b_e || !workspace || !x_e->data || !b_e->data) {
+        set_error("tm_solve_multi: null field or workspace");
+        return TM_ERR_ARG;
+    }
+    if (x_e->prec != TM_PREC_F64 || b_e->prec != TM_PREC_F64 || x_e->nrhs != b_e->nrhs || x_e->nrhs < 1 ||
+        x_e->nrhs > TM_MAX_RHS) {
+        set_error("tm_solve_multi: x and b must be FP64 fields with the same nrhs in [1, %d]", TM_MAX_RHS);
+        return TM_ERR_ARG;
+    }
+    if (x_e->data == b_e->data) { set_error("tm_solve_multi: x must not alias b"); return TM_ERR_ARG; }
+    if (((uintptr_t)workspace & 255) != 0) { set_error("tm_solve_multi: workspace must be 256-byte aligned"); return TM_ERR_ARG; }
+    const size_t need = multi_workspace_need(g, sp, x_e->nrhs);
+    if (workspace_bytes < need) {
+        set_error("tm_solve_multi: workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, need);
+        return TM_ERR_NOMEM;
+    }
+    if (stats) memset(stats, 0, sizeof(*stats) * x_e->nrhs);
+    return solve_multi(g, x_e, b_e, sp, stats, workspace, (cudaStream_t)stream);
+}
+
+}  // extern "C"

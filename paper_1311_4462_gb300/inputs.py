@@ -98,6 +98,39 @@ def z2_noise(L, nf: int, seed: int) -> np.ndarray:
     return (re + 1j * im) / np.sqrt(2.0)
 
 
+# Counter-based Z2 noise: element i (flat index into the canonical array) of source `seed`
+# takes its two sign bits from SplitMix64's output function (Steele, Lea & Flood, "Fast
+# splittable pseudorandom number generators", OOPSLA 2014) applied to the counter
+# state = (seed + 1) * G + (i + 1) * G, G = 0x9E3779B97F4A7C15 (mod 2^64): bit 0 -> sign of the
+# real part, bit 1 -> sign of the imaginary part.  The library implements the same definition
+# on the device (tm_noise_z2), so large batches of sources need not cross the host link.
+_SM_G = np.uint64(0x9E3779B97F4A7C15)
+_SM_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_SM_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(state: np.ndarray) -> np.ndarray:
+    z = state.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _SM_M1
+        z = (z ^ (z >> np.uint64(27))) * _SM_M2
+    return z ^ (z >> np.uint64(31))
+
+
+def z2_noise_counter(L, nf: int, seed: int) -> np.ndarray:
+    Lx, Ly, Lz, Lt = L
+    shape = (Lt, Lz, Ly, Lx, nf, 4, 3)
+    n = int(np.prod(shape))
+    with np.errstate(over="ignore"):
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        state = np.uint64(seed + 1) * _SM_G + i * _SM_G
+    z = splitmix64(state)
+    re = 1.0 - 2.0 * (z & np.uint64(1)).astype(np.float64)
+    im = 1.0 - 2.0 * ((z >> np.uint64(1)) & np.uint64(1)).astype(np.float64)
+    h = 0.70710678118654752440  # 1/sqrt(2), the double nearest the exact value (same literal on the device)
+    return ((re + 1j * im) * h).reshape(shape)
+
+
 def gauge_transform(L, seed: int) -> np.ndarray:
     """Random SU(3) matrix per site, [Lt, Lz, Ly, Lx, 3, 3] (for gauge-covariance checks)."""
     Lx, Ly, Lz, Lt = L
