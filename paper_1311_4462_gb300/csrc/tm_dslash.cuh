@@ -327,19 +327,24 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__
     dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
 }
 
-// Several right-hand sides in one launch (multi-RHS, sources share the gauge field): thread
-// t handles site t / nact of right-hand side act[t % nact] (act = NULL: rhs = t % nact).  The
-// right-hand sides of a site sit in consecutive lanes, so their identical link loads are one
-// request per warp: each link leaves memory once per site for all nact sources.
+// Several right-hand sides in one launch (multi-RHS, sources share the gauge field).  A block
+// of 128 threads is 32 consecutive sites x 4 right-hand sides, one warp per right-hand side, so
+// every spinor load of a warp is one contiguous 512-byte request and the four warps of a block
+// read the same links (served from L1 after the first); consecutive blocks take the next group
+// of four right-hand sides of the same 32 sites, so the remaining link reads hit L2 and each
+// link leaves DRAM about once per site for all sources.  Slot k of the active set is
+// right-hand side act[k] (act = NULL: k).
 template <int PREC, int NF, int RECON, bool PRO>
 __global__ void __launch_bounds__(128, 4)
     k_dslash_multi(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act, int nact,
                    int nrhs)
 {
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long cb = tid / nact;
-    if (cb >= a.Vh) return;
-    const int slot = (int)(tid - cb * nact);
+    const int ngrp = (nact + 3) >> 2;
+    const int grp = (int)(blockIdx.x % ngrp);
+    const long sblk = blockIdx.x / ngrp;
+    const int slot = grp * 4 + (threadIdx.x >> 5);
+    const long cb = sblk * 32 + (threadIdx.x & 31);
+    if (slot >= nact || cb >= a.Vh) return;
     const int rhs = act ? __ldg(act + slot) : slot;
     if (rhs < 0 || rhs >= nrhs) return;  // an index outside the fields is skipped, never dereferenced
     dslash_body<PREC, NF, RECON, PRO>(a, (int)cb, rhs);
@@ -349,8 +354,7 @@ template <int PREC>
 cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                      const int *act, int nact, int nrhs, cudaStream_t s)
 {
-    const long threads = (long)a.Vh * nact;
-    const unsigned grid = (unsigned)((threads + 127) / 128);
+    const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + 3) / 4));
 #define TM_M(NF, R, P) k_dslash_multi<PREC, NF, R, P><<<grid, 128, 0, s>>>(a, act, nact, nrhs)
 #define TM_MR(NF, P)                        \
     switch (recon) {                        \

@@ -536,6 +536,7 @@ static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_fiel
     for (int k = 0; k < nrhs; k++) {
         if (!isfinite(bb[k])) { set_error("tm_solve_multi: non-finite source %d", k); st = TM_ERR_NAN; goto mdone; }
         act[k] = bb[k] > 0.0;
+        if (!act[k]) conv_it[k] = 0;  // a zero source has the zero solution
     }
     // x = 0 (or the given guess), r = bhat - A^dag A x
     if (sp->use_x0) {
