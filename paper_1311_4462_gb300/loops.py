@@ -37,7 +37,7 @@ def g5_trace(gauge, nsources=256, batch=16, seed0=3000, tol=1e-8, solver="mixed"
         t_solve += time.time() - t0
         vals.extend(list(g5dot(gauge, ee, xe) + g5dot(gauge, eo, xo)))
         iters.extend(s["iterations"] for s in stats)
-        if return_solutions:
+        if return_solutions and b0 == 0:  # the first batch only (a 32^3x64 batch of 16 is 6.4 GB)
             sols.append((xe, xo))
     v = np.array(vals)
     out = {"estimate": complex(v.mean()), "stderr": float(np.sqrt(v.real.var(ddof=1) + v.imag.var(ddof=1))
