@@ -29,7 +29,8 @@
  * Field storage (tm_field): one parity of a spinor field in structure-of-arrays form,
  *   data: [nrhs][nf][chunk][Vh] with the 24 reals of a site, ordered (spin*3 + colour)*2 + re/im,
  *         cut into 16-byte chunks (FP64: 12, FP32: 6, FP16: 3 chunks per site and flavour);
- *   norm: FP16 only, float [nrhs][nf][Vh], the site's max |real| (stored half = value / norm).
+ *   norm: FP16 only, float [nrhs][nf][Vh], the site's max |real| (stored half = value / norm);
+ *   DF64: 12 chunks per site and flavour, each (hi, lo, hi, lo) of two consecutive reals.
  * Vh = Lx Ly Lz Lt / 2; even sites have (x+y+z+t) even; site index within a parity is
  * (x + Lx (y + Ly (z + Lz t))) / 2.  tm_field_bytes() gives the sizes to allocate.
  *
@@ -57,8 +58,12 @@ typedef enum {
 
 /* twist_flavor (sec. 2.2): one flavour with tau3 = +1 / -1, or the two-flavour doublet. */
 typedef enum { TM_TWIST_PLUS = 1, TM_TWIST_MINUS = -1, TM_NDEG_DOUBLET = 2 } tm_flavor;
-/* storage precision: bytes per real; FP16 carries a per-site float norm, arithmetic is FP32. */
-typedef enum { TM_PREC_F64 = 8, TM_PREC_F32 = 4, TM_PREC_F16 = 2 } tm_prec;
+/* storage precision.  F64/F32/F16: value = bytes per real; FP16 carries a per-site float norm and
+ * computes in FP32.  DF64: each real is a pair of floats hi + lo (8 bytes, 48-bit significand,
+ * relative rounding ~3.6e-15) computed with error-free float transformations -- double-precision
+ * class accuracy at FP32-pipe throughput, which GB300 issues far faster than FP64.  DF64 links
+ * use 18 or 12 reals (recon 8 handles keep 12 for their DF64 copy). */
+typedef enum { TM_PREC_F64 = 8, TM_PREC_F32 = 4, TM_PREC_F16 = 2, TM_PREC_DF64 = 16 } tm_prec;
 /* gauge link storage (sec. 3): 18 reals, 2 rows (12 reals), or 8 reals. */
 typedef enum { TM_RECON_18 = 18, TM_RECON_12 = 12, TM_RECON_8 = 8 } tm_recon;
 /* even-odd preconditioning: asymmetric (eq. 2.2) or symmetric (eq. 2.3). */
@@ -97,7 +102,7 @@ typedef struct {
     int nrhs;    /* right-hand sides stored back to back (1 for single fields) */
 } tm_field;
 
-typedef struct tm_gauge tm_gauge; /* opaque: packed links in FP64, FP32 and FP16 + scratch */
+typedef struct tm_gauge tm_gauge; /* opaque: packed links in FP64, FP32, FP16, DF64 + scratch */
 
 /* Library version string. */
 const char *tm_version(void);
@@ -187,7 +192,8 @@ tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o
  *   SYM:   b'_e = R_ee^-1 (b_e + kappa H_eo R_oo^-1 b_o)
  * dagger = 1 daggers every factor (source of M^dag psi = b).  For SYM with dagger = 1 the
  * system is preconditioned from the right, M_sym^dag y = b'_e with b'_e as for ASYM, and
- * psi_e = R_ee^-dag y.  One fused launch (input twist in the prologue).
+ * psi_e = R_ee^-dag y.  One fused launch (input twist in the prologue).  FP64/FP32/FP16 fields
+ * (DF64 is not offered here: the right-hand side is prepared once, in FP64).
  */
 tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_field *b_e, const tm_field *b_o,
                          int pc, int dagger, void *stream);
@@ -225,6 +231,9 @@ typedef struct {
     int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
     int use_x0;      /* 1: x_e holds the initial guess on entry; 0: start from zero */
     int want_pc_residual; /* 1: also compute stats->pc_residual (one more FP64 operator application) */
+    int true_prec;   /* TM_PREC_F64 (default, 0 means F64) or TM_PREC_DF64: precision of the solution
+                        accumulation, the true residual and (plain CG) the whole iteration; x and b
+                        stay FP64 fields either way */
     int use_graph;   /* tm_solve_multi: capture the sloppy iteration as a CUDA graph and replay it */
 } tm_solver_params;
 
@@ -295,14 +304,15 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
 
 /* ---------------------------------------------------------------------------- autotuning */
 /*
- * Time every launch choice of the hopping kernel (thread-per-site or, for the doublet,
- * thread-per-site-and-flavour; 64-256 threads per block) for each precision, with and without
+ * Time every launch choice of the hopping kernel (thread per site with 64-256 threads per block,
+ * the same with a two-stage load pipeline, or with a 128-register cap) for each precision, with and without
  * the input-twist prologue, on this handle's lattice, and keep the fastest.  Allocates three
  * scratch fields for the duration of the call and synchronises `stream`; do not call it while
  * capturing a graph.  Until it runs (or a table is imported) the handle uses defaults.
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);
-/* The tuned table as text ("f32:0:1:128 ..." = precision:prologue:variant:block), and back. */
+/* The tuned table as text ("f32:0:3:128 ..." = precision:prologue:variant:block; variant 0 plain,
+ * 2 pipelined, 3 register-capped), and back. */
 tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n);
 tm_status tm_tune_import(tm_gauge *g, const char *text);
 

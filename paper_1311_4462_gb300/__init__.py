@@ -11,9 +11,9 @@ import ctypes
 from . import _lib as L
 from ._lib import (TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT, TM_SOLVER_CG, TM_SOLVER_MIXED, TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM,
                    TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_NDEG_DOUBLET, TM_PC_ASYM, TM_PC_SYM, TM_PREC_F16, TM_PREC_F32,
-                   TM_PREC_F64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
+                   TM_PREC_F64, TM_PREC_DF64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
 
-PRECS = {"f64": TM_PREC_F64, "f32": TM_PREC_F32, "f16": TM_PREC_F16}
+PRECS = {"f64": TM_PREC_F64, "f32": TM_PREC_F32, "f16": TM_PREC_F16, "df64": TM_PREC_DF64}
 
 
 def _torch():
@@ -212,7 +212,8 @@ DEFAULT_DELTA = {TM_PREC_F16: 1e-2, TM_PREC_F32: 1e-3}
 
 
 def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000,
-                  delta=None, sloppy_prec=TM_PREC_F32, use_x0=False, want_pc_residual=False, use_graph=False):
+                  delta=None, sloppy_prec=TM_PREC_F32, use_x0=False, want_pc_residual=False, use_graph=False,
+                  true_prec=TM_PREC_F64):
     sp = L.tm_solver_params()
     sp.solver = TM_SOLVER_MIXED if solver == "mixed" else TM_SOLVER_CG
     sp.solution, sp.pc, sp.dagger = int(solution), int(pc), int(dagger)
@@ -220,6 +221,7 @@ def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=F
     sp.delta = float(delta if delta is not None else DEFAULT_DELTA.get(int(sloppy_prec), 0.1))
     sp.sloppy_prec, sp.use_x0, sp.want_pc_residual = int(sloppy_prec), int(use_x0), int(want_pc_residual)
     sp.use_graph = int(use_graph)
+    sp.true_prec = int(true_prec)
     return sp
 
 

@@ -11,7 +11,7 @@ TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOCONV, TM_ERR_NAN, TM_ERR_TIMEOUT, TM_ER
 STATUS_NAMES = {0: "TM_OK", -1: "TM_ERR_ARG", -2: "TM_ERR_CUDA", -3: "TM_ERR_NOCONV", -4: "TM_ERR_NAN",
                 -5: "TM_ERR_TIMEOUT", -6: "TM_ERR_NOMEM"}
 TM_TWIST_PLUS, TM_TWIST_MINUS, TM_NDEG_DOUBLET = 1, -1, 2
-TM_PREC_F64, TM_PREC_F32, TM_PREC_F16 = 8, 4, 2
+TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64 = 8, 4, 2, 16
 TM_PC_ASYM, TM_PC_SYM = 0, 1
 TM_C128, TM_C64 = 0, 1
 TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_EPI_TWINV_XPAY = range(6)
@@ -33,7 +33,7 @@ class tm_solver_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("solution", ctypes.c_int), ("pc", ctypes.c_int), ("dagger", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("delta", ctypes.c_double),
                 ("sloppy_prec", ctypes.c_int), ("use_x0", ctypes.c_int), ("want_pc_residual", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("true_prec", ctypes.c_int)]
 
 
 class tm_solver_stats(ctypes.Structure):

@@ -16,6 +16,30 @@ cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, boo
                               cudaStream_t s);
 cudaError_t launch_dslash_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, int variant, int block,
                               cudaStream_t s);
+#define TM_DF_DECL(NF, R)                                                                                    \
+    cudaError_t launch_dslash_pdf_nf##NF##_r##R(const DslashArgs<df64> &a, int block, cudaStream_t s);                 \
+    cudaError_t launch_dslash_multi_pdf_nf##NF##_r##R(const DslashArgs<df64> &a, const int *act, int nact, int nrhs, \
+                                                      cudaStream_t s);
+TM_DF_DECL(1, 18)
+TM_DF_DECL(1, 12)
+TM_DF_DECL(2, 18)
+TM_DF_DECL(2, 12)
+#undef TM_DF_DECL
+
+static cudaError_t launch_dslash_pdf(const DslashArgs<df64> &a, int nf, int recon, int block, cudaStream_t s)
+{
+    if (nf == 1) return recon == 18 ? launch_dslash_pdf_nf1_r18(a, block, s) : launch_dslash_pdf_nf1_r12(a, block, s);
+    return recon == 18 ? launch_dslash_pdf_nf2_r18(a, block, s) : launch_dslash_pdf_nf2_r12(a, block, s);
+}
+static cudaError_t launch_dslash_multi_pdf(const DslashArgs<df64> &a, int nf, int recon, const int *act, int nact,
+                                           int nrhs, cudaStream_t s)
+{
+    if (nf == 1)
+        return recon == 18 ? launch_dslash_multi_pdf_nf1_r18(a, act, nact, nrhs, s)
+                           : launch_dslash_multi_pdf_nf1_r12(a, act, nact, nrhs, s);
+    return recon == 18 ? launch_dslash_multi_pdf_nf2_r18(a, act, nact, nrhs, s)
+                       : launch_dslash_multi_pdf_nf2_r12(a, act, nact, nrhs, s);
+}
 cudaError_t launch_dslash_multi_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, const int *act, int nact,
                                     int nrhs, cudaStream_t s);
 cudaError_t launch_dslash_multi_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
@@ -30,6 +54,8 @@ cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void
 cudaError_t launch_noise_z2(const tm_gauge *g, const tm_field *f, int parity, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
                          cudaStream_t s);
+cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
+                                const int *act, int nact, cudaStream_t s);
 
 static thread_local char g_err[512];
 constexpr int TM_MAX_RHS_API = 64;
@@ -55,21 +81,24 @@ int prec_index(int prec)
     case TM_PREC_F64: return 0;
     case TM_PREC_F32: return 1;
     case TM_PREC_F16: return 2;
+    case TM_PREC_DF64: return 3;
     default: return -1;
     }
 }
 
-int spinor_chunks(int prec) { return prec == TM_PREC_F64 ? 12 : (prec == TM_PREC_F32 ? 6 : 3); }
+size_t real_bytes(int prec) { return prec == TM_PREC_DF64 ? 8 : (size_t)prec; }
+
+int spinor_chunks(int prec) { return (prec == TM_PREC_F64 || prec == TM_PREC_DF64) ? 12 : (prec == TM_PREC_F32 ? 6 : 3); }
 size_t chunk_bytes(int) { return 16; }
 
 static int link_reals_per_chunk(int prec, int recon)
 {
     // chunk geometry of LinkLayout<PREC, RECON> in tm_core.cuh
-    if (prec == TM_PREC_F64) return 2;
+    if (prec == TM_PREC_F64 || prec == TM_PREC_DF64) return 2;
     if (prec == TM_PREC_F32) return recon == 18 ? 2 : 4;
     return recon == 18 ? 2 : (recon == 12 ? 4 : 8);
 }
-static size_t link_chunk_bytes(int prec, int recon) { return (size_t)link_reals_per_chunk(prec, recon) * prec; }
+static size_t link_chunk_bytes(int prec, int recon) { return (size_t)link_reals_per_chunk(prec, recon) * real_bytes(prec); }
 
 // ---------------------------------------------------------------------------- twist tables
 // R = 1 + i a gamma5 tau3 + b tau1 (doublet) or 1 + i a s gamma5 (one flavour, s = +-1), with
@@ -108,6 +137,15 @@ static Twist<double> make_twist(const tm_gauge *g, int kind, int dagger)
         }
     }
     return t;
+}
+
+static Twist<df64> to_df64(const Twist<double> &t)
+{
+    Twist<df64> f;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+            for (int k = 0; k < 2; k++) f.m[i][j][k] = {df64(t.m[i][j][k].r), df64(t.m[i][j][k].i)};
+    return f;
 }
 
 static Twist<float> to_float(const Twist<double> &t)
@@ -211,6 +249,21 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.tw_pro = tp;
         e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s)
                   : launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
+    } else if (pidx == 3) {
+        DslashArgs<df64> a;
+        fill_common(a, g, out, in, x, out_parity, pidx);
+        a.epilogue = epi;
+        a.sigma = df64(dagger ? -1.0 : 1.0);
+        a.coef = df64(coef);
+        a.tw_epi = to_df64(te);
+        a.tw_pro = to_df64(tp);
+        const int r = g->p.recon == 18 ? 18 : 12;
+        if (pro) {
+            set_error("DF64 has no input-twist prologue kernel (the operators apply that twist separately)");
+            return TM_ERR_ARG;
+        }
+        e = multi ? launch_dslash_multi_pdf(a, g->nf, r, act, nact, out->nrhs, s)
+                  : launch_dslash_pdf(a, g->nf, r, 64, s);
     } else {
         DslashArgs<float> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -294,6 +347,12 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
         return dslash_launch(g, out_e, tmp_o, in_e, 0, 0, EPI_X_TWAXPY, -k2, &Ri, nullptr, s, act, nact);
     }
     // adjoint of the symmetric operator: tmp = R^-dag_oo H^dag_oe R^-dag_ee in ; out = in - kappa^2 H^dag_eo tmp
+    if (out_e->prec == TM_PREC_DF64) {
+        // DF64: the input twist as its own launch into out_e (overwritten by the last launch)
+        TM_TRY(cuda_check(launch_twist_active(g, out_e, in_e, Ri, act, nact, s), "twist"));
+        TM_TRY(dslash_launch(g, tmp_o, out_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
+    }
     TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s, act, nact));
     return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
 }
@@ -326,18 +385,18 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     const long V = (long)p->L[0] * p->L[1] * p->L[2] * p->L[3];
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 4; i++)
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
     cudaStream_t s = (cudaStream_t)stream;
     tm_status st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
     if (st == TM_OK) st = cuda_check(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
                                      "cudaDeviceGetAttribute");
-    const int precs[3] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16};
-    for (int i = 0; i < 3 && st == TM_OK; i++) {
-        const int nreal = p->recon;
-        const size_t per_link = (size_t)nreal * precs[i];
-        const size_t chunks = per_link / link_chunk_bytes(precs[i], p->recon);
-        g->link_bytes[i] = 8ull * g->Vh * chunks * link_chunk_bytes(precs[i], p->recon);
+    const int precs[4] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64};
+    for (int i = 0; i < 4 && st == TM_OK; i++) {
+        const int recon_i = (precs[i] == TM_PREC_DF64 && p->recon == 8) ? 12 : p->recon;
+        const size_t per_link = (size_t)recon_i * real_bytes(precs[i]);
+        const size_t chunks = per_link / link_chunk_bytes(precs[i], recon_i);
+        g->link_bytes[i] = 8ull * g->Vh * chunks * link_chunk_bytes(precs[i], recon_i);
         if (cudaMalloc(&g->links[i], g->link_bytes[i]) != cudaSuccess) {
             set_error("tm_gauge_create: cudaMalloc of %zu bytes failed", g->link_bytes[i]);
             st = TM_ERR_NOMEM;
@@ -371,7 +430,7 @@ tm_status tm_gauge_destroy(tm_gauge *g)
 {
     if (!g) return TM_OK;
     cudaDeviceSynchronize();
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 4; i++)
         if (g->links[i]) cudaFree(g->links[i]);
     if (g->scratch) cudaFree(g->scratch);
     if (g->host_scalars) cudaFreeHost(g->host_scalars);
@@ -384,7 +443,7 @@ tm_status tm_field_bytes(const tm_gauge *g, int prec, int nrhs, size_t *data_byt
     if (!g || !data_bytes || !norm_bytes) { set_error("tm_field_bytes: null pointer"); return TM_ERR_ARG; }
     if (prec_index(prec) < 0 || nrhs < 1) { set_error("tm_field_bytes: bad prec or nrhs"); return TM_ERR_ARG; }
     const size_t sites = (size_t)g->Vh * g->nf * nrhs;
-    *data_bytes = sites * 24 * (size_t)prec;
+    *data_bytes = sites * 24 * real_bytes(prec);
     *norm_bytes = (prec == TM_PREC_F16) ? sites * sizeof(float) : 0;
     return TM_OK;
 }
@@ -501,6 +560,7 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
     TM_TRY(same_prec(bprime_e, b_o, "tm_prepare_rhs"));
     if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
     if (bprime_e->data == b_o->data) { set_error("tm_prepare_rhs: bprime_e must not alias b_o"); return TM_ERR_ARG; }
+    if (bprime_e->prec == TM_PREC_DF64) { set_error("tm_prepare_rhs: use FP64 fields (no DF64 form)"); return TM_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
     const double k = g->p.kappa;
@@ -554,11 +614,12 @@ tm_status tm_autotune(tm_gauge *g, void *stream)
         for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
             float best = 1e30f;
             tm_tune_entry bestc = g->tune[pi][pro];
-            for (int variant = 0; variant < 7; variant++) {
-                if (pro && (variant == 1 || variant == 2)) continue;  // split and pipeline: no prologue
-                if (variant == 1 && g->nf != 2) continue;  // flavour split needs the doublet
+            const int variants[3] = {0, 2, 3};
+            for (int vi = 0; vi < 3; vi++) {
+                const int variant = variants[vi];
+                if (pro && variant == 2) continue;  // the pipelined form has no prologue
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
-                    if (variant >= 3 && blocks[bi] != 128) continue;  // register-capped forms use 128
+                    if (variant == 3 && blocks[bi] != 128) continue;  // the capped form uses 128
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
                     float ms = 0;
                     for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -619,7 +680,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant > 6 || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || (variant != 0 && variant != 2 && variant != 3) || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

@@ -15,14 +15,15 @@ namespace tmk {
 // ---------------------------------------------------------------------------- twist
 template <int PREC, int NF>
 __global__ void k_twist(void *out, float *out_norm, const void *in, const float *in_norm, int Vh, int nrhs,
-                        Twist<typename Traits<PREC>::real> tw)
+                        Twist<typename Traits<PREC>::real> tw, const int *act, int nact)
 {
     using T = typename Traits<PREC>::real;
     using SC = typename Traits<PREC>::schunk;
     const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (long)Vh * nrhs) return;
+    if (id >= (long)Vh * nact) return;
     const int cb = (int)(id % Vh);
-    const long rhs = id / Vh;
+    const long rhs = act ? (long)__ldg(act + id / Vh) : id / Vh;
+    if (rhs < 0 || rhs >= nrhs) return;
     const long fstride = (long)Traits<PREC>::SCHUNKS * Vh;
     T v[NF][24];
 #pragma unroll
@@ -50,15 +51,19 @@ static Twist<T> cast_twist(const Twist<double> &t)
     return o;
 }
 
-cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
-                         cudaStream_t s)
+cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
+                                const int *act, int nact, cudaStream_t s)
 {
-    const long n = (long)g->Vh * out->nrhs;
+    const long n = (long)g->Vh * nact;
     const int block = 128;
     const long grid = (n + block - 1) / block;
-#define TM_T(P, NF, TT) \
-    k_twist<P, NF><<<grid, block, 0, s>>>(out->data, out->norm, in->data, in->norm, g->Vh, out->nrhs, cast_twist<TT>(tw))
-    if (g->nf == 1) {
+#define TM_T(P, NF, TT)                                                                                          \
+    k_twist<P, NF><<<grid, block, 0, s>>>(out->data, out->norm, in->data, in->norm, g->Vh, out->nrhs, cast_twist<TT>(tw), \
+                                          act, nact)
+    if (in->prec == TM_PREC_DF64) {
+        if (g->nf == 1) TM_T(PDF, 1, df64);
+        else TM_T(PDF, 2, df64);
+    } else if (g->nf == 1) {
         if (in->prec == TM_PREC_F64) TM_T(P64, 1, double);
         else if (in->prec == TM_PREC_F32) TM_T(P32, 1, float);
         else TM_T(P16, 1, float);
@@ -69,6 +74,12 @@ cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field 
     }
 #undef TM_T
     return cudaGetLastError();
+}
+
+cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
+                         cudaStream_t s)
+{
+    return launch_twist_active(g, out, in, tw, nullptr, out->nrhs, s);
 }
 
 // ---------------------------------------------------------------------------- reductions
@@ -233,8 +244,11 @@ __global__ void __launch_bounds__(256) k_site_op(SiteOpArgs a)
 template <int PA, int PB, int PC, int PD>
 static cudaError_t run_combo(const SiteOpArgs &a, dim3 grid, int block, cudaStream_t s)
 {
+    // arithmetic: binary64 if any operand is FP64, double-float if any is DF64, else binary32
     constexpr bool any64 = (PA == P64) || (PB == P64) || (PC == P64) || (PD == P64);
-    if (any64) k_site_op<PA, PB, PC, PD, double><<<grid, block, 0, s>>>(a);
+    constexpr bool anydf = (PA == PDF) || (PB == PDF) || (PC == PDF) || (PD == PDF);
+    if constexpr (any64) k_site_op<PA, PB, PC, PD, double><<<grid, block, 0, s>>>(a);
+    else if constexpr (anydf) k_site_op<PA, PB, PC, PD, df64><<<grid, block, 0, s>>>(a);
     else k_site_op<PA, PB, PC, PD, float><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -253,7 +267,13 @@ static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
     X(P64, P64, P16, P64)     \
     X(P32, P32, P64, P32)     \
     X(P16, P16, P64, P16)     \
-    X(P32, P32, P16, P32)
+    X(P32, P32, P16, P32)     \
+    X(PDF, PDF, PDF, PDF)     \
+    X(P64, P64, PDF, P64)     \
+    X(PDF, PDF, P64, PDF)     \
+    X(P32, PDF, PDF, P32)     \
+    X(PDF, PDF, P32, PDF)     \
+    X(PDF, PDF, P16, PDF)
 
 cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s)
 {

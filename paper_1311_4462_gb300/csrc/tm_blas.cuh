@@ -75,7 +75,7 @@ __device__ __forceinline__ void store_block(const FieldRef &f, long blk, int cb,
     for (int k = 0; k < 24; k++) tmp[k] = (R)v[k];
     SC *p = reinterpret_cast<SC *>(f.data) + blk * Traits<PREC>::SCHUNKS * (long)Vh;
     store_spinor<PREC>(p, f.norm ? f.norm + blk * Vh : nullptr, cb, Vh, tmp);
-    if (PREC == P16) {
+    if constexpr (PREC == P16) {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; k++) m = fmaxf(m, fabsf((float)tmp[k]));

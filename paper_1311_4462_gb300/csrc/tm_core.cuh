@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tm_df64.cuh"
+
 namespace tmk {
 
 template <typename T>
@@ -41,7 +43,8 @@ template <typename T> __device__ __forceinline__ C<T> cscale(T s, C<T> a) { retu
 
 // -------------------------------------------------------------------------------------------------
 // Precision traits.  `real` is the arithmetic type; FP16 storage computes in FP32.
-enum Prec { P64 = 8, P32 = 4, P16 = 2 };
+// PDF: double-float pairs (tm_df64.cuh), 8 bytes per real like P64, arithmetic on the FP32 pipes
+enum Prec { P64 = 8, P32 = 4, P16 = 2, PDF = 16 };
 
 template <int PREC> struct Traits;
 template <> struct Traits<P64> {
@@ -54,6 +57,12 @@ template <> struct Traits<P32> {
     using real = float;
     using schunk = float4;
     static constexpr int SCHUNKS = 6;
+    static constexpr bool NORM = false;
+};
+template <> struct Traits<PDF> {
+    using real = df64;
+    using schunk = float4;    // (hi, lo) of two reals
+    static constexpr int SCHUNKS = 12;
     static constexpr bool NORM = false;
 };
 template <> struct Traits<P16> {
@@ -71,6 +80,8 @@ template <> struct LinkLayout<P64, 8>  { using chunk = double2; static constexpr
 template <> struct LinkLayout<P32, 18> { using chunk = float2; static constexpr int N = 9; };
 template <> struct LinkLayout<P32, 12> { using chunk = float4; static constexpr int N = 3; };
 template <> struct LinkLayout<P32, 8>  { using chunk = float4; static constexpr int N = 2; };
+template <> struct LinkLayout<PDF, 18> { using chunk = float4; static constexpr int N = 9; };
+template <> struct LinkLayout<PDF, 12> { using chunk = float4; static constexpr int N = 6; };
 template <> struct LinkLayout<P16, 18> { using chunk = uint32_t; static constexpr int N = 9; };   // 2 halves
 template <> struct LinkLayout<P16, 12> { using chunk = uint2; static constexpr int N = 3; };      // 4 halves
 template <> struct LinkLayout<P16, 8>  { using chunk = uint4; static constexpr int N = 1; };      // 8 halves
@@ -137,6 +148,18 @@ __device__ __forceinline__ void load_spinor<P16>(const void *base, const float *
     }
 }
 
+template <>
+__device__ __forceinline__ void load_spinor<PDF>(const void *base, const float *, int cb, int Vh, df64 v[24])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(base) + cb;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        float4 c = ldg(p + (size_t)k * Vh);
+        v[2 * k] = df64(c.x, c.y);
+        v[2 * k + 1] = df64(c.z, c.w);
+    }
+}
+
 // FP16 only: the stored halves of a site without the norm factor, and the norm itself, so a
 // linear consumer can apply the norm once to its result instead of to all 24 inputs.
 __device__ __forceinline__ float load_spinor_f16_unscaled(const void *base, const float *norm, int cb, int Vh,
@@ -173,6 +196,13 @@ __device__ __forceinline__ void store_spinor<P32>(void *base, float *, int cb, i
     float4 *p = reinterpret_cast<float4 *>(base) + cb;
 #pragma unroll
     for (int k = 0; k < 6; k++) p[(size_t)k * Vh] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <>
+__device__ __forceinline__ void store_spinor<PDF>(void *base, float *, int cb, int Vh, const df64 v[24])
+{
+    float4 *p = reinterpret_cast<float4 *>(base) + cb;
+#pragma unroll
+    for (int k = 0; k < 12; k++) p[(size_t)k * Vh] = make_float4(v[2 * k].hi, v[2 * k].lo, v[2 * k + 1].hi, v[2 * k + 1].lo);
 }
 // FP16 with per-site norm: norm = max |v_k| over the site, stored halves = v_k / norm (|.| <= 1).
 template <>
@@ -301,6 +331,22 @@ struct LinkLoader<P32, RECON> {
             }
             decode_link8(r, U);
         }
+    }
+};
+
+template <int RECON>
+struct LinkLoader<PDF, RECON> {
+    __device__ static __forceinline__ void load(const void *g, int cb, int Vh, Link<df64> &U)
+    {
+        static_assert(RECON == 18 || RECON == 12, "DF64 links are stored with 18 or 12 reals");
+        const float4 *p = reinterpret_cast<const float4 *>(g) + cb;
+        constexpr int NC = RECON / 2;  // complex entries stored
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+            float4 c = ldg(p + (size_t)k * Vh);
+            U.u[k / 3][k % 3] = {df64(c.x, c.y), df64(c.z, c.w)};
+        }
+        if (RECON == 12) complete_row3(U);
     }
 };
 

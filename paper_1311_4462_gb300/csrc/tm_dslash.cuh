@@ -154,35 +154,6 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
     }
 }
 
-// One flavour of the doublet per thread (flavour = lane & 1): the 8 hops use this flavour's
-// spinor only; the link loads of the two lanes of a pair hit the same addresses and are served
-// by one request.  Flavour mixing in the epilogue takes the partner lane's values by shuffle.
-template <typename T>
-__device__ __forceinline__ void partner(const T v[24], T p[24])
-{
-#pragma unroll
-    for (int k = 0; k < 24; k++) p[k] = __shfl_xor_sync(0xffffffffu, v[k], 1);
-}
-
-// out_f = m[g][f][f] own + m[g][f][1-f] other, per spin block g
-template <typename T>
-__device__ __forceinline__ void twist_split(const Twist<T> &tw, int f, T own[24], const T other[24])
-{
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        const int gi = s >> 1;
-        const C<T> d = tw.m[gi][f][f], o = tw.m[gi][f][1 - f];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int k = 2 * (3 * s + c);
-            const C<T> a = {own[k], own[k + 1]}, b = {other[k], other[k + 1]};
-            const C<T> r = cadd(cmul(d, a), cmul(o, b));
-            own[k] = r.r;
-            own[k + 1] = r.i;
-        }
-    }
-}
-
 template <int PREC, int NF, int RECON, bool PRO>
 __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs)
 {
@@ -318,7 +289,8 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
 }
 
 // The same kernel with a register cap: 128-thread blocks, at least MINB resident per SM
-// (65536 / (128 MINB) registers per thread), traded against spills by the autotuner.
+// (65536 / (128 MINB) registers per thread).  MINB = 4 measured fastest on GB300 for every
+// storage form (caps for 5, 6, 8 blocks spilled; the uncapped doublet kernel holds only 12 warps).
 template <int PREC, int NF, int RECON, bool PRO, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
@@ -334,8 +306,10 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__
 // of four right-hand sides of the same 32 sites, so the remaining link reads hit L2 and each
 // link leaves DRAM about once per site for all sources.  Slot k of the active set is
 // right-hand side act[k] (act = NULL: k).
+// (the register cap of 128 x 4 applies to the binary32 / binary16 / binary64 forms; double-float
+// code needs about 200-255 registers and is launched without the cap)
 template <int PREC, int NF, int RECON, bool PRO>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, (PREC == PDF ? 1 : 4))
     k_dslash_multi(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act, int nact,
                    int nrhs)
 {
@@ -356,13 +330,10 @@ cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::rea
 {
     const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + 3) / 4));
 #define TM_M(NF, R, P) k_dslash_multi<PREC, NF, R, P><<<grid, 128, 0, s>>>(a, act, nact, nrhs)
-#define TM_MR(NF, P)                        \
-    switch (recon) {                        \
-    case 18: TM_M(NF, 18, P); break;        \
-    case 12: TM_M(NF, 12, P); break;        \
-    case 8: TM_M(NF, 8, P); break;          \
-    default: return cudaErrorInvalidValue;  \
-    }
+#define TM_MR(NF, P)                                          \
+    if (recon == 18) TM_M(NF, 18, P);                         \
+    else if (recon == 12 || PREC == PDF) TM_M(NF, 12, P);     \
+    else TM_M(NF, (PREC == PDF ? 12 : 8), P);
     if (nf == 1) {
         if (pro) { TM_MR(1, true) } else { TM_MR(1, false) }
     } else {
@@ -371,118 +342,6 @@ cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::rea
 #undef TM_MR
 #undef TM_M
     return cudaGetLastError();
-}
-
-template <int PREC, int RECON>
-__global__ void __launch_bounds__(256) k_dslash_fsplit(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
-{
-    using T = typename Traits<PREC>::real;
-    using LL = LinkLayout<PREC, RECON>;
-    using LC = typename LL::chunk;
-    using SC = typename Traits<PREC>::schunk;
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int f = (int)(tid & 1);
-    const bool live = (tid >> 1) < a.Vh;
-    // lanes past the end compute the last site again (shuffles need the whole warp) and do not store
-    const int cb = live ? (int)(tid >> 1) : a.Vh - 1;
-
-    int r = cb;
-    const int xh = r % a.X1h;
-    r /= a.X1h;
-    const int y = r % a.Ly;
-    r /= a.Ly;
-    const int z = r % a.Lz;
-    const int t = r / a.Lz;
-    const int op = a.out_parity;
-    const int x = 2 * xh + ((op + y + z + t) & 1);
-    const int row = cb - xh;
-    const size_t gpar = (size_t)LL::N * a.Vh;
-    const LC *G = reinterpret_cast<const LC *>(a.gauge);
-    const LC *Gout = G + (size_t)op * gpar;
-    const LC *Gin = G + (size_t)(1 - op) * gpar;
-    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
-    DslashArgs<T> af = a;  // this lane's flavour block as a one-flavour field
-    af.in = reinterpret_cast<const SC *>(a.in) + f * fstride;
-    af.in_norm = a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr;
-
-    T acc[1][24];
-#pragma unroll
-    for (int k = 0; k < 24; k++) acc[0][k] = T(0);
-    Link<T> U;
-    const T one = T(1);
-    {
-        const int nf_ = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
-        LinkLoader<PREC, RECON>::load(Gout + 0 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, 1, false, 0, true>(acc, U, af, nf_, one);
-        const int nb_ = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
-        LinkLoader<PREC, RECON>::load(Gin + 0 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, 1, false, 0, false>(acc, U, af, nb_, one);
-    }
-    {
-        const int s = a.X1h;
-        const int nf_ = (y == a.Ly - 1) ? cb - (a.Ly - 1) * s : cb + s;
-        LinkLoader<PREC, RECON>::load(Gout + 1 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, 1, false, 1, true>(acc, U, af, nf_, one);
-        const int nb_ = (y == 0) ? cb + (a.Ly - 1) * s : cb - s;
-        LinkLoader<PREC, RECON>::load(Gin + 1 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, 1, false, 1, false>(acc, U, af, nb_, one);
-    }
-    {
-        const int s = a.X1h * a.Ly;
-        const int nf_ = (z == a.Lz - 1) ? cb - (a.Lz - 1) * s : cb + s;
-        LinkLoader<PREC, RECON>::load(Gout + 2 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, 1, false, 2, true>(acc, U, af, nf_, one);
-        const int nb_ = (z == 0) ? cb + (a.Lz - 1) * s : cb - s;
-        LinkLoader<PREC, RECON>::load(Gin + 2 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, 1, false, 2, false>(acc, U, af, nb_, one);
-    }
-    {
-        const int s = a.X1h * a.Ly * a.Lz;
-        const bool wf = (t == a.Lt - 1), wb = (t == 0);
-        const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
-        LinkLoader<PREC, RECON>::load(Gout + 3 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, 1, false, 3, true>(acc, U, af, nf_, (wf && a.tbc) ? -one : one);
-        const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
-        LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, 1, false, 3, false>(acc, U, af, nb_, (wb && a.tbc) ? -one : one);
-    }
-
-    T *v = acc[0];
-    T other[24];
-    const int epi = a.epilogue;
-    if (epi == EPI_SCALE) {
-#pragma unroll
-        for (int k = 0; k < 24; k++) v[k] *= a.coef;
-    } else if (epi == EPI_TW) {
-        partner(v, other);
-        twist_split(a.tw_epi, f, v, other);
-    } else {
-        T xv[24];
-        const SC *X = reinterpret_cast<const SC *>(a.x) + f * fstride;
-        load_spinor<PREC>(X, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv);
-        if (epi == EPI_TWX_AXPY) {
-            partner(xv, other);
-            twist_split(a.tw_epi, f, xv, other);
-#pragma unroll
-            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
-        } else if (epi == EPI_X_TWAXPY) {
-            partner(v, other);
-            twist_split(a.tw_epi, f, v, other);
-#pragma unroll
-            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 24; k++) v[k] = fma(a.coef, v[k], xv[k]);
-            if (epi == EPI_TW_XPAY) {
-                partner(v, other);
-                twist_split(a.tw_epi, f, v, other);
-            }
-        }
-    }
-    if (live) {
-        SC *O = reinterpret_cast<SC *>(a.out) + f * fstride;
-        store_spinor<PREC>(O, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, v);
-    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -630,40 +489,21 @@ __global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ Dsl
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
-// variant 0: one thread per site (both flavours); variant 1: one thread per site and flavour
-// (doublet without prologue only); variant 2: variant 0 with the two-stage load pipeline (no prologue);
-// variants 3-6: variant 0 with a register cap for 4, 5, 6, 8 resident 128-thread blocks.  block: threads per block (multiple of 32, <= 256).
+// variant 0: one thread per site (both flavours); variant 2: the two-stage load pipeline (no
+// prologue); variant 3: variant 0 with a register cap (4 resident 128-thread blocks per SM).
 template <int PREC>
 cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                int variant, int block, cudaStream_t s)
 {
-    if (nf == 2 && !pro && variant == 1) {
-        const long threads = 2L * a.Vh;
-        const int grid = (int)((threads + block - 1) / block);
-        switch (recon) {
-        case 18: k_dslash_fsplit<PREC, 18><<<grid, block, 0, s>>>(a); break;
-        case 12: k_dslash_fsplit<PREC, 12><<<grid, block, 0, s>>>(a); break;
-        case 8: k_dslash_fsplit<PREC, 8><<<grid, block, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    if (variant >= 3) {
-        // register-capped launches, 128 threads per block
+    if (variant == 3) {
+        // register-capped launch: 128 threads per block, at least 4 resident blocks per SM
         const int g128 = (a.Vh + 127) / 128;
-#define TM_LB(NF, R, P)                                                           \
-    switch (variant) {                                                            \
-    case 3: k_dslash_lb<PREC, NF, R, P, 4><<<g128, 128, 0, s>>>(a); break;        \
-    case 4: k_dslash_lb<PREC, NF, R, P, 5><<<g128, 128, 0, s>>>(a); break;        \
-    case 5: k_dslash_lb<PREC, NF, R, P, 6><<<g128, 128, 0, s>>>(a); break;        \
-    default: k_dslash_lb<PREC, NF, R, P, 8><<<g128, 128, 0, s>>>(a); break;       \
-    }
-#define TM_LBR(NF, P)                   \
-    switch (recon) {                    \
-    case 18: TM_LB(NF, 18, P) break;     \
-    case 12: TM_LB(NF, 12, P) break;     \
-    case 8: TM_LB(NF, 8, P) break;       \
-    default: return cudaErrorInvalidValue; \
+#define TM_LBR(NF, P)                                                             \
+    switch (recon) {                                                              \
+    case 18: k_dslash_lb<PREC, NF, 18, P, 4><<<g128, 128, 0, s>>>(a); break;      \
+    case 12: k_dslash_lb<PREC, NF, 12, P, 4><<<g128, 128, 0, s>>>(a); break;      \
+    case 8: k_dslash_lb<PREC, NF, 8, P, 4><<<g128, 128, 0, s>>>(a); break;        \
+    default: return cudaErrorInvalidValue;                                        \
     }
         if (nf == 1) {
             if (pro) { TM_LBR(1, true) } else { TM_LBR(1, false) }
@@ -671,7 +511,6 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
             if (pro) { TM_LBR(2, true) } else { TM_LBR(2, false) }
         }
 #undef TM_LBR
-#undef TM_LB
         return cudaGetLastError();
     }
     const int grid = (a.Vh + block - 1) / block;

@@ -214,7 +214,10 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
             return TM_ERR_ARG;
         }
     }
-    if (psi_e->prec == TM_PREC_F16) { set_error("tm_force: FP64 or FP32 fields only"); return TM_ERR_ARG; }
+    if (psi_e->prec != TM_PREC_F64 && psi_e->prec != TM_PREC_F32) {
+        set_error("tm_force: FP64 or FP32 fields only");
+        return TM_ERR_ARG;
+    }
     if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("tm_force: unknown canon_type"); return TM_ERR_ARG; }
     ForceArgs a;
     a.psi[0] = psi_e->data;

@@ -27,7 +27,7 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
 struct tm_tune_entry {
-    int variant;  // 0: one thread per site; 1: one thread per site and flavour (doublet)
+    int variant;  // 0: one thread per site; 2: two-stage load pipeline; 3: register-capped (128 x 4)
     int block;    // threads per block
 };
 
@@ -38,16 +38,17 @@ struct tm_gauge {
     int Vh, X1h;
     int device;
     int num_sms;
-    void *links[3];     // packed links, index 0: FP64, 1: FP32, 2: FP16
-    size_t link_bytes[3];
+    void *links[4];     // packed links, index 0: FP64, 1: FP32, 2: FP16, 3: DF64
+    size_t link_bytes[4];
     double *scratch;    // reduction partials + device scalars (library-owned)
     double *host_scalars;  // pinned mirror for scalar readback
-    tm_tune_entry tune[3][2];  // [precision index][prologue]
+    tm_tune_entry tune[4][2];  // [precision index][prologue]
     size_t scratch_bytes;
 };
 
 namespace tmk {
-int prec_index(int prec);          // 0/1/2 for F64/F32/F16, -1 otherwise
+int prec_index(int prec);          // 0/1/2/3 for F64/F32/F16/DF64, -1 otherwise
+size_t real_bytes(int prec);       // storage bytes per real
 int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
 size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);

@@ -123,6 +123,16 @@ __global__ void k_pack_gauge(void *out, const double2 *canon, int recon, Geo g)
         const int N = nr / 2;
         double2 *o = reinterpret_cast<double2 *>(out) + slot * N * (long)g.Vh + cb;
         for (int k = 0; k < N; k++) o[(long)k * g.Vh] = make_double2(r[2 * k], r[2 * k + 1]);
+    } else if (PREC == PDF) {
+        // (hi, lo) pairs of two reals per float4; 8-real storage is not used for DF64 (12 reals)
+        const int nre = (recon == 18) ? 18 : 12;
+        if (recon == 8) encode_link(u, 12, r);
+        const int N = nre / 2;
+        float4 *o = reinterpret_cast<float4 *>(out) + slot * N * (long)g.Vh + cb;
+        for (int k = 0; k < N; k++) {
+            const df64 a(r[2 * k]), b(r[2 * k + 1]);
+            o[(long)k * g.Vh] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
     } else if (PREC == P32) {
         if (recon == 18) {
             float2 *o = reinterpret_cast<float2 *>(out) + slot * 9 * (long)g.Vh + cb;
@@ -185,13 +195,14 @@ __global__ void k_noise_z2(void *out, float *norm, int parity, unsigned long lon
     const unsigned long long G = 0x9E3779B97F4A7C15ull;
     const unsigned long long base = (seed + rhs + 1ull) * G;
     const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+    const T mh = -h;
     T v[24];
 #pragma unroll
     for (int k = 0; k < 12; k++) {
         const unsigned long long i = (unsigned long long)((lex * g.nf + f) * 12 + k);
         const unsigned long long z = splitmix64_out(base + (i + 1ull) * G);
-        v[2 * k] = (z & 1ull) ? -h : h;
-        v[2 * k + 1] = (z & 2ull) ? -h : h;
+        v[2 * k] = (z & 1ull) ? mh : h;
+        v[2 * k + 1] = (z & 2ull) ? mh : h;
     }
     const long blk = (long)rhs * g.nf + f;
     SC *o = reinterpret_cast<SC *>(out) + blk * Traits<PREC>::SCHUNKS * (long)g.Vh;
@@ -219,7 +230,10 @@ cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void 
     const int block = 128;
     const long grid = (n + block - 1) / block;
 #define TM_P(P, CT) k_pack_spinor<P, CT><<<grid, block, 0, s>>>(f->data, f->norm, (const CT *)canon, parity, G)
-    if (ctype == TM_C128) {
+    if (f->prec == TM_PREC_DF64) {
+        if (ctype == TM_C128) TM_P(PDF, double2);
+        else TM_P(PDF, float2);
+    } else if (ctype == TM_C128) {
         if (f->prec == TM_PREC_F64) TM_P(P64, double2);
         else if (f->prec == TM_PREC_F32) TM_P(P32, double2);
         else TM_P(P16, double2);
@@ -240,7 +254,10 @@ cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, cons
     const int block = 128;
     const long grid = (n + block - 1) / block;
 #define TM_U(P, CT) k_unpack_spinor<P, CT><<<grid, block, 0, s>>>((CT *)canon, f->data, f->norm, parity, G)
-    if (ctype == TM_C128) {
+    if (f->prec == TM_PREC_DF64) {
+        if (ctype == TM_C128) TM_U(PDF, double2);
+        else TM_U(PDF, float2);
+    } else if (ctype == TM_C128) {
         if (f->prec == TM_PREC_F64) TM_U(P64, double2);
         else if (f->prec == TM_PREC_F32) TM_U(P32, double2);
         else TM_U(P16, double2);
@@ -259,7 +276,8 @@ cudaError_t launch_noise_z2(const tm_gauge *g, const tm_field *f, int parity, un
     const long n = (long)G.Vh * G.nf * G.nrhs;
     const int block = 128;
     const long grid = (n + block - 1) / block;
-    if (f->prec == TM_PREC_F64) k_noise_z2<P64><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
+    if (f->prec == TM_PREC_DF64) k_noise_z2<PDF><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
+    else if (f->prec == TM_PREC_F64) k_noise_z2<P64><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
     else if (f->prec == TM_PREC_F32) k_noise_z2<P32><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
     else k_noise_z2<P16><<<grid, block, 0, s>>>(f->data, f->norm, parity, seed, G);
     return cudaGetLastError();
@@ -274,7 +292,8 @@ cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void
     const double2 *c = (const double2 *)canon;
     if (pidx == 0) k_pack_gauge<P64><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
     else if (pidx == 1) k_pack_gauge<P32><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
-    else k_pack_gauge<P16><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    else if (pidx == 2) k_pack_gauge<P16><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    else k_pack_gauge<PDF><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
     return cudaGetLastError();
 }
 

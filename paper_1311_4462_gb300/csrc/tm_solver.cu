@@ -52,10 +52,18 @@ struct Carve {
     }
 };
 
+static int true_prec_of(const tm_solver_params *sp)
+{
+    return sp->true_prec == TM_PREC_DF64 ? TM_PREC_DF64 : TM_PREC_F64;
+}
+
 static size_t workspace_need(const tm_gauge *g, const tm_solver_params *sp)
 {
     Carve c{nullptr, 0, (size_t)-1};
-    for (int i = 0; i < 6; i++) c.take(g, TM_PREC_F64);
+    const int tp = true_prec_of(sp);
+    for (int i = 0; i < 6; i++) c.take(g, tp);
+    if (tp == TM_PREC_DF64)
+        for (int i = 0; i < 2; i++) c.take(g, tp);  // x and b in DF64
     if (sp->solver == TM_SOLVER_MIXED_CG) {
         for (int i = 0; i < 5; i++) c.take(g, sp->sloppy_prec);
         c.take(g, TM_PREC_F32);
@@ -139,6 +147,10 @@ static tm_status check_solver_params(const tm_gauge *g, const tm_solver_params *
     }
     if (sp->pc != TM_PC_ASYM && sp->pc != TM_PC_SYM) { set_error("unknown pc"); return TM_ERR_ARG; }
     if (!(sp->tol > 0.0) || sp->maxiter < 1) { set_error("tol must be > 0 and maxiter >= 1"); return TM_ERR_ARG; }
+    if (sp->true_prec != 0 && sp->true_prec != TM_PREC_F64 && sp->true_prec != TM_PREC_DF64) {
+        set_error("true_prec must be TM_PREC_F64 or TM_PREC_DF64");
+        return TM_ERR_ARG;
+    }
     if (sp->solver == TM_SOLVER_MIXED_CG) {
         if (sp->sloppy_prec != TM_PREC_F32 && sp->sloppy_prec != TM_PREC_F16) {
             set_error("sloppy_prec must be TM_PREC_F32 or TM_PREC_F16");
@@ -168,8 +180,14 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
     sv_.H = g->host_scalars;
     Solver &V = sv_;
     Carve c{reinterpret_cast<char *>(ws), 0, ws_bytes};
-    tm_field r = c.take(g, TM_PREC_F64), p = c.take(g, TM_PREC_F64), Ap = c.take(g, TM_PREC_F64);
-    tm_field te = c.take(g, TM_PREC_F64), to = c.take(g, TM_PREC_F64), bh = c.take(g, TM_PREC_F64);
+    const int tp = true_prec_of(sp);
+    tm_field r = c.take(g, tp), p = c.take(g, tp), Ap = c.take(g, tp);
+    tm_field te = c.take(g, tp), to = c.take(g, tp), bh = c.take(g, tp);
+    tm_field xt{}, bt{};
+    if (tp == TM_PREC_DF64) {
+        xt = c.take(g, tp);
+        bt = c.take(g, tp);
+    }
     const bool mixed = sp->solver == TM_SOLVER_MIXED_CG;
     tm_field rs{}, ps{}, Aps{}, tes{}, tos{}, xs{};
     if (mixed) {
@@ -187,7 +205,16 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
     double bb = 0, rr = 0, r2 = 0;
     int it = 0, nrel = 0;
     const double tol2 = sp->tol * sp->tol;
-    const tm_field *bhat = b;
+    const tm_field *x_user = x;
+    const tm_field *bhat = nullptr;
+    if (tp == TM_PREC_DF64) {
+        // the iteration works on DF64 copies of b and x; x is converted back at the end
+        TRY(V.copy(&bt, b));
+        if (sp->use_x0) TRY(V.copy(&xt, x));
+        b = &bt;
+        x = &xt;
+    }
+    bhat = b;
     // right-hand side of the normal equations
     if (sp->solution == TM_SOLUTION_MAT) {
         TRY(tm_precond_op(g, &bh, b, &to, sp->pc, !sp->dagger, s));  // bhat = A^dag b
@@ -295,6 +322,10 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
         st = TM_ERR_NOCONV;
     }
 done:
+    if (x != x_user && (st == TM_OK || st == TM_ERR_NOCONV)) {
+        const tm_status cst = V.copy(x_user, x);  // DF64 -> FP64
+        if (st == TM_OK) st = cst;
+    }
     if (stats) {
         stats->iterations = it;
         stats->reliable_updates = nrel;
@@ -376,10 +407,11 @@ namespace tmk {
 static size_t multi_workspace_need(const tm_gauge *g, const tm_solver_params *sp, int nrhs)
 {
     size_t need = 0, d, n;
-    const int ps = sp->solver == TM_SOLVER_MIXED_CG ? sp->sloppy_prec : TM_PREC_F64;
-    const int px = sp->solver == TM_SOLVER_MIXED_CG ? TM_PREC_F32 : TM_PREC_F64;
-    tm_field_bytes(g, TM_PREC_F64, nrhs, &d, &n);
-    need += 5 * align256(d);
+    const int tp = true_prec_of(sp);
+    const int ps = sp->solver == TM_SOLVER_MIXED_CG ? sp->sloppy_prec : tp;
+    const int px = sp->solver == TM_SOLVER_MIXED_CG ? TM_PREC_F32 : tp;
+    tm_field_bytes(g, tp, nrhs, &d, &n);
+    need += (tp == TM_PREC_DF64 ? 7 : 5) * align256(d);
     tm_field_bytes(g, ps, nrhs, &d, &n);
     need += 5 * (align256(d) + align256(n));
     tm_field_bytes(g, px, nrhs, &d, &n);
@@ -488,11 +520,18 @@ static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_fiel
     auto t0 = std::chrono::steady_clock::now();
     const int nrhs = x->nrhs;
     const bool mixed = sp->solver == TM_SOLVER_MIXED_CG;
-    const int ps = mixed ? sp->sloppy_prec : TM_PREC_F64;
-    const int px = mixed ? TM_PREC_F32 : TM_PREC_F64;
+    const int tp = true_prec_of(sp);
+    const int ps = mixed ? sp->sloppy_prec : tp;
+    const int px = mixed ? TM_PREC_F32 : tp;
     MultiCarve c{reinterpret_cast<char *>(ws), 0};
-    tm_field r = c.take(g, TM_PREC_F64, nrhs), Ap = c.take(g, TM_PREC_F64, nrhs), te = c.take(g, TM_PREC_F64, nrhs);
-    tm_field to = c.take(g, TM_PREC_F64, nrhs), bh = c.take(g, TM_PREC_F64, nrhs);
+    tm_field r = c.take(g, tp, nrhs), Ap = c.take(g, tp, nrhs), te = c.take(g, tp, nrhs);
+    tm_field to = c.take(g, tp, nrhs), bh = c.take(g, tp, nrhs);
+    tm_field xt{}, bt{};
+    if (tp == TM_PREC_DF64) {
+        xt = c.take(g, tp, nrhs);
+        bt = c.take(g, tp, nrhs);
+    }
+    const tm_field *x_user = x;
     tm_field rs = c.take(g, ps, nrhs), pp = c.take(g, ps, nrhs), Aps = c.take(g, ps, nrhs);
     tm_field tes = c.take(g, ps, nrhs), tos = c.take(g, ps, nrhs), xs = c.take(g, px, nrhs);
     MultiSolver V;
@@ -527,6 +566,14 @@ static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_fiel
     MTRY(cuda_check(cudaEventRecord(ev, user_stream), "event"));
     MTRY(cuda_check(cudaStreamWaitEvent(s, ev, 0), "event wait"));
     MTRY(V.set_active(act, &nact));
+    if (tp == TM_PREC_DF64) {
+        // DF64 copies of b (and the initial x); x is converted back at the end
+        MTRY(V.site(OP_COPY, fref(b), fnone(), fref(&bt), fnone(), sv(1), sv(0), 0, 0, 0, false));
+        if (sp->use_x0) MTRY(V.site(OP_COPY, fref(x), fnone(), fref(&xt), fnone(), sv(1), sv(0), 0, 0, 0, false));
+        b = &bt;
+        x = &xt;
+        bhat = b;
+    }
     if (sp->solution == TM_SOLUTION_MAT) {
         MTRY(precond_core(g, &bh, b, &to, sp->pc, !sp->dagger, s, V.d_list, nact));  // bhat = A^dag b
         bhat = &bh;
@@ -546,7 +593,7 @@ static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_fiel
                     false));
     } else {
         size_t d, n;
-        tm_field_bytes(g, TM_PREC_F64, nrhs, &d, &n);
+        tm_field_bytes(g, tp, nrhs, &d, &n);
         MTRY(cuda_check(cudaMemsetAsync(x->data, 0, d, s), "memset"));
         MTRY(V.site(OP_COPY, fref(bhat), fnone(), fref(&r), fnone(), sv(1), sv(0), 0, 0, 0, false));
         MTRY(V.site(OP_NORM, fref(&r), fnone(), fnone(), fnone(), sv(0), sv(0), 1, FIN_STORE, SL_TMP0, false));
@@ -643,6 +690,10 @@ static tm_status solve_multi(const tm_gauge *g, const tm_field *x, const tm_fiel
         st = TM_ERR_NOCONV;
     }
 mdone:
+    if (x != x_user && (st == TM_OK || st == TM_ERR_NOCONV)) {
+        const tm_status cst = V.site(OP_COPY, fref(x), fnone(), fref(x_user), fnone(), sv(1), sv(0), 0, 0, 0, false);
+        if (st == TM_OK) st = cst;
+    }
     if (stats) {
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int k = 0; k < nrhs; k++) {

@@ -81,9 +81,10 @@ def test_precond_op_active_subset_and_bad_index():
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("solver,sloppy", [("cg", 8), ("mixed", 4), ("mixed", 2)])
+@pytest.mark.parametrize("solver,sloppy,tp", [("cg", 8, 8), ("mixed", 4, 8), ("mixed", 2, 8), ("mixed", 2, 16),
+                                              ("cg", 8, 16)])
 @pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
-def test_solve_multi_matches_single_solves(case, solver, sloppy, graph):
+def test_solve_multi_matches_single_solves(case, solver, sloppy, tp, graph):
     nr = 4
     tmq, p, po, U, g, src = make(case, nr)
     src[2] = 0.0                  # a zero source converges at iteration 0
@@ -93,7 +94,7 @@ def test_solve_multi_matches_single_solves(case, solver, sloppy, graph):
     bp = tmq.Field(g, 8, nr)
     tmq.prepare_rhs(g, bp, be, bo, 0, False)
     xe = tmq.Field(g, 8, nr)
-    kw = dict(solver=solver, tol=1e-10, maxiter=5000, use_graph=graph)
+    kw = dict(solver=solver, tol=1e-10, maxiter=5000, use_graph=graph, true_prec=tp)
     if solver == "mixed":
         kw["sloppy_prec"] = sloppy
     status, stats = tmq.solve_multi(g, xe, bp, **kw)
@@ -116,7 +117,7 @@ def test_solve_multi_matches_single_solves(case, solver, sloppy, graph):
     g.close()
 
 
-@pytest.mark.parametrize("prec", [8, 4, 2])
+@pytest.mark.parametrize("prec", [8, 16, 4, 2])
 def test_g5dot(prec):
     nr = 3
     tmq, p, po, U, g, src = make(CASES[0], nr)
@@ -127,7 +128,7 @@ def test_g5dot(prec):
     g5 = np.array([1, 1, -1, -1])[:, None]
     for r in range(nr):
         ref = np.vdot(a[r], (b[r] * g5))
-        assert abs(got[r] - ref) / (np.linalg.norm(a[r]) * np.linalg.norm(b[r])) < (1e-14 if prec == 8 else 1e-6)
+        assert abs(got[r] - ref) / (np.linalg.norm(a[r]) * np.linalg.norm(b[r])) < (1e-14 if prec in (8, 16) else 1e-6)
     g.close()
 
 
@@ -158,7 +159,7 @@ def test_loop_estimator_against_dense_trace():
     g.close()
 
 
-@pytest.mark.parametrize("prec", [8, 4, 2])
+@pytest.mark.parametrize("prec", [8, 16, 4, 2])
 def test_device_noise_matches_counter_definition(prec):
     import paper_1311_4462_gb300 as tmq
     nr = 3
@@ -171,6 +172,8 @@ def test_device_noise_matches_counter_definition(prec):
         ref = inputs.z2_noise_counter(p.L, p.nf, 41 + r)
         if prec == 8:
             assert np.array_equal(got[r], ref)  # bit-exact
+        elif prec == 16:
+            assert np.abs(got[r] - ref).max() < 1e-15
         else:
             assert np.abs(got[r] - ref).max() < 1e-3
     g.close()

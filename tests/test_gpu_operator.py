@@ -13,7 +13,7 @@ from paper_1311_4462_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {8: 1e-13, 4: 1e-6, 2: 5e-3}
+TOL = {8: 1e-13, 16: 1e-13, 4: 1e-6, 2: 5e-3}  # 16: DF64 (double-float), held to the FP64 bound
 
 # (name, L, flavor, kappa, mu, eps): covers L = 2 extents (x+mu == x-mu), ragged tails
 # (Vh not a multiple of the 128-thread block), non-cubic shapes, both flavour signs.
@@ -24,7 +24,7 @@ CASES = [
     ("minus_8x6x4x10", (8, 6, 4, 10), -1, 0.1612, 0.004, 0.0),
     ("nd_2^4", (2, 2, 2, 2), 2, 0.16, 0.135, 0.15),
 ]
-PRECS = [8, 4, 2]
+PRECS = [8, 16, 4, 2]
 RECONS = [18, 12, 8]
 
 
@@ -52,7 +52,7 @@ def setup(case, recon):
 
 def use_variant(tmq, g, variant, block=128):
     """Force the hopping-kernel launch choice (variant 1 = thread per site and flavour, doublet only)."""
-    pro_variant = variant if variant >= 3 else 0
+    pro_variant = 3 if variant == 3 else 0
     tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
 
@@ -76,7 +76,7 @@ def test_pack_unpack_roundtrip(case, prec, recon):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
     e, o = fields(tmq, g, prec, psi)
     back = get(tmq, g, e, 0) + get(tmq, g, o, 1)
-    tol = {8: 0.0, 4: 1e-7, 2: 6e-4}[prec]
+    tol = {8: 0.0, 16: 1e-14, 4: 1e-7, 2: 6e-4}[prec]
     assert rel(back, psi) <= tol
 
 
@@ -85,12 +85,10 @@ def test_pack_unpack_roundtrip(case, prec, recon):
 @pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
-@pytest.mark.parametrize("variant", [0, 1, 2, 4, 6], ids=["site", "split", "pipe", "cap5", "cap8"])
+@pytest.mark.parametrize("variant", [0, 2, 3], ids=["site", "pipe", "cap4"])
 def test_precond_op(case, prec, recon, pc, dagger, variant):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
-    if variant == 1 and p.nf == 1:
-        pytest.skip("flavour split applies to the doublet")
-    use_variant(tmq, g, variant, block=64 if variant in (1, 2) else 128)
+    use_variant(tmq, g, variant, block=64 if variant == 2 else 128)
     xe, _ = fields(tmq, g, prec, psi)
     out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
     tmq.precond_op(g, out, xe, tmp, pc, dagger)
@@ -117,13 +115,11 @@ def test_full_operator(case, prec, dagger):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 @pytest.mark.parametrize("out_parity", [0, 1])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 5], ids=["site", "split", "pipe", "cap4", "cap6"])
+@pytest.mark.parametrize("variant", [0, 2, 3], ids=["site", "pipe", "cap4"])
 def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
     """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
     tmq, p, po, U, g, psi, chi = setup(case, 12)
-    if variant == 1 and p.nf == 1:
-        pytest.skip("flavour split applies to the doublet")
-    use_variant(tmq, g, variant, block=96 if variant in (1, 2) else 128)
+    use_variant(tmq, g, variant, block=96 if variant == 2 else 128)
     ip = 1 - out_parity
     fin = fields(tmq, g, prec, psi)[ip]
     fx = fields(tmq, g, prec, chi)[out_parity]
@@ -154,6 +150,16 @@ def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 def test_prepare_rhs_and_reconstruct(case, prec, pc, dagger):
     tmq, p, po, U, g, psi, chi = setup(case, 12)
+    if prec == 16:
+        be, bo = fields(tmq, g, prec, chi)
+        with pytest.raises(tmq.TMError):  # the right-hand side is prepared in FP64, not DF64
+            tmq.prepare_rhs(g, tmq.Field(g, prec), be, bo, pc, dagger)
+        xe, _ = fields(tmq, g, prec, psi)
+        xo = tmq.Field(g, prec)
+        tmq.reconstruct_odd(g, xo, bo, xe, dagger)
+        ref = orc.reconstruct_odd(po, U, mask(po, psi, 0), chi, dagger=dagger)
+        assert rel(get(tmq, g, xo, 1), ref) < TOL[prec]
+        return
     be, bo = fields(tmq, g, prec, chi)
     bp = tmq.Field(g, prec)
     tmq.prepare_rhs(g, bp, be, bo, pc, dagger)
@@ -223,7 +229,7 @@ def test_autotune_roundtrip_and_parity():
     tmq.tune_import(g, table)
     assert tmq.tune_export(g) == table
     with pytest.raises(tmq.TMError):
-        tmq.tune_import(g, "f32:0:1:100")  # block not a multiple of 32
+        tmq.tune_import(g, "f32:0:3:100")  # block not a multiple of 32
     xe, _ = fields(tmq, g, 4, psi)
     out, tmp = tmq.Field(g, 4), tmq.Field(g, 4)
     tmq.precond_op(g, out, xe, tmp, 0, False)

@@ -166,3 +166,25 @@ def test_norm_and_dot_reductions(prec):
     assert abs(tmq.norm2(g, fb) - np.vdot(bb, bb).real) / np.vdot(bb, bb).real < tol
     d = np.vdot(bb, cc).real
     assert abs(tmq.dot(g, fb, fc) - d) / (np.linalg.norm(bb) * np.linalg.norm(cc)) < tol
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("solver,sloppy", [("cg", 4), ("mixed", 4), ("mixed", 2)])
+def test_df64_true_precision(case, solver, sloppy):
+    """Solution accumulation and true residual in double-float: same solutions as the FP64 solver."""
+    tmq, p, po, U, g, b = setup(case)
+    for pc in (0, 1):
+        psi, st = full_solve(tmq, g, b, pc, False, solver=solver, sloppy_prec=sloppy, tol=1e-10, maxiter=5000,
+                             true_prec=tmq.TM_PREC_DF64)
+        assert st["status"] == 0 and st["true_residual"] <= 1e-10
+        psi64, _ = full_solve(tmq, g, b, pc, False, solver="cg", tol=1e-12, maxiter=5000)
+        assert rel(psi, psi64) < 1e-6
+        assert rel(orc.apply_M(po, U, psi), b) < 1e-6
+
+
+def test_df64_cg_to_1e12():
+    """A whole CG in DF64 reaches an FP64-level tolerance."""
+    tmq, p, po, U, g, b = setup(CASES[1])
+    psi, st = full_solve(tmq, g, b, 0, False, solver="cg", tol=1e-12, maxiter=5000, true_prec=tmq.TM_PREC_DF64)
+    assert st["status"] == 0 and st["true_residual"] <= 1e-12
+    assert rel(orc.apply_M(po, U, psi), b) < 1e-8
