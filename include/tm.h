@@ -231,10 +231,10 @@ typedef struct {
     int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
     int use_x0;      /* 1: x_e holds the initial guess on entry; 0: start from zero */
     int want_pc_residual; /* 1: also compute stats->pc_residual (one more FP64 operator application) */
+    int use_graph;   /* tm_solve_multi: capture the sloppy iteration as a CUDA graph and replay it */
     int true_prec;   /* TM_PREC_F64 (default, 0 means F64) or TM_PREC_DF64: precision of the solution
                         accumulation, the true residual and (plain CG) the whole iteration; x and b
                         stay FP64 fields either way */
-    int use_graph;   /* tm_solve_multi: capture the sloppy iteration as a CUDA graph and replay it */
 } tm_solver_params;
 
 typedef struct {
