@@ -302,8 +302,8 @@ def per_precision(tmq, U, psi, dev, args):
             g = tmq.Gauge(p, U)
             tmq.autotune(g)
             src = psi if nf == 2 else psi[..., :1, :, :].contiguous()
-            for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16, tmq.TM_PREC_F64):
-                if recon != 12 and prec == tmq.TM_PREC_F64:
+            for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16, tmq.TM_PREC_F64, tmq.TM_PREC_DF64):
+                if recon == 8 and prec in (tmq.TM_PREC_F64, tmq.TM_PREC_DF64):
                     continue
                 xe = tmq.pack(g, src, 0, prec)
                 out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
@@ -311,15 +311,17 @@ def per_precision(tmq, U, psi, dev, args):
                     for dag in (0, 1):
                         if recon != 12 and (pc or dag):
                             continue
-                        reps = 3 if prec == 8 else 10
+                        if prec == tmq.TM_PREC_DF64 and (pc or dag):
+                            continue
+                        reps = 3 if prec in (8, 16) else 10
                         ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, pc, dag), reps, flush)
                         fl = (FLOPS_SYM if pc else FLOPS_PER_SITE)[nf] * p.Vh
                         by = asym_bytes(prec, nf, recon) * p.Vh
                         row = {"op": ("M_sym" if pc else "M_asym") + ("^dag" if dag else ""),
-                               "flavours": nf, "prec": {8: "f64", 4: "f32", 2: "f16"}[prec], "recon": recon,
+                               "flavours": nf, "prec": {8: "f64", 4: "f32", 2: "f16", 16: "df64"}[prec], "recon": recon,
                                "us": round(ms * 1e3, 1), "gflops": round(fl / (ms * 1e-3) / 1e9, 1),
                                "gbs": round(by / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(by / (ms * 1e-3) / 1e9 / peak, 3)}
-                        if prec == 8:
+                        if prec in (8, 16):
                             row["fp64_alu_frac_of_nominal_1250"] = round(fl / (ms * 1e-3) / 1e9 / 1250.0, 3)
                         rows.append(row)
                 del xe, out, tmp
@@ -363,8 +365,11 @@ def cg_section(tmq, g, U, psi, dev, args):
             "fp64_cg": run(g, bp, pc, 1, solver="cg"),
             "mixed_f16": run(g, bp, pc, 3, solver="mixed", sloppy_prec=tmq.TM_PREC_F16),
             "mixed_f32": run(g, bp, pc, 3, solver="mixed", sloppy_prec=tmq.TM_PREC_F32),
+            "mixed_f32_df64_true_residual": run(g, bp, pc, 3, solver="mixed", sloppy_prec=tmq.TM_PREC_F32,
+                                                true_prec=tmq.TM_PREC_DF64),
         }
-        best = min(nd[pname]["mixed_f16"]["ms"], nd[pname]["mixed_f32"]["ms"])
+        best = min(nd[pname]["mixed_f16"]["ms"], nd[pname]["mixed_f32"]["ms"],
+                   nd[pname]["mixed_f32_df64_true_residual"]["ms"])
         nd[pname]["speedup_mixed_vs_fp64"] = round(nd[pname]["fp64_cg"]["ms"] / best, 2)
     res["doublet_32x32x32x64"] = nd
     # one flavour 16^3x32, kappa 0.1612, mu 0.004: FP64 CG + reconstruction, full-system residual

@@ -66,14 +66,14 @@ __host__ __device__ __forceinline__ df64 two_prod(float a, float b)
     return df64(p, df_fma(a, b, -p));
 }
 
-// sum: exact sum of the high parts plus the low parts, renormalised
+// sum: exact sum of the high parts, plus the low parts, renormalised once.  The error is a few
+// 2^-48 relative to |a| + |b| (not to |a + b| under cancellation), which is what a sum of
+// similar-sized stencil terms needs, at 11 operations instead of the 20 of the fully
+// renormalised form.
 __host__ __device__ __forceinline__ df64 operator+(df64 a, df64 b)
 {
     df64 s = two_sum(a.hi, b.hi);
-    const df64 t = two_sum(a.lo, b.lo);
-    s.lo = df_add(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = df_add(s.lo, t.lo);
+    s.lo = df_add(s.lo, df_add(a.lo, b.lo));
     return fast_two_sum(s.hi, s.lo);
 }
 __host__ __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
@@ -88,17 +88,15 @@ __host__ __device__ __forceinline__ df64 operator*(df64 a, df64 b)
 }
 __host__ __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __host__ __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
-// a * b + c with the product kept unrounded until the sum
+// a * b + c with the product kept unrounded until the sum (error a few 2^-48 relative to
+// |a b| + |c|; 15 operations)
 __host__ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
 {
     df64 p = two_prod(a.hi, b.hi);
     p.lo = df_fma(a.hi, b.lo, p.lo);
     p.lo = df_fma(a.lo, b.hi, p.lo);
     df64 s = two_sum(p.hi, c.hi);
-    const df64 t = two_sum(p.lo, c.lo);
-    s.lo = df_add(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = df_add(s.lo, t.lo);
+    s.lo = df_add(s.lo, df_add(p.lo, c.lo));
     return fast_two_sum(s.hi, s.lo);
 }
 
