@@ -226,6 +226,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.quick:
         result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
         result["per_precision"] = per_precision(tmq, U, psi, dev, args)
+        result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
         result["cpu_baseline"] = cpu_baseline(U_np, psi_np, args)
@@ -325,6 +326,42 @@ def per_precision(tmq, U, psi, dev, args):
                             row["fp64_alu_frac_of_nominal_1250"] = round(fl / (ms * 1e-3) / 1e9 / 1250.0, 3)
                         rows.append(row)
                 del xe, out, tmp
+            g.close()
+    return rows
+
+
+# Table 1 of the paper (single GTX Titan, 32^3x64, asymmetric operator, GFLOPS) for context
+PAPER_TABLE1 = {("double", 12): (184, 190, 163), ("double", 8): (179, 183, 115), ("single", 12): (401, 415, 516),
+                ("single", 8): (472, 487, 567), ("half", 12): (732, 759, 879), ("half", 8): (829, 858, 624)}
+
+
+def table1_section(tmq, U, psi, dev, args):
+    """Analog of the paper's Table 1 on GB300: M_asym GFLOPS for Wilson (mu = 0), degenerate and
+    non-degenerate twisted mass, double / single / half storage, 12- and 8-real links, 32^3x64."""
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ops = {"wilson": (1, 0.0, 0.0), "deg_tm": (1, MU_DEG, 0.0), "nd_tm": (2, MU_ND, EPS_ND)}
+    precs = {"double": tmq.TM_PREC_F64, "single": tmq.TM_PREC_F32, "half": tmq.TM_PREC_F16}
+    rows = []
+    for recon in (12, 8):
+        handles = {}
+        for name, (nf, mu, eps) in ops.items():
+            p = tmq.Params(L_FULL, KAPPA, mu, eps, flavor=(tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS),
+                           recon=recon)
+            handles[name] = (p, tmq.Gauge(p, U), nf)
+            tmq.autotune(handles[name][1])
+        for pname, prec in precs.items():
+            row = {"prec": pname, "recon": recon}
+            for name, (p, g, nf) in handles.items():
+                src = psi if nf == 2 else psi[..., :1, :, :].contiguous()
+                xe = tmq.pack(g, src, 0, prec)
+                out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+                ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, 0, False), 3 if prec == 8 else 10, flush)
+                row[name] = round(FLOPS_PER_SITE[nf] * p.Vh / (ms * 1e-3) / 1e9, 1)
+                del xe, out, tmp
+            row["paper_kepler_wilson_deg_nd"] = PAPER_TABLE1[(pname, recon)]
+            rows.append(row)
+        for p, g, nf in handles.values():
             g.close()
     return rows
 
