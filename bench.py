@@ -32,17 +32,22 @@ L_FULL = (32, 32, 32, 64)
 KAPPA, MU_ND, EPS_ND, MU_DEG = 0.1612, 0.135, 0.15, 0.004
 FLOPS_PER_SITE = {1: 2808, 2: 5808}          # M_asym per even site (flop convention)
 FLOPS_SYM = {1: 2832, 2: 5856}               # M_sym per even site
-SPINOR_BYTES = {8: 192, 4: 96, 2: 52}        # per site and flavour, FP16 includes the 4-byte norm
+SPINOR_BYTES = {8: 192, 16: 192, 4: 96, 2: 52}  # per site and flavour; FP16 includes the 4-byte norm
+REAL_BYTES = {8: 8, 16: 8, 4: 4, 2: 2}          # storage bytes per real (16 = DF64, a float pair)
+
+
+def link_reals(prec, recon):
+    return 12 if (prec == 16 and recon == 8) else recon  # DF64 keeps 12 reals for recon-8 handles
 
 
 def asym_bytes(prec, nf, recon):
     """Algorithmic bytes per even site of M_asym: 16 links + 5 spinor passes."""
-    return 16 * recon * prec + 5 * SPINOR_BYTES[prec] * nf
+    return 16 * link_reals(prec, recon) * REAL_BYTES[prec] + 5 * SPINOR_BYTES[prec] * nf
 
 
 def launch_bytes(prec, nf, recon):
     """(kernel A, kernel B) bytes per output site: A reads 8 links + 1 spinor, writes 1; B also reads x."""
-    link = 8 * recon * prec
+    link = 8 * link_reals(prec, recon) * REAL_BYTES[prec]
     s = SPINOR_BYTES[prec] * nf
     return link + 2 * s, link + 3 * s
 
