@@ -66,6 +66,8 @@ def test_host_side_parameter_validation_without_gpu(lib):
     st, msg = create((4, 4, 4, 4), kappa=0.125, mu=0.0, eps=4.0, flavor=2)
     assert st == L.TM_ERR_ARG and "singular" in msg
     assert create((4, 4, 4, 4), recon=9)[0] == L.TM_ERR_ARG
+    st, msg = create((128, 128, 128, 128))  # 24 * Vh beyond 32-bit chunk indexing: the maximum size
+    assert st == L.TM_ERR_ARG and "too large" in msg
     assert create((4, 4, 4, 4), flavor=3)[0] == L.TM_ERR_ARG
     assert create((4, 4, 4, 4), kappa=-1.0)[0] == L.TM_ERR_ARG
     h = ctypes.c_void_p()
