@@ -16,8 +16,11 @@
  *  - Operator calls (tm_dslash*, tm_precond_op, tm_mat, tm_prepare_rhs, tm_reconstruct_odd,
  *    tm_twist) accept fields with nrhs >= 1 (all operands sharing nrhs): every right-hand side
  *    is processed in one launch that reads each link once per site for all of them.
- *  - All pointers to field or gauge data are DEVICE pointers (cudaMalloc'd or from an
- *    allocator such as torch).  The caller owns every field; the library never frees one.
+ *  - Field data (tm_field) are DEVICE pointers (cudaMalloc'd or from an allocator such as
+ *    torch).  Canonical buffers (tm_gauge_create, tm_pack, tm_unpack) may also be pinned host
+ *    memory, which the kernels read or write in place over the CPU-GPU link; pageable host
+ *    memory is rejected with TM_ERR_ARG.  The caller owns every buffer; the library never
+ *    frees one.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call except
  *    tm_gauge_create / tm_gauge_destroy / tm_solve / tm_solve_multi only enqueues work on
  *    `stream` and returns; errors found on the host are reported before anything is enqueued.

@@ -128,8 +128,8 @@ def pack(gauge: Gauge, canon, parity: int, prec=TM_PREC_F32, nrhs=1, out: Field 
     """tm_pack: canonical complex128/complex64 device tensor -> one parity Field."""
     torch = _torch()
     canon = torch.as_tensor(canon)
-    if canon.device.type != "cuda":
-        canon = canon.to("cuda")
+    if canon.device.type != "cuda" and not canon.is_pinned():
+        canon = canon.to("cuda")  # pinned host tensors are read in place by the kernel
     canon = canon.contiguous()
     ct = L.TM_C128 if canon.dtype == torch.complex128 else L.TM_C64
     if canon.dtype not in (torch.complex128, torch.complex64):
@@ -140,7 +140,8 @@ def pack(gauge: Gauge, canon, parity: int, prec=TM_PREC_F32, nrhs=1, out: Field 
 
 
 def unpack(gauge: Gauge, field: Field, parity: int, canon=None, dtype=None, stream=None):
-    """tm_unpack: writes the sites of `parity` into canon (a new zero tensor if None)."""
+    """tm_unpack: writes the sites of `parity` into canon (a new zero device tensor if None; a
+    pinned host tensor is written in place over the CPU-GPU link)."""
     torch = _torch()
     shape = gauge.params.spinor_shape
     if field.nrhs > 1:

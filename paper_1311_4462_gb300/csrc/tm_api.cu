@@ -158,6 +158,31 @@ static Twist<float> to_float(const Twist<double> &t)
 }
 
 // ----------------------------------------------------------------------------- validation
+// A canonical (user-layout) buffer may be device memory, managed memory, or pinned host memory;
+// pinned host memory is accessed in place by the kernels through its device mapping (on GB300
+// over the coherent CPU-GPU link), so a host-resident field is read or written without a
+// staging copy.  Pageable host memory is rejected instead of faulting.
+static tm_status resolve_canon(const void *p, void **dev_out, const char *what)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s: cannot query the canonical buffer (%s)", what, cudaGetErrorString(e));
+        return TM_ERR_ARG;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        *dev_out = const_cast<void *>(p);
+        return TM_OK;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *dev_out = at.devicePointer;
+        return TM_OK;
+    }
+    set_error("%s: the canonical buffer must be device, managed or pinned host memory", what);
+    return TM_ERR_ARG;
+}
+
 static tm_status check_field(const tm_gauge *g, const tm_field *f, const char *name)
 {
     if (!f) { set_error("%s: null tm_field", name); return TM_ERR_ARG; }
@@ -388,7 +413,14 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     for (int i = 0; i < 4; i++)
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
     cudaStream_t s = (cudaStream_t)stream;
-    tm_status st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
+    void *Ud = nullptr;
+    tm_status st = resolve_canon(U_canon, &Ud, "tm_gauge_create");
+    if (st != TM_OK) {
+        delete g;
+        return st;
+    }
+    U_canon = Ud;
+    st = cuda_check(cudaGetDevice(&g->device), "cudaGetDevice");
     if (st == TM_OK) st = cuda_check(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device),
                                      "cudaDeviceGetAttribute");
     const int precs[4] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64};
@@ -454,7 +486,9 @@ tm_status tm_pack(const tm_gauge *g, const tm_field *out, const void *canon, int
     TM_TRY(check_field(g, out, "out"));
     if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
     if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("unknown canon_type"); return TM_ERR_ARG; }
-    return cuda_check(launch_pack_spinor(g, out, canon, canon_type, parity, (cudaStream_t)stream), "tm_pack");
+    void *cd = nullptr;
+    TM_TRY(resolve_canon(canon, &cd, "tm_pack"));
+    return cuda_check(launch_pack_spinor(g, out, cd, canon_type, parity, (cudaStream_t)stream), "tm_pack");
 }
 
 tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_field *in, int parity, void *stream)
@@ -463,7 +497,9 @@ tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_fie
     TM_TRY(check_field(g, in, "in"));
     if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
     if (canon_type != TM_C128 && canon_type != TM_C64) { set_error("unknown canon_type"); return TM_ERR_ARG; }
-    return cuda_check(launch_unpack_spinor(g, canon, canon_type, in, parity, (cudaStream_t)stream), "tm_unpack");
+    void *cd = nullptr;
+    TM_TRY(resolve_canon(canon, &cd, "tm_unpack"));
+    return cuda_check(launch_unpack_spinor(g, cd, canon_type, in, parity, (cudaStream_t)stream), "tm_unpack");
 }
 
 tm_status tm_noise_z2(const tm_gauge *g, const tm_field *out, int parity, unsigned long long seed, void *stream)

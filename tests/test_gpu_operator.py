@@ -235,3 +235,26 @@ def test_autotune_roundtrip_and_parity():
     tmq.precond_op(g, out, xe, tmp, 0, False)
     ref = orc.apply_M_pc(po, U, mask(po, psi, 0))
     assert rel(get(tmq, g, out, 0), ref) < TOL[4]
+
+
+@pytest.mark.parametrize("prec", [8, 4, 2])
+def test_pinned_host_canonical_buffers_are_used_in_place(prec):
+    import ctypes
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import _lib as L
+    tmq_, p, po, U, g, psi, chi = setup(CASES[1], 12)
+    host = torch.from_numpy(psi).pin_memory()
+    f_host = tmq.pack(g, host, 0, prec)
+    f_dev = tmq.pack(g, host.to("cuda"), 0, prec)
+    torch.cuda.synchronize()
+    assert torch.equal(f_host.data, f_dev.data)
+    out_host = torch.zeros(p.spinor_shape, dtype=torch.complex128).pin_memory()
+    tmq.unpack(g, f_dev, 0, canon=out_host)
+    torch.cuda.synchronize()
+    assert torch.equal(out_host, tmq.unpack(g, f_dev, 0).cpu())
+    # pageable host memory is refused (never dereferenced by a kernel)
+    pageable = np.zeros(p.spinor_shape, dtype=np.complex128)
+    st = L.load().tm_unpack(g.h, ctypes.c_void_p(pageable.ctypes.data), L.TM_C128, f_dev.ref(), 0, None)
+    assert st == L.TM_ERR_ARG
+    st = L.load().tm_pack(g.h, f_dev.ref(), ctypes.c_void_p(pageable.ctypes.data), L.TM_C128, 0, None)
+    assert st == L.TM_ERR_ARG
