@@ -208,8 +208,10 @@ def dot(gauge, a: Field, b: Field, stream=None) -> float:
 
 
 # reliable-update thresholds: the sloppy residual may fall by this factor between FP64 updates
-# (FP16 storage keeps about 3 digits, FP32 about 7; chosen from a sweep on the 32^3x64 doublet)
-DEFAULT_DELTA = {TM_PREC_F16: 1e-2, TM_PREC_F32: 1e-3}
+# (FP16 storage keeps about 3 digits, FP32 about 7).  Chosen from a sweep on the 32^3x64
+# doublet to 1e-10: FP32 1e-5 needs 2 updates (141 ms) where 1e-3 needs 4 (184 ms) at the same
+# 78 iterations; FP16 3e-3 needs 4 updates (174 ms) where 1e-2 needs 5 and 1e-3 costs 127 iterations.
+DEFAULT_DELTA = {TM_PREC_F16: 3e-3, TM_PREC_F32: 1e-5}
 
 
 def solver_params(solver="cg", solution=TM_SOLUTION_MAT, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000,

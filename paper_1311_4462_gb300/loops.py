@@ -17,7 +17,7 @@ from . import (TM_PC_ASYM, TM_PREC_F32, TM_PREC_F64, Field, g5dot, noise_z2, pre
 
 
 def g5_trace(gauge, nsources=256, batch=16, seed0=3000, tol=1e-8, solver="mixed", sloppy_prec=TM_PREC_F32,
-             use_graph=True, pc=TM_PC_ASYM, return_solutions=False):
+             use_graph=True, pc=TM_PC_ASYM, return_solutions=False, true_prec=TM_PREC_F64):
     import torch
     vals, iters, t_solve = [], [], 0.0
     sols = []
@@ -31,7 +31,7 @@ def g5_trace(gauge, nsources=256, batch=16, seed0=3000, tol=1e-8, solver="mixed"
         t0 = time.time()
         prepare_rhs(gauge, bp, ee, eo, pc, False)
         _, stats = solve_multi(gauge, xe, bp, solver=solver, sloppy_prec=sloppy_prec, tol=tol, pc=pc,
-                               use_graph=use_graph)
+                               use_graph=use_graph, true_prec=true_prec)
         reconstruct_odd(gauge, xo, eo, xe, False)
         torch.cuda.synchronize()
         t_solve += time.time() - t0
