@@ -128,6 +128,23 @@ def read_traffic(kernel_key):
     return None
 
 
+def aggregate_ranks(total_ms, units_local, world, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time bounds the job, and
+    the work is every rank's units.  Returns (max_ms, units_per_second_total)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms), float(units_local)], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, units = float(tmax[0].item()), float(tsum[1].item())
+    else:
+        units = float(units_local)
+    return total_ms, units / (total_ms * 1e-3)
+
+
 # ------------------------------------------------------------------------------------------- ours
 def run_ours(args, rank, world):
     import numpy as np
@@ -185,17 +202,13 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    total_ms = e_start.elapsed_time(e_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ta = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
     tb = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
     Vh = p_nd.Vh
     flops_step = FLOPS_PER_SITE[nf] * Vh
+    total_ms, flops_per_s = aggregate_ranks(e_start.elapsed_time(e_end), flops_step * K, world, dev)
     ms_per_step = total_ms / K
-    value = flops_step * K * world / (total_ms * 1e-3) / 1e9
+    value = flops_per_s / 1e9
     la, lb = launch_bytes(prec, nf, recon)
     avg_launch_ms = (sum(ta) + sum(tb)) / (2 * K)
     achieved = ((la + lb) / 2 * Vh) / (avg_launch_ms * 1e-3) / 1e9
