@@ -315,7 +315,7 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text ("f32:0:3:128 ..." = precision:prologue:variant:block; variant 0 plain,
- * 2 pipelined, 3 register-capped), and back. */
+ * 2 pipelined, 3 / 4 / 5 capped at 128 registers with 128 / 64 / 256-thread blocks), and back. */
 tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n);
 tm_status tm_tune_import(tm_gauge *g, const char *text);
 

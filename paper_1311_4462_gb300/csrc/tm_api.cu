@@ -650,12 +650,12 @@ tm_status tm_autotune(tm_gauge *g, void *stream)
         for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
             float best = 1e30f;
             tm_tune_entry bestc = g->tune[pi][pro];
-            const int variants[3] = {0, 2, 3};
-            for (int vi = 0; vi < 3; vi++) {
+            const int variants[5] = {0, 2, 3, 4, 5};
+            for (int vi = 0; vi < 5; vi++) {
                 const int variant = variants[vi];
                 if (pro && variant == 2) continue;  // the pipelined form has no prologue
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
-                    if (variant == 3 && blocks[bi] != 128) continue;  // the capped form uses 128
+                    if (variant >= 3 && blocks[bi] != 128) continue;  // capped forms fix their own block
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
                     float ms = 0;
                     for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -716,7 +716,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || (variant != 0 && variant != 2 && variant != 3) || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 5 || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
 // The same kernel with a register cap: 128-thread blocks, at least MINB resident per SM
 // (65536 / (128 MINB) registers per thread).  MINB = 4 measured fastest on GB300 for every
 // storage form (caps for 5, 6, 8 blocks spilled; the uncapped doublet kernel holds only 12 warps).
-template <int PREC, int NF, int RECON, bool PRO, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+template <int PREC, int NF, int RECON, bool PRO, int MINB, int BS = 128>
+__global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= a.Vh) return;
@@ -495,15 +495,20 @@ template <int PREC>
 cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                int variant, int block, cudaStream_t s)
 {
-    if (variant == 3) {
-        // register-capped launch: 128 threads per block, at least 4 resident blocks per SM
-        const int g128 = (a.Vh + 127) / 128;
-#define TM_LBR(NF, P)                                                             \
-    switch (recon) {                                                              \
-    case 18: k_dslash_lb<PREC, NF, 18, P, 4><<<g128, 128, 0, s>>>(a); break;      \
-    case 12: k_dslash_lb<PREC, NF, 12, P, 4><<<g128, 128, 0, s>>>(a); break;      \
-    case 8: k_dslash_lb<PREC, NF, 8, P, 4><<<g128, 128, 0, s>>>(a); break;        \
-    default: return cudaErrorInvalidValue;                                        \
+    if (variant == 3 || variant == 4 || variant == 5) {
+        // register-capped launches, 128 registers per thread: 128 x 4, 64 x 8 or 256 x 2 blocks per SM
+        const int bs = variant == 3 ? 128 : (variant == 4 ? 64 : 256);
+        const int gb = (a.Vh + bs - 1) / bs;
+#define TM_LB1(NF, R, P)                                                                        \
+    if (variant == 3) k_dslash_lb<PREC, NF, R, P, 4, 128><<<gb, 128, 0, s>>>(a);                 \
+    else if (variant == 4) k_dslash_lb<PREC, NF, R, P, 8, 64><<<gb, 64, 0, s>>>(a);              \
+    else k_dslash_lb<PREC, NF, R, P, 2, 256><<<gb, 256, 0, s>>>(a);
+#define TM_LBR(NF, P)                   \
+    switch (recon) {                    \
+    case 18: { TM_LB1(NF, 18, P) } break; \
+    case 12: { TM_LB1(NF, 12, P) } break; \
+    case 8: { TM_LB1(NF, 8, P) } break;   \
+    default: return cudaErrorInvalidValue; \
     }
         if (nf == 1) {
             if (pro) { TM_LBR(1, true) } else { TM_LBR(1, false) }
@@ -511,6 +516,7 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
             if (pro) { TM_LBR(2, true) } else { TM_LBR(2, false) }
         }
 #undef TM_LBR
+#undef TM_LB1
         return cudaGetLastError();
     }
     const int grid = (a.Vh + block - 1) / block;

@@ -51,8 +51,8 @@ def setup(case, recon):
 
 
 def use_variant(tmq, g, variant, block=128):
-    """Force the hopping-kernel launch choice (variant 1 = thread per site and flavour, doublet only)."""
-    pro_variant = 3 if variant == 3 else 0
+    """Force the hopping-kernel launch choice (0 plain, 2 pipelined, 3/4/5 register-capped 128x4/64x8/256x2)."""
+    pro_variant = variant if variant >= 3 else 0
     tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
 
@@ -85,7 +85,7 @@ def test_pack_unpack_roundtrip(case, prec, recon):
 @pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
-@pytest.mark.parametrize("variant", [0, 2, 3], ids=["site", "pipe", "cap4"])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5], ids=["site", "pipe", "cap128x4", "cap64x8", "cap256x2"])
 def test_precond_op(case, prec, recon, pc, dagger, variant):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
     use_variant(tmq, g, variant, block=64 if variant == 2 else 128)
