@@ -41,11 +41,11 @@ static cudaError_t launch_dslash_multi_pdf(const DslashArgs<df64> &a, int nf, in
                        : launch_dslash_multi_pdf_nf2_r12(a, act, nact, nrhs, s);
 }
 cudaError_t launch_dslash_multi_p64(const DslashArgs<double> &a, int nf, int recon, bool pro, const int *act, int nact,
-                                    int nrhs, cudaStream_t s);
+                                    int nrhs, int rpb, cudaStream_t s);
 cudaError_t launch_dslash_multi_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
-                                    int nrhs, cudaStream_t s);
+                                    int nrhs, int rpb, cudaStream_t s);
 cudaError_t launch_dslash_multi_p16(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
-                                    int nrhs, cudaStream_t s);
+                                    int nrhs, int rpb, cudaStream_t s);
 cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void *canon, int ctype, int parity,
                                cudaStream_t s);
 cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, const tm_field *f, int parity,
@@ -272,7 +272,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.coef = coef;
         a.tw_epi = te;
         a.tw_pro = tp;
-        e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s)
+        e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[0], s)
                   : launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     } else if (pidx == 3) {
         DslashArgs<df64> a;
@@ -298,8 +298,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.tw_epi = to_float(te);
         a.tw_pro = to_float(tp);
         if (multi)
-            e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s)
-                            : launch_dslash_multi_p16(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, s);
+            e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[1], s)
+                            : launch_dslash_multi_p16(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[2], s);
         else
             e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s)
                             : launch_dslash_p16(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
@@ -410,8 +410,10 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     const long V = (long)p->L[0] * p->L[1] * p->L[2] * p->L[3];
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < 4; i++) {
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
+        g->multi_rpb[i] = 4;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     void *Ud = nullptr;
     tm_status st = resolve_canon(U_canon, &Ud, "tm_gauge_create");
@@ -677,6 +679,51 @@ tm_status tm_autotune(tm_gauge *g, void *stream)
             g->tune[pi][pro] = bestc;
         }
     }
+    // multi-RHS block shape (right-hand sides per block), timed on 8 right-hand sides of the
+    // single-RHS buffers' size each: the fields are carved from one allocation of 3 x 8 fields
+    for (int pi = 0; pi < 3 && st == TM_OK; pi++) {
+        const int nr = 8;
+        tm_field_bytes(g, precs[pi], nr, &d, &n);
+        const size_t fbm = ((d + 255) & ~(size_t)255) + ((n + 255) & ~(size_t)255);
+        void *mbuf = nullptr;
+        if (cudaMalloc(&mbuf, 3 * fbm) != cudaSuccess) {
+            cudaGetLastError();
+            break;  // not enough memory for the multi-RHS timing: keep the default shape
+        }
+        st = cuda_check(cudaMemsetAsync(mbuf, 0, 3 * fbm, s), "tm_autotune memset");
+        tm_field f[3];
+        for (int k = 0; k < 3; k++) {
+            f[k].data = (char *)mbuf + k * fbm;
+            f[k].norm = n ? (float *)((char *)mbuf + k * fbm + ((d + 255) & ~(size_t)255)) : nullptr;
+            f[k].prec = precs[pi];
+            f[k].nrhs = nr;
+        }
+        const Twist<double> Ri = make_twist(g, TW_RINV, 0);
+        const int rpbs[3] = {2, 4, 8};
+        float best = 1e30f;
+        int bestr = g->multi_rpb[pi];
+        for (int ri = 0; ri < 3 && st == TM_OK; ri++) {
+            g->multi_rpb[pi] = rpbs[ri];
+            float ms = 0;
+            for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
+                st = cuda_check(cudaEventRecord(e0, s), "event");
+                if (st == TM_OK)
+                    st = dslash_launch(g, &f[0], &f[1], &f[2], 0, 0, EPI_TWX_AXPY, -0.01, &Ri, nullptr, s, nullptr, nr);
+                if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+                if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+                float t = 0;
+                if (st == TM_OK) cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;
+            }
+            if (st == TM_OK && ms < best) {
+                best = ms;
+                bestr = rpbs[ri];
+            }
+        }
+        g->multi_rpb[pi] = bestr;
+        cudaStreamSynchronize(s);
+        cudaFree(mbuf);
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
@@ -697,6 +744,11 @@ tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n)
             if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
             off += (size_t)w;
         }
+    for (int pi = 0; pi < 3; pi++) {
+        int w = snprintf(buf + off, n - off, " %s:m:%d", names[pi], g->multi_rpb[pi]);
+        if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
+        off += (size_t)w;
+    }
     return TM_OK;
 }
 
@@ -704,13 +756,27 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
 {
     if (!g || !text) { set_error("tm_tune_import: null argument"); return TM_ERR_ARG; }
     tm_tune_entry t[3][2];
+    int mr[3];
     memcpy(t, g->tune, sizeof(t));
+    memcpy(mr, g->multi_rpb, sizeof(mr));
     const char *p = text;
     while (*p) {
         while (*p == ' ') p++;
         if (!*p) break;
         char name[8] = {0};
         int pro, variant, block, used = 0;
+        if (sscanf(p, "%3[a-z0-9]:m:%d%n", name, &block, &used) == 2 && used > 0) {
+            // multi-RHS entry "<prec>:m:<right-hand sides per block>"
+            const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
+            if (pi < 0 || (block != 2 && block != 4 && block != 8)) {
+                set_error("tm_tune_import: invalid entry '%.32s'", p);
+                return TM_ERR_ARG;
+            }
+            mr[pi] = block;
+            p += used;
+            continue;
+        }
+        used = 0;
         if (sscanf(p, "%3[a-z0-9]:%d:%d:%d%n", name, &pro, &variant, &block, &used) != 4 || used == 0) {
             set_error("tm_tune_import: cannot parse '%.32s'", p);
             return TM_ERR_ARG;
@@ -725,6 +791,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
         p += used;
     }
     memcpy(g->tune, t, sizeof(t));
+    memcpy(g->multi_rpb, mr, sizeof(mr));
     return TM_OK;
 }
 

@@ -300,23 +300,23 @@ __global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ 
 }
 
 // Several right-hand sides in one launch (multi-RHS, sources share the gauge field).  A block
-// of 128 threads is 32 consecutive sites x 4 right-hand sides, one warp per right-hand side, so
-// every spinor load of a warp is one contiguous 512-byte request and the four warps of a block
-// read the same links (served from L1 after the first); consecutive blocks take the next group
-// of four right-hand sides of the same 32 sites, so the remaining link reads hit L2 and each
-// link leaves DRAM about once per site for all sources.  Slot k of the active set is
-// right-hand side act[k] (act = NULL: k).
-// (the register cap of 128 x 4 applies to the binary32 / binary16 / binary64 forms; double-float
-// code needs about 200-255 registers and is launched without the cap)
-template <int PREC, int NF, int RECON, bool PRO>
-__global__ void __launch_bounds__(128, (PREC == PDF ? 1 : 4))
+// is 32 consecutive sites x RPB right-hand sides, one warp per right-hand side, so every spinor
+// load of a warp is one contiguous 512-byte request and the RPB warps of a block read the same
+// links (served from L1 after the first); consecutive blocks take the next group of RPB
+// right-hand sides of the same 32 sites, so the remaining link reads hit L2 and each link leaves
+// DRAM about once per site for all sources.  RPB (2, 4 or 8) is chosen by the autotuner.
+// Slot k of the active set is right-hand side act[k] (act = NULL: k).
+// (the register cap of 128 registers applies to the binary32 / binary16 / binary64 forms;
+// double-float code needs about 200-255 registers and is launched without the cap)
+template <int PREC, int NF, int RECON, bool PRO, int RPB = 4>
+__global__ void __launch_bounds__(32 * RPB, (PREC == PDF ? 1 : 16 / RPB))
     k_dslash_multi(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act, int nact,
                    int nrhs)
 {
-    const int ngrp = (nact + 3) >> 2;
+    const int ngrp = (nact + RPB - 1) / RPB;
     const int grp = (int)(blockIdx.x % ngrp);
     const long sblk = blockIdx.x / ngrp;
-    const int slot = grp * 4 + (threadIdx.x >> 5);
+    const int slot = grp * RPB + (threadIdx.x >> 5);
     const long cb = sblk * 32 + (threadIdx.x & 31);
     if (slot >= nact || cb >= a.Vh) return;
     const int rhs = act ? __ldg(act + slot) : slot;
@@ -326,14 +326,19 @@ __global__ void __launch_bounds__(128, (PREC == PDF ? 1 : 4))
 
 template <int PREC>
 cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
-                                     const int *act, int nact, int nrhs, cudaStream_t s)
+                                     const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + 3) / 4));
-#define TM_M(NF, R, P) k_dslash_multi<PREC, NF, R, P><<<grid, 128, 0, s>>>(a, act, nact, nrhs)
+    if (rpb != 2 && rpb != 4 && rpb != 8) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + rpb - 1) / rpb));
+#define TM_M1(NF, R, P, B) k_dslash_multi<PREC, NF, R, P, B><<<grid, 32 * B, 0, s>>>(a, act, nact, nrhs)
+#define TM_M(NF, R, P)                     \
+    if (rpb == 2) TM_M1(NF, R, P, 2);      \
+    else if (rpb == 4) TM_M1(NF, R, P, 4); \
+    else TM_M1(NF, R, P, 8);
 #define TM_MR(NF, P)                                          \
-    if (recon == 18) TM_M(NF, 18, P);                         \
-    else if (recon == 12 || PREC == PDF) TM_M(NF, 12, P);     \
-    else TM_M(NF, (PREC == PDF ? 12 : 8), P);
+    if (recon == 18) { TM_M(NF, 18, P) }                      \
+    else if (recon == 12) { TM_M(NF, 12, P) }                 \
+    else { TM_M(NF, 8, P) }
     if (nf == 1) {
         if (pro) { TM_MR(1, true) } else { TM_MR(1, false) }
     } else {
@@ -341,6 +346,7 @@ cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::rea
     }
 #undef TM_MR
 #undef TM_M
+#undef TM_M1
     return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// Instantiations of the fused hopping kernel for FP32 storage (one translation unit per
+// Instantiations of the single-RHS fused hopping kernels for FP32 storage (one translation unit per
 // precision so the three compile in parallel).
 #include "tm_dslash.cuh"
 
@@ -7,10 +7,5 @@ cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, boo
                               cudaStream_t s)
 {
     return launch_dslash_impl<P32>(a, nf, recon, pro, variant, block, s);
-}
-cudaError_t launch_dslash_multi_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
-                                    int nrhs, cudaStream_t s)
-{
-    return launch_dslash_multi_impl<P32>(a, nf, recon, pro, act, nact, nrhs, s);
 }
 }  // namespace tmk

@@ -1,0 +1,11 @@
+// Instantiations of the multi-RHS fused hopping kernel for FP32 storage (2, 4 and 8 right-hand
+// sides per block; a translation unit of its own so it compiles in parallel with the rest).
+#include "tm_dslash.cuh"
+
+namespace tmk {
+cudaError_t launch_dslash_multi_p32(const DslashArgs<float> &a, int nf, int recon, bool pro, const int *act, int nact,
+                                    int nrhs, int rpb, cudaStream_t s)
+{
+    return launch_dslash_multi_impl<P32>(a, nf, recon, pro, act, nact, nrhs, rpb, s);
+}
+}  // namespace tmk

@@ -27,7 +27,8 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
 struct tm_tune_entry {
-    int variant;  // 0: one thread per site; 2: two-stage load pipeline; 3: register-capped (128 x 4)
+    int variant;  // 0: one thread per site; 2: two-stage load pipeline; 3 / 4 / 5: register-capped
+                  // (128 x 4, 64 x 8, 256 x 2 threads x blocks per SM)
     int block;    // threads per block
 };
 
@@ -43,6 +44,7 @@ struct tm_gauge {
     double *scratch;    // reduction partials + device scalars (library-owned)
     double *host_scalars;  // pinned mirror for scalar readback
     tm_tune_entry tune[4][2];  // [precision index][prologue]
+    int multi_rpb[4];          // right-hand sides per block of the multi-RHS kernel (2, 4, 8)
     size_t scratch_bytes;
 };
 

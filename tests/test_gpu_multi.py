@@ -32,9 +32,11 @@ def make(case, nrhs, recon=12):
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", [8, 4, 2])
-def test_multi_rhs_operators_match_oracle(case, prec):
-    nr = 5
+@pytest.mark.parametrize("rpb", [2, 4, 8], ids=["rpb2", "rpb4", "rpb8"])
+def test_multi_rhs_operators_match_oracle(case, prec, rpb):
+    nr = 5  # not a multiple of any block shape: the last group of every shape is ragged
     tmq, p, po, U, g, src = make(case, nr)
+    tmq.tune_import(g, f"f64:m:{rpb} f32:m:{rpb} f16:m:{rpb}")
     t = torch.from_numpy(src)
     xe, xo = tmq.pack(g, t, 0, prec, nrhs=nr), tmq.pack(g, t, 1, prec, nrhs=nr)
     for pc in (0, 1):

@@ -225,11 +225,19 @@ def test_autotune_roundtrip_and_parity():
     tmq_, p, po, U, g, psi, chi = setup(case, 12)
     table = tmq.autotune(g)
     entries = table.split()
-    assert len(entries) == 6 and all(len(e.split(":")) == 4 for e in entries)
+    single = [e for e in entries if e.split(":")[1] != "m"]
+    multi = [e for e in entries if e.split(":")[1] == "m"]
+    assert len(single) == 6 and all(len(e.split(":")) == 4 for e in single)
+    assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8") for e in multi)
     tmq.tune_import(g, table)
     assert tmq.tune_export(g) == table
-    with pytest.raises(tmq.TMError):
-        tmq.tune_import(g, "f32:0:3:100")  # block not a multiple of 32
+    for bad in ("f32:0:3:100",   # block not a multiple of 32
+                "f32:m:3",       # right-hand sides per block not 2, 4 or 8
+                "f32:0:9:128",   # no such variant
+                "f99:0:3:128"):  # no such precision
+        with pytest.raises(tmq.TMError):
+            tmq.tune_import(g, bad)
+    assert tmq.tune_export(g) == table  # a rejected import leaves the table unchanged
     xe, _ = fields(tmq, g, 4, psi)
     out, tmp = tmq.Field(g, 4), tmq.Field(g, 4)
     tmq.precond_op(g, out, xe, tmp, 0, False)
