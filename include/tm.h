@@ -209,9 +209,38 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
 tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_field *b_o, const tm_field *psi_e,
                              int dagger, void *stream);
 
-/* Local twist on one parity: out = R in, R^-1 in (inverse = 1), daggered when dagger = 1. */
+/* Local twist on one parity: out = R in, R^-1 in (inverse = 1), daggered when dagger = 1.
+ * A clover handle's local operator depends on the site: tm_twist returns TM_ERR_ARG there
+ * (use tm_local_op). */
 tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger,
                    void *stream);
+
+/* ------------------------------------------------------------------------------- clover term */
+/*
+ * Clover-improved twisted mass (the combination the paper's Conclusion names as the next step).
+ * After tm_gauge_set_clover(g, c_sw) every operator of the handle uses the local operator
+ *   L(x) = 1 + T(x) + (R - 1),   T(x) = i kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x)
+ * in place of R (eq. 2.1-2.4 with R -> L):  M = L - kappa H,  M_asym = L_ee - kappa^2 H_eo
+ * L_oo^-1 H_oe,  M_sym = 1 - kappa^2 L_ee^-1 H_eo L_oo^-1 H_oe, b'_e and psi_o likewise.
+ * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] (DeGrand-Rossi), F_{mu nu} = (Q - Q^dag)/8 with Q
+ * the four plaquettes of the mu-nu plane that start and end at x (same sense, mu first).
+ * The field is computed on the device from the handle's FP64 links and stored per parity as
+ * C = 1 + T and (C^2 - X^2)^-1 per gamma5 block (X = R - 1) in FP64, FP32 and FP16 (about
+ * 1.15 / 0.58 / 0.33 KB per site; 32^3x64: 2.4 / 1.2 / 0.7 GB).  c_sw = 0 removes the term.
+ * Synchronises `stream`.  With a clover term: operator calls take nrhs = 1 FP64 / FP32 / FP16
+ * fields (no DF64, no multi-RHS, no tm_solve_multi); tm_force returns TM_ERR_ARG (the link
+ * derivative of T is not implemented); tm_prepare_rhs draws one odd temporary from CUDA's
+ * stream-ordered pool (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * Errors: TM_ERR_ARG (non-finite c_sw; C^2 - X^2 numerically singular at some site: the
+ * handle keeps its previous clover state), TM_ERR_NOMEM, TM_ERR_CUDA.
+ */
+tm_status tm_gauge_set_clover(tm_gauge *g, double csw, void *stream);
+
+/* Local operator of one parity: out = L in (inverse = 0) or L^-1 in, daggered when dagger = 1,
+ * on the sites of `parity` (0 even, 1 odd).  L is R without a clover term (then any nrhs and
+ * precision) and 1 + T + (R - 1) with one (nrhs = 1, FP64 / FP32 / FP16). */
+tm_status tm_local_op(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, int inverse, int dagger,
+                      void *stream);
 
 /* ------------------------------------------------------------------------------ solvers */
 /* CG on the normal equations (sec. 2.2: solve_type NORMOP on the even-odd preconditioned

@@ -74,6 +74,7 @@ class Gauge:
     def __init__(self, params: Params, U, stream=None):
         torch = _torch()
         self.params = params
+        self.csw = 0.0
         U = torch.as_tensor(U)
         if U.device.type != "cuda":
             U = U.to("cuda")
@@ -191,6 +192,21 @@ def reconstruct_odd(gauge, psi_o: Field, b_o: Field, psi_e: Field, dagger=False,
 def twist(gauge, out: Field, inp: Field, inverse=False, dagger=False, stream=None):
     L.check(L.load().tm_twist(gauge.h, out.ref(), inp.ref(), int(inverse), int(dagger), _stream(stream)))
     return out
+
+
+def local_op(gauge, out: Field, inp: Field, parity: int, inverse=False, dagger=False, stream=None):
+    """tm_local_op: out = L in (or L^-1, daggered) on the sites of `parity`; L = R, or the clover
+    operator 1 + T + (R - 1) of a handle with a clover term."""
+    L.check(L.load().tm_local_op(gauge.h, out.ref(), inp.ref(), int(parity), int(inverse), int(dagger),
+                                 _stream(stream)))
+    return out
+
+
+def set_clover(gauge, csw: float, stream=None):
+    """tm_gauge_set_clover: add the clover term with coefficient c_sw (0 removes it)."""
+    L.check(L.load().tm_gauge_set_clover(gauge.h, float(csw), _stream(stream)))
+    gauge.csw = float(csw)
+    return gauge
 
 
 def norm2(gauge, x: Field, stream=None) -> float:

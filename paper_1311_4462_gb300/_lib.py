@@ -84,6 +84,8 @@ _SIGS = {
     "tm_g5dot": [vp, FP, FP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp],
     "tm_tune_export": [vp, ctypes.c_char_p, ctypes.c_size_t],
     "tm_tune_import": [vp, ctypes.c_char_p],
+    "tm_gauge_set_clover": [vp, ctypes.c_double, vp],
+    "tm_local_op": [vp, FP, FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
 }
 
 

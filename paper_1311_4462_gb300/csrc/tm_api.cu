@@ -56,6 +56,11 @@ cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field 
                          cudaStream_t s);
 cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
                                 const int *act, int nact, cudaStream_t s);
+cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, cudaStream_t s);
+cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, cudaStream_t s);
+cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon, cudaStream_t s);
+cudaError_t launch_clover_apply(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, bool inverse,
+                                const Twist<double> &X, cudaStream_t s);
 
 static thread_local char g_err[512];
 constexpr int TM_MAX_RHS_API = 64;
@@ -136,6 +141,16 @@ static Twist<double> make_twist(const tm_gauge *g, int kind, int dagger)
             }
         }
     }
+    return t;
+}
+
+// X = R - 1 (R^dag - 1 for the adjoint): the part of the local operator that a clover handle
+// adds to its per-site C = 1 + T
+static Twist<double> clover_x(const tm_gauge *g, int dagger)
+{
+    Twist<double> t = make_twist(g, TW_R, dagger);
+    for (int gi = 0; gi < 2; gi++)
+        for (int f = 0; f < 2; f++) t.m[gi][f][f].r -= 1.0;
     return t;
 }
 
@@ -248,6 +263,8 @@ static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out
     a.Lt = g->p.L[3];
     a.out_parity = out_parity;
     a.tbc = g->p.t_antiperiodic ? 1 : 0;
+    a.clov = pidx < 3 ? g->clov[pidx] : nullptr;
+    a.clov_norm = g->clov_norm;
 }
 
 // Generic fused hopping launch: out = epi(H or H^dag (pro(in))).  With nact > 1 (or a list act of
@@ -264,6 +281,34 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
     const tm_tune_entry tu = g->tune[pidx][pro ? 1 : 0];
     const bool multi = act != nullptr || nact > 1;
     cudaError_t e;
+    if (g->csw != 0.0) {
+        // clover handle: the per-site local operator in the epilogue (tw_epi only marks that an
+        // epilogue applies it; the kernel uses X = R - 1 and the site's clover blocks)
+        if (pidx == 3) { set_error("clover handles have no DF64 form"); return TM_ERR_ARG; }
+        if (multi) { set_error("clover handles take single-RHS fields (nrhs = 1)"); return TM_ERR_ARG; }
+        if (pro) { set_error("internal: no input prologue with a clover term"); return TM_ERR_ARG; }
+        const Twist<double> X = clover_x(g, dagger);
+        if (pidx == 0) {
+            DslashArgs<double> a;
+            fill_common(a, g, out, in, x, out_parity, pidx);
+            a.epilogue = epi;
+            a.sigma = dagger ? -1.0 : 1.0;
+            a.coef = coef;
+            a.tw_epi = X;
+            a.tw_pro = X;
+            e = launch_dslash_clov_p64(a, g->nf, g->p.recon, s);
+        } else {
+            DslashArgs<float> a;
+            fill_common(a, g, out, in, x, out_parity, pidx);
+            a.epilogue = epi;
+            a.sigma = dagger ? -1.0f : 1.0f;
+            a.coef = (float)coef;
+            a.tw_epi = to_float(X);
+            a.tw_pro = a.tw_epi;
+            e = pidx == 1 ? launch_dslash_clov_p32(a, g->nf, g->p.recon, s) : launch_dslash_clov_p16(a, g->nf, g->p.recon, s);
+        }
+        return cuda_check(e, "clover dslash launch");
+    }
     if (pidx == 0) {
         DslashArgs<double> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -361,6 +406,10 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
 {
     const double k2 = g->p.kappa * g->p.kappa;
     const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
+    if (g->csw != 0.0 && (out_e->prec == TM_PREC_DF64 || act != nullptr || nact > 1)) {
+        set_error("clover handles take single-RHS FP64 / FP32 / FP16 fields");
+        return TM_ERR_ARG;
+    }
     if (pc == TM_PC_ASYM) {
         // tmp = R^-1_oo H_oe in ;  out = R_ee in - kappa^2 H_eo tmp
         TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
@@ -372,6 +421,12 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
         return dslash_launch(g, out_e, tmp_o, in_e, 0, 0, EPI_X_TWAXPY, -k2, &Ri, nullptr, s, act, nact);
     }
     // adjoint of the symmetric operator: tmp = R^-dag_oo H^dag_oe R^-dag_ee in ; out = in - kappa^2 H^dag_eo tmp
+    if (g->csw != 0.0) {
+        // clover: L^-dag_ee as a pass into out_e (overwritten by the last launch)
+        TM_TRY(cuda_check(launch_clover_apply(g, out_e, in_e, 0, true, clover_x(g, 1), s), "clover apply"));
+        TM_TRY(dslash_launch(g, tmp_o, out_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
+        return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
+    }
     if (out_e->prec == TM_PREC_DF64) {
         // DF64: the input twist as its own launch into out_e (overwritten by the last launch)
         TM_TRY(cuda_check(launch_twist_active(g, out_e, in_e, Ri, act, nact, s), "twist"));
@@ -466,6 +521,7 @@ tm_status tm_gauge_destroy(tm_gauge *g)
     cudaDeviceSynchronize();
     for (int i = 0; i < 4; i++)
         if (g->links[i]) cudaFree(g->links[i]);
+    clover_free(g);
     if (g->scratch) cudaFree(g->scratch);
     if (g->host_scalars) cudaFreeHost(g->host_scalars);
     delete g;
@@ -602,6 +658,32 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
     cudaStream_t s = (cudaStream_t)stream;
     const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
     const double k = g->p.kappa;
+    if (g->csw != 0.0) {
+        // clover: t_o = L^-1_oo b_o in a temporary from the stream-ordered pool, then
+        // b' = b_e + kappa H_eo t_o (sym: L^-1_ee of that)
+        if (b_o->nrhs != 1) { set_error("clover handles take single-RHS fields (nrhs = 1)"); return TM_ERR_ARG; }
+        size_t db = 0, nb = 0;
+        TM_TRY(tm_field_bytes(g, b_o->prec, 1, &db, &nb));
+        void *tbuf = nullptr;
+        const size_t dpad = (db + 255) & ~(size_t)255;
+        if (cudaMallocAsync(&tbuf, dpad + nb, s) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("tm_prepare_rhs: temporary allocation failed");
+            return TM_ERR_NOMEM;
+        }
+        tm_field t;
+        t.data = tbuf;
+        t.norm = nb ? (float *)((char *)tbuf + dpad) : nullptr;
+        t.prec = b_o->prec;
+        t.nrhs = 1;
+        tm_status st = cuda_check(launch_clover_apply(g, &t, b_o, 1, true, clover_x(g, dagger), s), "clover apply");
+        if (st == TM_OK) {
+            if (pc == TM_PC_SYM && !dagger) st = dslash_launch(g, bprime_e, &t, b_e, 0, 0, EPI_TW_XPAY, k, &Ri, nullptr, s);
+            else st = dslash_launch(g, bprime_e, &t, b_e, 0, dagger, EPI_XPAY, k, nullptr, nullptr, s);
+        }
+        cudaFreeAsync(tbuf, s);
+        return st;
+    }
     // b' = b_e + kappa H_eo (R^-1_oo b_o)   [the R^-1 twist is the prologue on every neighbour]
     if (pc == TM_PC_SYM && !dagger)
         return dslash_launch(g, bprime_e, b_o, b_e, 0, 0, EPI_TW_XPAY, k, &Ri, &Ri, s);
@@ -622,9 +704,23 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
     return dslash_launch(g, psi_o, psi_e, b_o, 1, dagger, EPI_TW_XPAY, g->p.kappa, &Ri, nullptr, (cudaStream_t)stream);
 }
 
-tm_status tm_autotune(tm_gauge *g, void *stream)
+tm_status tm_autotune(tm_gauge *g0, void *stream)
 {
-    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    if (!g0) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    // the tune table chooses among the twisted-mass kernels; a clover handle's kernels have one
+    // launch form, so the table is tuned on a shallow copy of the handle without the clover term
+    tm_gauge gcopy = *g0;
+    gcopy.csw = 0.0;
+    tm_gauge *g = &gcopy;
+    struct CopyBack {
+        tm_gauge *dst;
+        const tm_gauge *src;
+        ~CopyBack()
+        {
+            memcpy(dst->tune, src->tune, sizeof(dst->tune));
+            memcpy(dst->multi_rpb, src->multi_rpb, sizeof(dst->multi_rpb));
+        }
+    } copy_back{g0, g};
     cudaStream_t s = (cudaStream_t)stream;
     const int precs[3] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16};
     const int blocks[4] = {64, 128, 192, 256};
@@ -801,8 +897,44 @@ tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, i
     TM_TRY(check_field(g, out, "out"));
     TM_TRY(check_field(g, in, "in"));
     TM_TRY(same_prec(out, in, "tm_twist"));
+    if (g->csw != 0.0) {
+        set_error("tm_twist: a clover handle's local operator depends on the site; use tm_local_op");
+        return TM_ERR_ARG;
+    }
     const Twist<double> T = make_twist(g, inverse ? TW_RINV : TW_R, dagger);
     return cuda_check(launch_twist(g, out, in, T, (cudaStream_t)stream), "tm_twist");
+}
+
+tm_status tm_local_op(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, int inverse, int dagger,
+                      void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    TM_TRY(check_field(g, in, "in"));
+    TM_TRY(same_prec(out, in, "tm_local_op"));
+    if (parity != 0 && parity != 1) { set_error("tm_local_op: parity must be 0 or 1"); return TM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->csw == 0.0) {
+        const Twist<double> T = make_twist(g, inverse ? TW_RINV : TW_R, dagger);
+        return cuda_check(launch_twist(g, out, in, T, s), "tm_local_op");
+    }
+    if (in->prec == TM_PREC_DF64 || in->nrhs != 1) {
+        set_error("tm_local_op: clover handles take single-RHS FP64 / FP32 / FP16 fields");
+        return TM_ERR_ARG;
+    }
+    return cuda_check(launch_clover_apply(g, out, in, parity, inverse != 0, clover_x(g, dagger), s), "tm_local_op");
+}
+
+tm_status tm_gauge_set_clover(tm_gauge *g, double csw, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    if (!isfinite(csw)) { set_error("tm_gauge_set_clover: c_sw must be finite"); return TM_ERR_ARG; }
+    if (csw == 0.0) {
+        cudaDeviceSynchronize();
+        clover_free(g);
+        return TM_OK;
+    }
+    return clover_build(g, csw, (cudaStream_t)stream);
 }
 
 }  // extern "C"

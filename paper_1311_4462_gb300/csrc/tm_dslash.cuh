@@ -20,6 +20,7 @@
 // For the doublet both flavours are computed by the same thread, so each link is loaded once
 // and used for both (sec. 2.1).
 #pragma once
+#include "tm_clover.cuh"
 #include "tm_core.cuh"
 #include "tm_internal.h"
 
@@ -41,6 +42,8 @@ struct DslashArgs {
     T sigma;  // +1: H, -1: H^dag
     T coef;
     Twist<T> tw_epi, tw_pro;
+    const void *clov;        // clover handles: per-site local operator of this precision (tm_clover.cuh)
+    const float *clov_norm;  // FP16 block scales
 };
 
 template <typename T>
@@ -154,7 +157,16 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
     }
 }
 
-template <int PREC, int NF, int RECON, bool PRO>
+// the local operator of the epilogue: the twist (a constant matrix per gamma5 block, R or R^-1
+// as the host built it) or, for a clover handle, L = C + X or L^-1 of this site with X = tw
+template <int PREC, int NF, bool CLOV, bool INV, typename T>
+__device__ __forceinline__ void local_op(const DslashArgs<T> &a, int cb, T v[NF][24])
+{
+    if constexpr (CLOV) apply_clover<PREC, NF, INV>(a.clov, a.clov_norm, a.out_parity, cb, a.Vh, a.tw_epi, v);
+    else apply_twist<T, NF>(a.tw_epi, v);
+}
+
+template <int PREC, int NF, int RECON, bool PRO, bool CLOV = false>
 __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs)
 {
     using T = typename Traits<PREC>::real;
@@ -247,7 +259,7 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] *= a.coef;
     } else if (epi == EPI_TW) {
-        apply_twist<T, NF>(a.tw_epi, acc);
+        local_op<PREC, NF, CLOV, true>(a, cb, acc);
     } else {
         T xv[NF][24];
         const SC *X = reinterpret_cast<const SC *>(a.x);
@@ -255,13 +267,13 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
         for (int f = 0; f < NF; f++)
             load_spinor<PREC>(X + f * fstride, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv[f]);
         if (epi == EPI_TWX_AXPY) {
-            apply_twist<T, NF>(a.tw_epi, xv);
+            local_op<PREC, NF, CLOV, false>(a, cb, xv);
 #pragma unroll
             for (int f = 0; f < NF; f++)
 #pragma unroll
                 for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
         } else if (epi == EPI_X_TWAXPY) {
-            apply_twist<T, NF>(a.tw_epi, acc);
+            local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
             for (int f = 0; f < NF; f++)
 #pragma unroll
@@ -271,7 +283,7 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
             for (int f = 0; f < NF; f++)
 #pragma unroll
                 for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
-            if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+            if (epi == EPI_TW_XPAY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
         }
     }
     SC *O = reinterpret_cast<SC *>(a.out);
@@ -297,6 +309,33 @@ __global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ 
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= a.Vh) return;
     dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
+}
+
+// Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in
+// the epilogue instead of the constant twist; no input prologue (the operators apply L^-1 to an
+// input as a pass of its own).  The epilogue reads 72 (L) or 144 (L^-1) more reals per site.
+template <int PREC, int NF, int RECON>
+__global__ void __launch_bounds__(128) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+    dslash_body<PREC, NF, RECON, false, true>(a, cb, 0);
+}
+
+template <int PREC>
+cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((a.Vh + 127) / 128);
+#define TM_CL(NF)                                                                   \
+    switch (recon) {                                                                \
+    case 18: k_dslash_clov<PREC, NF, 18><<<grid, 128, 0, s>>>(a); break;            \
+    case 12: k_dslash_clov<PREC, NF, 12><<<grid, 128, 0, s>>>(a); break;            \
+    case 8: k_dslash_clov<PREC, NF, 8><<<grid, 128, 0, s>>>(a); break;              \
+    default: return cudaErrorInvalidValue;                                          \
+    }
+    if (nf == 1) { TM_CL(1) } else { TM_CL(2) }
+#undef TM_CL
+    return cudaGetLastError();
 }
 
 // Several right-hand sides in one launch (multi-RHS, sources share the gauge field).  A block

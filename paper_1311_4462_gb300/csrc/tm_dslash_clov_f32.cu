@@ -1,0 +1,10 @@
+// Instantiations of the clover-twisted-mass hopping kernel for FP32 storage (a translation unit
+// of its own so it compiles in parallel with the rest).
+#include "tm_dslash.cuh"
+
+namespace tmk {
+cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, cudaStream_t s)
+{
+    return launch_dslash_clov_impl<P32>(a, nf, recon, s);
+}
+}  // namespace tmk

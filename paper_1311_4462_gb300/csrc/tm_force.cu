@@ -207,6 +207,10 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
                               int project, void *stream)
 {
     if (!g || !F_canon || !psi_e || !psi_o || !g_e || !g_o) { set_error("tm_force: null argument"); return TM_ERR_ARG; }
+    if (g->csw != 0.0) {
+        set_error("tm_force: the link derivative of the clover term is not implemented");
+        return TM_ERR_ARG;
+    }
     const tm_field *fs[4] = {psi_e, psi_o, g_e, g_o};
     for (auto f : fs) {
         if (!f->data || f->prec != psi_e->prec || f->nrhs != 1 || (f->prec == TM_PREC_F16 && !f->norm)) {

@@ -20,6 +20,10 @@ enum Epilogue {
 // twist selector for host-built coefficient tables
 enum TwistKind { TW_R = 0, TW_RINV = 1 };
 
+// clover field of a handle (tm_clover.cu)
+tm_status clover_build(tm_gauge *g, double csw, cudaStream_t s);
+void clover_free(tm_gauge *g);
+size_t clover_bytes(int pidx, long Vh);
 // operator composition shared by the API and the solvers (tm_api.cu)
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact);
@@ -45,6 +49,9 @@ struct tm_gauge {
     double *host_scalars;  // pinned mirror for scalar readback
     tm_tune_entry tune[4][2];  // [precision index][prologue]
     int multi_rpb[4];          // right-hand sides per block of the multi-RHS kernel (2, 4, 8)
+    double csw;                // clover coefficient; 0: no clover term
+    void *clov[3];             // per-site local clover operator, FP64 / FP32 / FP16 (tm_clover.cuh)
+    float *clov_norm;          // FP16 block scales
     size_t scratch_bytes;
 };
 
@@ -55,6 +62,10 @@ int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
 size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);
 tm_status cuda_check(cudaError_t e, const char *what);
+// clover field of a handle (tm_clover.cu)
+tm_status clover_build(tm_gauge *g, double csw, cudaStream_t s);
+void clover_free(tm_gauge *g);
+size_t clover_bytes(int pidx, long Vh);
 // operator composition shared by the API and the solvers (tm_api.cu)
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact);
