@@ -104,10 +104,12 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(clover=False):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_4462_gb300", "csrc")
-    for f in ["tm_core.cuh", "tm_dslash.cuh", "tm_dslash_f32.cu"]:
+    files = (["tm_core.cuh", "tm_clover.cuh", "tm_dslash.cuh", "tm_dslash_clov_f32.cu"] if clover else
+             ["tm_core.cuh", "tm_dslash.cuh", "tm_dslash_f32.cu"])
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -121,7 +123,7 @@ def read_traffic(kernel_key):
             if line.startswith("#") or not line.strip():
                 continue
             key, srchash, nbytes = line.split()[:3]
-            if key == kernel_key and srchash == kernel_source_hash():
+            if key == kernel_key and srchash == kernel_source_hash(clover=kernel_key.startswith("k_dslash_clov")):
                 return float(nbytes)
     except OSError:
         pass
@@ -167,6 +169,8 @@ def run_ours(args, rank, world):
     else:
         p_nd = tmq.Params(L, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=recon)
     g = tmq.Gauge(p_nd, U)
+    if args.csw:
+        tmq.set_clover(g, args.csw)
     # the full run tunes its launch table; --quick (profiling) keeps the handle's default table so a
     # profiler's kernel filter sees only the benchmark's own launches
     tune_table = tmq.tune_export(g) if args.quick else tmq.autotune(g)
@@ -205,16 +209,19 @@ def run_ours(args, rank, world):
     ta = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
     tb = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
     Vh = p_nd.Vh
-    flops_step = FLOPS_PER_SITE[nf] * Vh
+    flops_site = CLOVER_FLOPS[nf] if args.csw else FLOPS_PER_SITE[nf]
+    flops_step = flops_site * Vh
     total_ms, flops_per_s = aggregate_ranks(e_start.elapsed_time(e_end), flops_step * K, world, dev)
     ms_per_step = total_ms / K
     value = flops_per_s / 1e9
     la, lb = launch_bytes(prec, nf, recon)
+    if args.csw:  # launch A reads the four clover blocks of L^-1, launch B the two of L
+        la, lb = la + CLOVER_BYTES[prec] * 2 // 3, lb + CLOVER_BYTES[prec] // 3
     avg_launch_ms = (sum(ta) + sum(tb)) / (2 * K)
     achieved = ((la + lb) / 2 * Vh) / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_src = load_peaks()
-    traffic = read_traffic("k_dslash_%s_%s_r%d_%s" % (args.prec, "nd" if nf == 2 else "deg", recon,
-                                                      "x".join(map(str, L))))
+    traffic = read_traffic("k_dslash%s_%s_%s_r%d_%s" % ("_clov" if args.csw else "", args.prec,
+                                                        "nd" if nf == 2 else "deg", recon, "x".join(map(str, L))))
 
     result = {
         "metric": "TM dslash GFLOPS & % HBM roofline per precision; CG time-to-1e-10 mixed vs FP64",
@@ -224,14 +231,17 @@ def run_ours(args, rank, world):
         "config": {"workload": ("M_asym (eq. 2.2 LHS), non-degenerate doublet %s, kappa=0.1612, mu=0.135, eps=0.15"
                                 % "x".join(map(str, L)) if nf == 2 else
                                 "M_asym (eq. 2.2 LHS), one flavour %s, kappa=0.1612, mu=0.004"
-                                % "x".join(map(str, L))) + ", %s storage, recon-%d" % (args.prec.upper(), recon),
+                                % "x".join(map(str, L))) + ", %s storage, recon-%d" % (args.prec.upper(), recon)
+                                + (", clover c_sw=%g" % args.csw if args.csw else ""),
                    "lattice": list(L), "flavours": nf, "storage": args.prec, "recon": recon,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: links 403 MB, each spinor parity 201 MB, no flush",
-                   "flops_per_even_site": FLOPS_PER_SITE[nf], "bytes_per_even_site": asym_bytes(prec, nf, recon)},
+                   "flops_per_even_site": flops_site,
+                   "bytes_per_even_site": asym_bytes(prec, nf, recon) + (CLOVER_BYTES[prec] if args.csw else 0)},
         "gpu_launches": 2 * K,
-        "roofline": {"bound": "hbm", "kernel": "k_dslash<%s, %s, recon-%d> (both launches of M_asym)"
-                     % (args.prec.upper(), "doublet" if nf == 2 else "one flavour", recon),
+        "roofline": {"bound": "hbm", "kernel": "%s<%s, %s, recon-%d> (both launches of M_asym)"
+                     % ("k_dslash_clov" if args.csw else "k_dslash", args.prec.upper(),
+                        "doublet" if nf == 2 else "one flavour", recon),
                      "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "bytes_per_launch_algorithmic": (la + lb) / 2 * Vh,
@@ -239,7 +249,7 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "launch_table": tune_table,
     }
-    if rank == 0 and not args.quick and (args.prec, nf, recon, L) != ("f32", 2, 12, (32, 32, 32, 64)):
+    if rank == 0 and not args.quick and (args.prec, nf, recon, L, args.csw) != ("f32", 2, 12, (32, 32, 32, 64), 0.0):
         args.quick = True  # the extra sections describe the default workload only
     if rank == 0 and not args.quick:
         result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
@@ -247,6 +257,7 @@ def run_ours(args, rank, world):
         result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
+        result["clover"] = clover_section(tmq, U, psi, dev, args)
         result["cpu_baseline"] = cpu_baseline(U_np, psi_np, args)
     result["input_generation_s"] = round(gen_s, 2)
     g.close()
@@ -502,6 +513,70 @@ def cg_section(tmq, g, U, psi, dev, args):
     return res
 
 
+# clover-twisted-mass (the paper's next step): flops and bytes per even site of M_asym, in the
+# flop convention above (hermitian 6x6 block times a vector: 252 flops; L = two blocks per
+# flavour plus the twist, L^-1 = four blocks per flavour plus the twist)
+CLOVER_CSW = 1.6
+CLOVER_FLOPS = {1: 2 * 1320 + (4 * 252 + 48) + (2 * 252 + 48) + 48,
+                2: 4 * 1320 + (8 * 252 + 192) + (4 * 252 + 192) + 96}
+CLOVER_BYTES = {8: 6 * 36 * 8, 4: 6 * 36 * 4, 2: 6 * (80 + 4)}  # 4 blocks (launch A) + 2 blocks (launch B)
+
+
+def clover_section(tmq, U, psi, dev, args):
+    """TM-clover M_asym / M_sym (c_sw = 1.6) at 32^3x64 for both doublets and all storage precisions,
+    and time to 1e-10 of FP64 CG vs mixed FP32 CG for the non-degenerate doublet."""
+    import torch
+    peak, _ = load_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rows = []
+    cg = {}
+    tables = {}
+    for nf, mu, eps in [(1, MU_DEG, 0.0), (2, MU_ND, EPS_ND)]:
+        p = tmq.Params(L_FULL, KAPPA, mu, eps, flavor=(tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS),
+                       recon=12)
+        g = tmq.Gauge(p, U)
+        tmq.set_clover(g, CLOVER_CSW)
+        tables["flavours_%d" % nf] = tmq.autotune(g)
+        src = psi if nf == 2 else psi[..., :1, :, :].contiguous()
+        for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16, tmq.TM_PREC_F64):
+            xe = tmq.pack(g, src, 0, prec)
+            out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+            for pc in (0, 1):
+                reps = 3 if prec == 8 else 10
+                ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, pc, False), reps, flush)
+                fl = CLOVER_FLOPS[nf] * p.Vh
+                by = (asym_bytes(prec, nf, 12) + CLOVER_BYTES[prec]) * p.Vh
+                rows.append({"op": "M_sym" if pc else "M_asym", "flavours": nf,
+                             "prec": {8: "f64", 4: "f32", 2: "f16"}[prec], "recon": 12, "us": round(ms * 1e3, 1),
+                             "gflops": round(fl / (ms * 1e-3) / 1e9, 1), "gbs": round(by / (ms * 1e-3) / 1e9, 1),
+                             "hbm_frac": round(by / (ms * 1e-3) / 1e9 / peak, 3)})
+            del xe, out, tmp
+        if nf == 2:
+            be, bo = tmq.pack(g, psi, 0, tmq.TM_PREC_F64), tmq.pack(g, psi, 1, tmq.TM_PREC_F64)
+            bp = tmq.Field(g, tmq.TM_PREC_F64)
+            tmq.prepare_rhs(g, bp, be, bo, 0, False)
+
+            def solve(**kw):
+                xe = tmq.Field(g, tmq.TM_PREC_F64)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = tmq.solve(g, xe, bp, tol=1e-10, maxiter=20000, check=False, **kw)
+                e1.record()
+                torch.cuda.synchronize()
+                return {"ms": round(e0.elapsed_time(e1), 2), "iterations": st["iterations"],
+                        "reliable_updates": st["reliable_updates"], "true_residual": st["true_residual"],
+                        "status": st["status"]}
+
+            solve(solver="mixed", sloppy_prec=tmq.TM_PREC_F32)  # warm-up
+            cg = {"fp64_cg": solve(solver="cg"), "mixed_f32": solve(solver="mixed", sloppy_prec=tmq.TM_PREC_F32),
+                  "mixed_f16": solve(solver="mixed", sloppy_prec=tmq.TM_PREC_F16)}
+            cg["speedup_mixed_vs_fp64"] = round(cg["fp64_cg"]["ms"] / min(cg["mixed_f32"]["ms"], cg["mixed_f16"]["ms"]), 2)
+        g.close()
+    return {"csw": CLOVER_CSW, "lattice": list(L_FULL), "flops_per_even_site": CLOVER_FLOPS,
+            "operators": rows, "cg_nd_asym_tol_1e-10": cg, "launch_tables": tables}
+
+
 def batching_section(tmq, U, dev, args):
     """Loop estimator Tr[gamma5 M^-1] on the 32^3x64 one-flavour lattice (kappa 0.1612, mu 0.004):
     256 Z2 sources, 16 per batched mixed-precision CG to 1e-8 with source dropping and CUDA-graph
@@ -623,6 +698,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline step only (no tables, e2e or baselines)")
+    ap.add_argument("--csw", type=float, default=0.0, help="time the clover-twisted-mass operator with this c_sw")
     ap.add_argument("--lattice", default=None, help="override the lattice, e.g. 32,32,32,32 (profiling runs)")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline storage (profiling runs)")
     ap.add_argument("--nf", type=int, default=2, choices=[1, 2], help="flavours of the headline step (profiling runs)")

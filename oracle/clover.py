@@ -173,3 +173,34 @@ def cg_normal(p: Params, U, csw: float, y, sym=False, dagger=False, tol=1e-12, m
         it += 1
     res = np.linalg.norm(y - AA(x)) / np.linalg.norm(y)
     return x, it, float(res)
+
+
+def apply_M_pc_at(p: Params, U, csw: float, psi, sites, sym=False, dagger=False, R=4):
+    """(M_pc psi)(x) at the given even sites x = (x, y, z, t), one by one, for lattices too large
+    for the whole-lattice oracle.  Each output depends only on psi within two hops and on links
+    within three hops of x, so it is the output at the centre of the whole-lattice oracle applied
+    to a 2R^4 patch (R = 4: coordinates x-4 ... x+3, periodic copy of the lattice around x).  The
+    patch is periodic in every direction: the antiperiodic time boundary of the lattice is carried
+    by negating U_t on its last time slice (every plaquette contains those links in pairs, so F is
+    unchanged, and each hop across the boundary picks up the -1).  Returns complex
+    [len(sites), nf, 4, 3]."""
+    Lx, Ly, Lz, Lt = p.L
+    n = 2 * R
+    assert min(p.L) >= n, "the lattice must be at least as large as the patch"
+    Ug = np.array(U, dtype=np.complex128, copy=True)
+    if p.t_antiperiodic:
+        Ug[3, Lt - 1] *= -1.0
+    pp = Params((n, n, n, n), p.kappa, p.mu, p.eps, flavor=p.flavor, t_antiperiodic=False)
+    out = []
+    for (x, y, z, t) in sites:
+        assert (x + y + z + t) % 2 == 0, "even sites only"
+        it = (np.arange(n) + t - R) % Lt
+        iz = (np.arange(n) + z - R) % Lz
+        iy = (np.arange(n) + y - R) % Ly
+        ix = (np.arange(n) + x - R) % Lx
+        sl = np.ix_(it, iz, iy, ix)
+        Up = np.stack([Ug[mu][sl] for mu in range(4)])
+        ps = np.asarray(psi)[sl]
+        r = apply_M_pc(pp, Up, csw, _proj(pp, ps, 0), sym=sym, dagger=dagger)
+        out.append(r[R, R, R, R])
+    return np.stack(out)

@@ -56,9 +56,9 @@ cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field 
                          cudaStream_t s);
 cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
                                 const int *act, int nact, cudaStream_t s);
-cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, cudaStream_t s);
-cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, cudaStream_t s);
-cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon, cudaStream_t s);
+cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, int minb, cudaStream_t s);
+cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
+cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_clover_apply(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, bool inverse,
                                 const Twist<double> &X, cudaStream_t s);
 
@@ -296,7 +296,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.coef = coef;
             a.tw_epi = X;
             a.tw_pro = X;
-            e = launch_dslash_clov_p64(a, g->nf, g->p.recon, s);
+            e = launch_dslash_clov_p64(a, g->nf, g->p.recon, g->clov_minb[0], s);
         } else {
             DslashArgs<float> a;
             fill_common(a, g, out, in, x, out_parity, pidx);
@@ -305,7 +305,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.coef = (float)coef;
             a.tw_epi = to_float(X);
             a.tw_pro = a.tw_epi;
-            e = pidx == 1 ? launch_dslash_clov_p32(a, g->nf, g->p.recon, s) : launch_dslash_clov_p16(a, g->nf, g->p.recon, s);
+            e = pidx == 1 ? launch_dslash_clov_p32(a, g->nf, g->p.recon, g->clov_minb[1], s)
+                           : launch_dslash_clov_p16(a, g->nf, g->p.recon, g->clov_minb[2], s);
         }
         return cuda_check(e, "clover dslash launch");
     }
@@ -468,6 +469,8 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     for (int i = 0; i < 4; i++) {
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
         g->multi_rpb[i] = 4;
+        // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
+        if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
     }
     cudaStream_t s = (cudaStream_t)stream;
     void *Ud = nullptr;
@@ -774,6 +777,30 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             }
             g->tune[pi][pro] = bestc;
         }
+        if (g0->csw != 0.0 && st == TM_OK) {
+            // clover kernel occupancy, timed on the heavier launch (the inverse L^-1 epilogue)
+            const int minbs[3] = {1, 3, 4};
+            float best = 1e30f;
+            int bestm = g0->clov_minb[pi];
+            for (int mi = 0; mi < 3 && st == TM_OK; mi++) {
+                g0->clov_minb[pi] = minbs[mi];
+                float ms = 0;
+                for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
+                    st = cuda_check(cudaEventRecord(e0, s), "event");
+                    if (st == TM_OK) st = dslash_launch(g0, &f[0], &f[1], nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s);
+                    if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+                    if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+                    float t = 0;
+                    if (st == TM_OK) cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) ms += t;
+                }
+                if (st == TM_OK && ms < best) {
+                    best = ms;
+                    bestm = minbs[mi];
+                }
+            }
+            g0->clov_minb[pi] = bestm;
+        }
     }
     // multi-RHS block shape (right-hand sides per block), timed on 8 right-hand sides of the
     // single-RHS buffers' size each: the fields are carved from one allocation of 3 x 8 fields
@@ -845,6 +872,11 @@ tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n)
         if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
         off += (size_t)w;
     }
+    for (int pi = 0; pi < 3; pi++) {
+        int w = snprintf(buf + off, n - off, " %s:c:%d", names[pi], g->clov_minb[pi]);
+        if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
+        off += (size_t)w;
+    }
     return TM_OK;
 }
 
@@ -852,9 +884,10 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
 {
     if (!g || !text) { set_error("tm_tune_import: null argument"); return TM_ERR_ARG; }
     tm_tune_entry t[3][2];
-    int mr[3];
+    int mr[3], cm[3];
     memcpy(t, g->tune, sizeof(t));
     memcpy(mr, g->multi_rpb, sizeof(mr));
+    memcpy(cm, g->clov_minb, sizeof(cm));
     const char *p = text;
     while (*p) {
         while (*p == ' ') p++;
@@ -869,6 +902,18 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
                 return TM_ERR_ARG;
             }
             mr[pi] = block;
+            p += used;
+            continue;
+        }
+        used = 0;
+        if (sscanf(p, "%3[a-z0-9]:c:%d%n", name, &block, &used) == 2 && used > 0) {
+            // clover entry "<prec>:c:<resident blocks per SM>"
+            const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
+            if (pi < 0 || (block != 1 && block != 3 && block != 4)) {
+                set_error("tm_tune_import: invalid entry '%.32s'", p);
+                return TM_ERR_ARG;
+            }
+            cm[pi] = block;
             p += used;
             continue;
         }
@@ -888,6 +933,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
     }
     memcpy(g->tune, t, sizeof(t));
     memcpy(g->multi_rpb, mr, sizeof(mr));
+    memcpy(g->clov_minb, cm, sizeof(cm));
     return TM_OK;
 }
 

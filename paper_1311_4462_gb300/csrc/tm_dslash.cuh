@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ 
 // Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in
 // the epilogue instead of the constant twist; no input prologue (the operators apply L^-1 to an
 // input as a pass of its own).  The epilogue reads 72 (L) or 144 (L^-1) more reals per site.
-template <int PREC, int NF, int RECON>
-__global__ void __launch_bounds__(128) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+template <int PREC, int NF, int RECON, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= a.Vh) return;
@@ -323,18 +323,26 @@ __global__ void __launch_bounds__(128) k_dslash_clov(const __grid_constant__ Dsl
 }
 
 template <int PREC>
-cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, cudaStream_t s)
+cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, int minb,
+                                    cudaStream_t s)
 {
+    // minb: resident 128-thread blocks per SM the register allocation must allow (1, 3 or 4)
+    if (minb != 1 && minb != 3 && minb != 4) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((a.Vh + 127) / 128);
-#define TM_CL(NF)                                                                   \
-    switch (recon) {                                                                \
-    case 18: k_dslash_clov<PREC, NF, 18><<<grid, 128, 0, s>>>(a); break;            \
-    case 12: k_dslash_clov<PREC, NF, 12><<<grid, 128, 0, s>>>(a); break;            \
-    case 8: k_dslash_clov<PREC, NF, 8><<<grid, 128, 0, s>>>(a); break;              \
-    default: return cudaErrorInvalidValue;                                          \
+#define TM_CL1(NF, R)                                                               \
+    if (minb == 1) k_dslash_clov<PREC, NF, R, 1><<<grid, 128, 0, s>>>(a);           \
+    else if (minb == 3) k_dslash_clov<PREC, NF, R, 3><<<grid, 128, 0, s>>>(a);      \
+    else k_dslash_clov<PREC, NF, R, 4><<<grid, 128, 0, s>>>(a);
+#define TM_CL(NF)                          \
+    switch (recon) {                       \
+    case 18: { TM_CL1(NF, 18) } break;     \
+    case 12: { TM_CL1(NF, 12) } break;     \
+    case 8: { TM_CL1(NF, 8) } break;       \
+    default: return cudaErrorInvalidValue; \
     }
     if (nf == 1) { TM_CL(1) } else { TM_CL(2) }
 #undef TM_CL
+#undef TM_CL1
     return cudaGetLastError();
 }
 

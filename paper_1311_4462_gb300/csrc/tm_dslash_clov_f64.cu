@@ -3,8 +3,8 @@
 #include "tm_dslash.cuh"
 
 namespace tmk {
-cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, cudaStream_t s)
+cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, int minb, cudaStream_t s)
 {
-    return launch_dslash_clov_impl<P64>(a, nf, recon, s);
+    return launch_dslash_clov_impl<P64>(a, nf, recon, minb, s);
 }
 }  // namespace tmk

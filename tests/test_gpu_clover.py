@@ -137,6 +137,35 @@ def test_mixed_cg_reaches_fp64_tolerance(case, sloppy):
     assert rel(cl.apply_M(po, U, CSW, psi), b) < 1e-6
 
 
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("minb", [1, 3, 4])
+def test_occupancy_forms(case, minb):
+    tmq, p, po, U, g, psi = setup(case)
+    saved = tmq.tune_export(g)
+    tmq.tune_import(g, f"f64:c:{minb} f32:c:{minb} f16:c:{minb}")
+    try:
+        pe = orc.project_parity(po, psi, 0)
+        for prec in (8, 4, 2):
+            xe = tmq.pack(g, torch.from_numpy(psi), 0, prec)
+            for sym in (0, 1):
+                out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+                tmq.precond_op(g, out, xe, tmp, sym, False)
+                assert rel(get(tmq, g, out, 0), cl.apply_M_pc(po, U, CSW, pe, sym=bool(sym))) < TOL[prec]
+    finally:
+        tmq.tune_import(g, saved)
+
+
+def test_autotune_on_a_clover_handle():
+    tmq, p, po, U, g, psi = setup(CASES[2])
+    table = tmq.autotune(g)
+    clov = [e for e in table.split() if e.split(":")[1] == "c"]
+    assert len(clov) == 3
+    xe = tmq.pack(g, torch.from_numpy(psi), 0, 4)
+    out, tmp = tmq.Field(g, 4), tmq.Field(g, 4)
+    tmq.precond_op(g, out, xe, tmp, 0, False)
+    assert rel(get(tmq, g, out, 0), cl.apply_M_pc(po, U, CSW, orc.project_parity(po, psi, 0))) < TOL[4]
+
+
 def test_removing_the_clover_term_restores_twisted_mass():
     import paper_1311_4462_gb300 as tmq
     name, L, flavor, kappa, mu, eps = CASES[2]

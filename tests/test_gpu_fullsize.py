@@ -6,6 +6,8 @@
   system residual recomputed by the oracle.
 * 32^3x64 one flavour: four sources through one multi-RHS operator launch, each against the oracle.
 * 24^3x48 one flavour: the link force against the oracle's.
+* 32^3x64 clover-twisted mass (both doublets): M_pc on 12 sampled sites against the one-site-at-a-time
+  clover oracle.
 Each oracle application at these sizes takes a few seconds on the host cores.
 """
 import numpy as np
@@ -108,4 +110,41 @@ def test_force_24x24x24x48():
         if prec == 8:
             ref = orc.force(po, U, psi, gv, coef=1.0, project=True)
         assert rel(F, ref) < tol
+    g.close()
+
+
+@pytest.mark.parametrize("nf", [1, 2], ids=["one_flavour", "doublet"])
+def test_clover_32x32x32x64_sampled_sites(nf):
+    """TM-clover M_pc at the benchmark's lattice and launch configuration (autotuned handle, c_sw
+    1.6), against the one-site-at-a-time clover oracle on 12 sampled even sites (including both
+    time-boundary slices)."""
+    import paper_1311_4462_gb300 as tmq
+    from oracle import clover as cl
+    L = (32, 32, 32, 64)
+    mu, eps, flavor = (0.135, 0.15, 2) if nf == 2 else (0.004, 0.0, 1)
+    p = tmq.Params(L, 0.1612, mu, eps, flavor=flavor, recon=12)
+    po = orc.Params(L, 0.1612, mu, eps, flavor=flavor)
+    U = inputs.gauge_field(L, 1002)
+    psi = inputs.spinor_field(L, nf, 2002)
+    g = tmq.Gauge(p, torch.from_numpy(U))
+    tmq.set_clover(g, 1.6)
+    tmq.autotune(g)
+    rng = np.random.default_rng(77)
+    sites = []
+    while len(sites) < 12:
+        x, y, z = (int(v) for v in rng.integers(0, 32, size=3))
+        t = [0, 63][len(sites)] if len(sites) < 2 else int(rng.integers(0, 64))
+        if (x + y + z + t) % 2 == 0:
+            sites.append((x, y, z, t))
+    for sym in (False, True):
+        ref = cl.apply_M_pc_at(po, U, 1.6, psi, sites, sym=sym)
+        for prec, tol in ((4, 1e-6), (2, 5e-3), (8, 1e-13)):
+            if sym and prec != 4:
+                continue
+            xe = tmq.pack(g, torch.from_numpy(psi), 0, prec)
+            out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+            tmq.precond_op(g, out, xe, tmp, int(sym), False)
+            got = tmq.unpack(g, out, 0).cpu().numpy()
+            got = np.stack([got[t, z, y, x] for (x, y, z, t) in sites])
+            assert rel(got, ref) < tol, (sym, prec, rel(got, ref))
     g.close()

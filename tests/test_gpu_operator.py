@@ -225,14 +225,17 @@ def test_autotune_roundtrip_and_parity():
     tmq_, p, po, U, g, psi, chi = setup(case, 12)
     table = tmq.autotune(g)
     entries = table.split()
-    single = [e for e in entries if e.split(":")[1] != "m"]
+    single = [e for e in entries if e.split(":")[1] not in ("m", "c")]
     multi = [e for e in entries if e.split(":")[1] == "m"]
+    clov = [e for e in entries if e.split(":")[1] == "c"]
     assert len(single) == 6 and all(len(e.split(":")) == 4 for e in single)
     assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8") for e in multi)
+    assert len(clov) == 3 and all(e.split(":")[2] in ("1", "3", "4") for e in clov)
     tmq.tune_import(g, table)
     assert tmq.tune_export(g) == table
     for bad in ("f32:0:3:100",   # block not a multiple of 32
                 "f32:m:3",       # right-hand sides per block not 2, 4 or 8
+                "f16:c:2",       # clover occupancy not 1, 3 or 4
                 "f32:0:9:128",   # no such variant
                 "f99:0:3:128"):  # no such precision
         with pytest.raises(tmq.TMError):

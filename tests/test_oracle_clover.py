@@ -235,3 +235,20 @@ def test_cg_reaches_the_dense_solution():
     assert res < 1e-11 and it > 0
     psi = x + cl.reconstruct_odd(p, U, csw, x, b)
     assert rel(cl.apply_M(p, U, csw, psi), b) < 1e-9
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2]], ids=["plus", "nd"])
+def test_patch_oracle_matches_the_whole_lattice_oracle(case):
+    """The one-site-at-a-time oracle used at full lattice sizes agrees with the whole-lattice one,
+    including sites next to the antiperiodic time boundary and the periodic wraps."""
+    L = (8, 10, 8, 12)
+    p = params(case, L)
+    U = inputs.gauge_field(L, 1710)
+    psi = inputs.spinor_field(L, p.nf, 2710)
+    pe = orc.project_parity(p, psi, 0)
+    sites = [(0, 0, 0, 0), (7, 9, 0, 0), (1, 3, 2, 10), (6, 2, 4, 6), (3, 9, 7, 11), (2, 2, 2, 0), (7, 1, 1, 11)]
+    for sym, dag in ((False, False), (True, False), (False, True), (True, True)):
+        full = cl.apply_M_pc(p, U, 1.3, pe, sym=sym, dagger=dag)
+        got = cl.apply_M_pc_at(p, U, 1.3, psi, sites, sym=sym, dagger=dag)
+        want = np.stack([full[t, z, y, x] for (x, y, z, t) in sites])
+        assert np.abs(got - want).max() < 1e-13 * np.abs(want).max(), (sym, dag)
