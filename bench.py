@@ -148,6 +148,21 @@ def aggregate_ranks(total_ms, units_local, world, device=None):
 
 
 # ------------------------------------------------------------------------------------------- ours
+FORMS = {0: "thread per site", 2: "register pipeline", 3: "register cap 128x4", 4: "register cap 64x8",
+         5: "register cap 256x2", 6: "shared-memory staged pipeline (cp.async)"}
+
+
+def launch_form(table, prec, csw=0.0):
+    """The launch form the tune table selects for this precision's no-prologue hopping launches."""
+    for e in table.split():
+        f = e.split(":")
+        if csw and f[0] == prec and f[1] == "c":
+            return "clover, %s blocks per SM" % f[2]
+        if not csw and f[0] == prec and f[1] == "0":
+            return "%s (variant %s)" % (FORMS.get(int(f[2]), "?"), f[2])
+    return "?"
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -239,9 +254,9 @@ def run_ours(args, rank, world):
                    "flops_per_even_site": flops_site,
                    "bytes_per_even_site": asym_bytes(prec, nf, recon) + (CLOVER_BYTES[prec] if args.csw else 0)},
         "gpu_launches": 2 * K,
-        "roofline": {"bound": "hbm", "kernel": "%s<%s, %s, recon-%d> (both launches of M_asym)"
+        "roofline": {"bound": "hbm", "kernel": "%s<%s, %s, recon-%d> (both launches of M_asym; launch form %s)"
                      % ("k_dslash_clov" if args.csw else "k_dslash", args.prec.upper(),
-                        "doublet" if nf == 2 else "one flavour", recon),
+                        "doublet" if nf == 2 else "one flavour", recon, launch_form(tune_table, args.prec, args.csw)),
                      "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "bytes_per_launch_algorithmic": (la + lb) / 2 * Vh,

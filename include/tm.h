@@ -337,20 +337,23 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
 /* ---------------------------------------------------------------------------- autotuning */
 /*
  * Time every launch choice of the hopping kernel (thread per site with 64-256 threads per block,
- * the same with a two-stage load pipeline, or with a 128-register cap in three block shapes) for
+ * the same with a two-stage load pipeline in registers or in shared memory, or with a
+ * 128-register cap in three block shapes) for
  * each precision, with and without the input-twist prologue, and the multi-RHS block shape (2, 4
  * or 8 right-hand sides per block, timed on 8 right-hand sides), on this handle's lattice, and
  * keep the fastest; with a clover term also the clover kernel's occupancy (1, 3 or 4 blocks per
  * SM).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
- * uses defaults (capped 128 x 4; 4 right-hand sides per block; clover 1 block per SM for FP64,
- * 3 for FP32 / FP16).
+ * uses defaults (capped 128 x 4; FP32 without prologue the shared-memory pipeline unless one
+ * flavour with 18-real links; 4 right-hand sides per block; clover 1 block per SM for FP64, 3 for
+ * FP16 and the FP32 doublet, 4 for FP32 one flavour).
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text, and back.  Single-RHS entries "f32:0:3:128" = precision:prologue:
- * variant:block (variant 0 plain, 2 pipelined, 3 / 4 / 5 capped at 128 registers with 128 / 64 /
- * 256-thread blocks); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
+ * variant:block (variant 0 plain, 2 pipelined in registers, 3 / 4 / 5 capped at 128 registers with
+ * 128 / 64 / 256-thread blocks, 6 pipelined through shared memory with cp.async; 2 and 6 have no
+ * prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4).  Import accepts any subset of the entries; an
  * invalid entry leaves the table unchanged and returns TM_ERR_ARG. */

@@ -467,7 +467,10 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
     for (int i = 0; i < 4; i++) {
-        for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};  // measured best on GB300 for every storage form
+        // measured on GB300 at 32^3x64: the register cap (3) for every storage form, and for FP32
+        // without prologue the shared-memory staged pipeline (6) except one flavour with 18-real links
+        for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};
+        if (i == 1 && (p->recon != 18 || p->flavor == TM_NDEG_DOUBLET)) g->tune[i][0] = tm_tune_entry{6, 128};
         g->multi_rpb[i] = 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
@@ -751,10 +754,10 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
         for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
             float best = 1e30f;
             tm_tune_entry bestc = g->tune[pi][pro];
-            const int variants[5] = {0, 2, 3, 4, 5};
-            for (int vi = 0; vi < 5; vi++) {
+            const int variants[6] = {0, 2, 3, 4, 5, 6};
+            for (int vi = 0; vi < 6; vi++) {
                 const int variant = variants[vi];
-                if (pro && variant == 2) continue;  // the pipelined form has no prologue
+                if (pro && (variant == 2 || variant >= 6)) continue;  // the pipelined forms have no prologue
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
                     if (variant >= 3 && blocks[bi] != 128) continue;  // capped forms fix their own block
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
@@ -923,7 +926,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 5 || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 6 || (pro && variant == 6) || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

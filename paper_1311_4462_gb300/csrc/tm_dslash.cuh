@@ -542,6 +542,238 @@ __global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ Dsl
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
+// ------------------------------------------------------------------------------------------
+// Variant 6: the two-stage pipeline of variant 2 with the staging in shared memory instead of
+// registers.  cp.async copies the raw chunks of hop h+1 (link, neighbour spinors, FP16 norms)
+// into this thread's slots of a double buffer while hop h is computed, so every warp keeps a
+// hop of loads in flight during its arithmetic without holding them in registers.  Shared
+// memory per block: 2 buffers x 128 threads x (link + spinor + norm bytes of one hop), laid out
+// [chunk][thread] so a warp's 16-byte reads are conflict-free.  Each thread reads back only its
+// own copies (cp.async.wait_group), so no block barrier is needed.
+template <int PREC, int RECON, int NF>
+struct AsyncHop {
+    using LC = typename LinkLayout<PREC, RECON>::chunk;
+    using SC = typename Traits<PREC>::schunk;
+    static constexpr int NL = LinkLayout<PREC, RECON>::N;
+    static constexpr int NS = NF * Traits<PREC>::SCHUNKS;
+    static constexpr int NN = (PREC == P16) ? NF : 0;
+    static constexpr int BS = 128;
+    static constexpr int LBYTES = NL * BS * (int)sizeof(LC);  // a multiple of 16
+    static constexpr int BUF = LBYTES + NS * BS * 16 + NN * BS * 4;
+};
+
+template <int N>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const size_t g = __cvta_generic_to_global(gmem);
+    if constexpr (N == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(g) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(g), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int PREC, int RECON, int NF>
+__device__ __forceinline__ void async_fetch_hop(char *buf, int tid, const typename LinkLayout<PREC, RECON>::chunk *g,
+                                                int lcb, const typename Traits<PREC>::schunk *in, const float *in_norm,
+                                                int nb, int Vh)
+{
+    using H = AsyncHop<PREC, RECON, NF>;
+    using LC = typename H::LC;
+    using SC = typename H::SC;
+    LC *sl = reinterpret_cast<LC *>(buf);
+    SC *ss = reinterpret_cast<SC *>(buf + H::LBYTES);
+#pragma unroll
+    for (int k = 0; k < H::NL; k++) cp_async<(int)sizeof(LC)>(sl + k * H::BS + tid, g + (size_t)k * Vh + lcb);
+#pragma unroll
+    for (int k = 0; k < H::NS; k++) cp_async<16>(ss + k * H::BS + tid, in + (size_t)k * Vh + nb);
+    if constexpr (H::NN > 0) {
+        float *sn = reinterpret_cast<float *>(buf + H::LBYTES + H::NS * H::BS * 16);
+#pragma unroll
+        for (int f = 0; f < H::NN; f++) cp_async<4>(sn + f * H::BS + tid, in_norm + (size_t)f * Vh + nb);
+    }
+}
+
+template <int PREC, int RECON, int NF, int MU, bool FWD, typename T>
+__device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *buf, int tid, T sp, T sg)
+{
+    using H = AsyncHop<PREC, RECON, NF>;
+    using LC = typename H::LC;
+    using SC = typename H::SC;
+    HopRaw<PREC, RECON, NF> r;
+    const LC *sl = reinterpret_cast<const LC *>(buf);
+    const SC *ss = reinterpret_cast<const SC *>(buf + H::LBYTES);
+#pragma unroll
+    for (int k = 0; k < H::NL; k++) r.l[k] = sl[k * H::BS + tid];
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+#pragma unroll
+        for (int k = 0; k < Traits<PREC>::SCHUNKS; k++) r.s[f][k] = ss[(f * Traits<PREC>::SCHUNKS + k) * H::BS + tid];
+    if constexpr (H::NN > 0) {
+        const float *sn = reinterpret_cast<const float *>(buf + H::LBYTES + H::NS * H::BS * 16);
+#pragma unroll
+        for (int f = 0; f < NF; f++) r.n[f] = sn[f * H::BS + tid];
+    }
+    compute_hop<PREC, RECON, NF, MU, FWD>(acc, r, sp, sg);
+}
+
+// the epilogue input x of this thread's site into the spinor / norm area of a buffer
+template <int PREC, int RECON, int NF>
+__device__ __forceinline__ void async_fetch_x(char *buf, int tid, const typename Traits<PREC>::schunk *X,
+                                              const float *x_norm, int cb, int Vh)
+{
+    using H = AsyncHop<PREC, RECON, NF>;
+    using SC = typename H::SC;
+    SC *ss = reinterpret_cast<SC *>(buf + H::LBYTES);
+#pragma unroll
+    for (int k = 0; k < H::NS; k++) cp_async<16>(ss + k * H::BS + tid, X + (size_t)k * Vh + cb);
+    if constexpr (H::NN > 0) {
+        float *sn = reinterpret_cast<float *>(buf + H::LBYTES + H::NS * H::BS * 16);
+#pragma unroll
+        for (int f = 0; f < H::NN; f++) cp_async<4>(sn + f * H::BS + tid, x_norm + (size_t)f * Vh + cb);
+    }
+}
+
+template <int PREC, int RECON, int NF, typename T>
+__device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[NF][24])
+{
+    using H = AsyncHop<PREC, RECON, NF>;
+    using SC = typename H::SC;
+    const SC *ss = reinterpret_cast<const SC *>(buf + H::LBYTES);
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        SC c[Traits<PREC>::SCHUNKS];
+#pragma unroll
+        for (int k = 0; k < Traits<PREC>::SCHUNKS; k++) c[k] = ss[(f * Traits<PREC>::SCHUNKS + k) * H::BS + tid];
+        spinor_from_chunks<PREC>(c, xv[f]);
+        if constexpr (H::NN > 0) {
+            const float n = reinterpret_cast<const float *>(buf + H::LBYTES + H::NS * H::BS * 16)[f * H::BS + tid];
+#pragma unroll
+            for (int k = 0; k < 24; k++) xv[f][k] *= n;
+        }
+    }
+}
+
+template <int PREC, int NF, int RECON, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    using T = typename Traits<PREC>::real;
+    using LL = LinkLayout<PREC, RECON>;
+    using LC = typename LL::chunk;
+    using SC = typename Traits<PREC>::schunk;
+    using H = AsyncHop<PREC, RECON, NF>;
+    extern __shared__ __align__(16) char smem_async[];
+    char *buf0 = smem_async, *buf1 = smem_async + H::BUF;
+    const int tid = threadIdx.x;
+    const int cb = blockIdx.x * H::BS + tid;
+    if (cb >= a.Vh) return;
+    int r = cb;
+    const int xh = r % a.X1h;
+    r /= a.X1h;
+    const int y = r % a.Ly;
+    r /= a.Ly;
+    const int z = r % a.Lz;
+    const int t = r / a.Lz;
+    const int op = a.out_parity;
+    const int x = 2 * xh + ((op + y + z + t) & 1);
+    const int row = cb - xh;
+    const size_t gpar = (size_t)LL::N * a.Vh;
+    const LC *G = reinterpret_cast<const LC *>(a.gauge);
+    const LC *Gout = G + (size_t)op * gpar, *Gin = G + (size_t)(1 - op) * gpar;
+    const SC *in = reinterpret_cast<const SC *>(a.in);
+    const int sy = a.X1h, sz = a.X1h * a.Ly, st = a.X1h * a.Ly * a.Lz;
+    const int n0 = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1), n1 = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
+    const int n2 = (y == a.Ly - 1) ? cb - (a.Ly - 1) * sy : cb + sy, n3 = (y == 0) ? cb + (a.Ly - 1) * sy : cb - sy;
+    const int n4 = (z == a.Lz - 1) ? cb - (a.Lz - 1) * sz : cb + sz, n5 = (z == 0) ? cb + (a.Lz - 1) * sz : cb - sz;
+    const int n6 = (t == a.Lt - 1) ? cb - (a.Lt - 1) * st : cb + st, n7 = (t == 0) ? cb + (a.Lt - 1) * st : cb - st;
+    const T one = T(1);
+    const T sgf = (t == a.Lt - 1 && a.tbc) ? -one : one, sgb = (t == 0 && a.tbc) ? -one : one;
+    const T spf = -a.sigma, spb = a.sigma;
+    const size_t m2 = 2 * gpar;
+
+    T acc[NF][24];
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+#pragma unroll
+        for (int k = 0; k < 24; k++) acc[f][k] = T(0);
+    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 0 * m2, cb, in, a.in_norm, n0, a.Vh);
+    cp_commit();
+    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 0 * m2, n1, in, a.in_norm, n1, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 0, true>(acc, buf0, tid, spf, one);
+    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 1 * m2, cb, in, a.in_norm, n2, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 0, false>(acc, buf1, tid, spb, one);
+    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 1 * m2, n3, in, a.in_norm, n3, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 1, true>(acc, buf0, tid, spf, one);
+    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 2 * m2, cb, in, a.in_norm, n4, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 1, false>(acc, buf1, tid, spb, one);
+    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 2 * m2, n5, in, a.in_norm, n5, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 2, true>(acc, buf0, tid, spf, one);
+    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 3 * m2, cb, in, a.in_norm, n6, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 2, false>(acc, buf1, tid, spb, one);
+    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 3 * m2, n7, in, a.in_norm, n7, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 3, true>(acc, buf0, tid, spf, sgf);
+    const int epi = a.epilogue;
+    const bool needx = epi != EPI_SCALE && epi != EPI_TW;
+    // the epilogue input streams in while the last hop is computed
+    if (needx) async_fetch_x<PREC, RECON, NF>(buf0, tid, reinterpret_cast<const SC *>(a.x), a.x_norm, cb, a.Vh);
+    cp_commit();
+    cp_wait<1>();
+    async_compute_hop<PREC, RECON, NF, 3, false>(acc, buf1, tid, spb, sgb);
+
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    if (epi == EPI_SCALE) {
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+#pragma unroll
+            for (int k = 0; k < 24; k++) acc[f][k] *= a.coef;
+    } else if (epi == EPI_TW) {
+        apply_twist<T, NF>(a.tw_epi, acc);
+    } else {
+        T xv[NF][24];
+        cp_wait<0>();
+        async_read_x<PREC, RECON, NF>(buf0, tid, xv);
+        if (epi == EPI_TWX_AXPY) apply_twist<T, NF>(a.tw_epi, xv);
+        else if (epi == EPI_X_TWAXPY) apply_twist<T, NF>(a.tw_epi, acc);
+#pragma unroll
+        for (int f = 0; f < NF; f++)
+#pragma unroll
+            for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+        if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+    }
+    SC *O = reinterpret_cast<SC *>(a.out);
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+        store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+}
+
+template <int PREC, int NF, int RECON, int MINB>
+cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
+{
+    constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
+    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    k_dslash_async<PREC, NF, RECON, MINB><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 // variant 0: one thread per site (both flavours); variant 2: the two-stage load pipeline (no
 // prologue); variant 3: variant 0 with a register cap (4 resident 128-thread blocks per SM).
 template <int PREC>
@@ -571,6 +803,20 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
 #undef TM_LBR
 #undef TM_LB1
         return cudaGetLastError();
+    }
+    if (variant == 6 && !pro) {
+        // shared-memory staged pipeline, registers for 3 resident blocks per SM
+#define TM_AS(NF, R) return launch_async<PREC, NF, R, 3>(a, s);
+#define TM_ASR(NF)                         \
+    switch (recon) {                       \
+    case 18: TM_AS(NF, 18)                 \
+    case 12: TM_AS(NF, 12)                 \
+    case 8: TM_AS(NF, 8)                   \
+    default: return cudaErrorInvalidValue; \
+    }
+        if (nf == 1) { TM_ASR(1) } else { TM_ASR(2) }
+#undef TM_ASR
+#undef TM_AS
     }
     const int grid = (a.Vh + block - 1) / block;
     if (variant == 2 && !pro) {
