@@ -341,8 +341,8 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * 128-register cap in three block shapes) for
  * each precision, with and without the input-twist prologue, and the multi-RHS block shape (2, 4
  * or 8 right-hand sides per block, timed on 8 right-hand sides), on this handle's lattice, and
- * keep the fastest; with a clover term also the clover kernel's occupancy (1, 3 or 4 blocks per
- * SM).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
+ * keep the fastest; with a clover term also the clover kernel's form (1, 3 or 4 blocks per SM,
+ * or the staged pipeline).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
  * uses defaults (capped 128 x 4; FP32 without prologue the shared-memory pipeline unless one
@@ -355,7 +355,7 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
  * 128 / 64 / 256-thread blocks, 6 pipelined through shared memory with cp.async; 2 and 6 have no
  * prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
- * kernel's register allocation allows (1, 3 or 4).  Import accepts any subset of the entries; an
+ * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline.  Import accepts any subset of the entries; an
  * invalid entry leaves the table unchanged and returns TM_ERR_ARG. */
 tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n);
 tm_status tm_tune_import(tm_gauge *g, const char *text);

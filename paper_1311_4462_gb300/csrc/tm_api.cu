@@ -782,10 +782,10 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
         }
         if (g0->csw != 0.0 && st == TM_OK) {
             // clover kernel occupancy, timed on the heavier launch (the inverse L^-1 epilogue)
-            const int minbs[3] = {1, 3, 4};
+            const int minbs[4] = {1, 3, 4, 6};
             float best = 1e30f;
             int bestm = g0->clov_minb[pi];
-            for (int mi = 0; mi < 3 && st == TM_OK; mi++) {
+            for (int mi = 0; mi < 4 && st == TM_OK; mi++) {
                 g0->clov_minb[pi] = minbs[mi];
                 float ms = 0;
                 for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -912,7 +912,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
         if (sscanf(p, "%3[a-z0-9]:c:%d%n", name, &block, &used) == 2 && used > 0) {
             // clover entry "<prec>:c:<resident blocks per SM>"
             const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-            if (pi < 0 || (block != 1 && block != 3 && block != 4)) {
+            if (pi < 0 || (block != 1 && block != 3 && block != 4 && block != 6)) {
                 set_error("tm_tune_import: invalid entry '%.32s'", p);
                 return TM_ERR_ARG;
             }

@@ -311,41 +311,6 @@ __global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ 
     dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
 }
 
-// Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in
-// the epilogue instead of the constant twist; no input prologue (the operators apply L^-1 to an
-// input as a pass of its own).  The epilogue reads 72 (L) or 144 (L^-1) more reals per site.
-template <int PREC, int NF, int RECON, int MINB = 1>
-__global__ void __launch_bounds__(128, MINB) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
-{
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= a.Vh) return;
-    dslash_body<PREC, NF, RECON, false, true>(a, cb, 0);
-}
-
-template <int PREC>
-cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, int minb,
-                                    cudaStream_t s)
-{
-    // minb: resident 128-thread blocks per SM the register allocation must allow (1, 3 or 4)
-    if (minb != 1 && minb != 3 && minb != 4) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)((a.Vh + 127) / 128);
-#define TM_CL1(NF, R)                                                               \
-    if (minb == 1) k_dslash_clov<PREC, NF, R, 1><<<grid, 128, 0, s>>>(a);           \
-    else if (minb == 3) k_dslash_clov<PREC, NF, R, 3><<<grid, 128, 0, s>>>(a);      \
-    else k_dslash_clov<PREC, NF, R, 4><<<grid, 128, 0, s>>>(a);
-#define TM_CL(NF)                          \
-    switch (recon) {                       \
-    case 18: { TM_CL1(NF, 18) } break;     \
-    case 12: { TM_CL1(NF, 12) } break;     \
-    case 8: { TM_CL1(NF, 8) } break;       \
-    default: return cudaErrorInvalidValue; \
-    }
-    if (nf == 1) { TM_CL(1) } else { TM_CL(2) }
-#undef TM_CL
-#undef TM_CL1
-    return cudaGetLastError();
-}
-
 // Several right-hand sides in one launch (multi-RHS, sources share the gauge field).  A block
 // is 32 consecutive sites x RPB right-hand sides, one warp per right-hand side, so every spinor
 // load of a warp is one contiguous 512-byte request and the RPB warps of a block read the same
@@ -657,7 +622,7 @@ __device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[N
     }
 }
 
-template <int PREC, int NF, int RECON, int MINB>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false>
 __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     using T = typename Traits<PREC>::real;
@@ -744,18 +709,18 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] *= a.coef;
     } else if (epi == EPI_TW) {
-        apply_twist<T, NF>(a.tw_epi, acc);
+        local_op<PREC, NF, CLOV, true>(a, cb, acc);
     } else {
         T xv[NF][24];
         cp_wait<0>();
         async_read_x<PREC, RECON, NF>(buf0, tid, xv);
-        if (epi == EPI_TWX_AXPY) apply_twist<T, NF>(a.tw_epi, xv);
-        else if (epi == EPI_X_TWAXPY) apply_twist<T, NF>(a.tw_epi, acc);
+        if (epi == EPI_TWX_AXPY) local_op<PREC, NF, CLOV, false>(a, cb, xv);
+        else if (epi == EPI_X_TWAXPY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
         for (int f = 0; f < NF; f++)
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
-        if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+        if (epi == EPI_TW_XPAY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
     }
     SC *O = reinterpret_cast<SC *>(a.out);
 #pragma unroll
@@ -763,14 +728,51 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
-template <int PREC, int NF, int RECON, int MINB>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false>
 cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
 {
     constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
-    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_dslash_async<PREC, NF, RECON, MINB><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in
+// the epilogue instead of the constant twist; no input prologue (the operators apply L^-1 to an
+// input as a pass of its own).  The epilogue reads 72 (L) or 144 (L^-1) more reals per site.
+template <int PREC, int NF, int RECON, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.Vh) return;
+    dslash_body<PREC, NF, RECON, false, true>(a, cb, 0);
+}
+
+template <int PREC>
+cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, int minb,
+                                    cudaStream_t s)
+{
+    // minb: resident 128-thread blocks per SM the register allocation must allow (1, 3 or 4), or 6:
+    // the shared-memory staged pipeline (3 blocks per SM)
+    if (minb != 1 && minb != 3 && minb != 4 && minb != 6) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((a.Vh + 127) / 128);
+#define TM_CL1(NF, R)                                                               \
+    if (minb == 6) return launch_async<PREC, NF, R, 3, true>(a, s);                 \
+    if (minb == 1) k_dslash_clov<PREC, NF, R, 1><<<grid, 128, 0, s>>>(a);           \
+    else if (minb == 3) k_dslash_clov<PREC, NF, R, 3><<<grid, 128, 0, s>>>(a);      \
+    else k_dslash_clov<PREC, NF, R, 4><<<grid, 128, 0, s>>>(a);
+#define TM_CL(NF)                          \
+    switch (recon) {                       \
+    case 18: { TM_CL1(NF, 18) } break;     \
+    case 12: { TM_CL1(NF, 12) } break;     \
+    case 8: { TM_CL1(NF, 8) } break;       \
+    default: return cudaErrorInvalidValue; \
+    }
+    if (nf == 1) { TM_CL(1) } else { TM_CL(2) }
+#undef TM_CL
+#undef TM_CL1
     return cudaGetLastError();
 }
 

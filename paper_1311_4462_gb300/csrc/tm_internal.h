@@ -52,7 +52,7 @@ struct tm_gauge {
     double csw;                // clover coefficient; 0: no clover term
     void *clov[3];             // per-site local clover operator, FP64 / FP32 / FP16 (tm_clover.cuh)
     float *clov_norm;          // FP16 block scales
-    int clov_minb[3];          // clover kernel: resident blocks per SM its registers allow (1, 3, 4)
+    int clov_minb[3];          // clover kernel: resident blocks per SM its registers allow (1, 3, 4), 6: staged
     size_t scratch_bytes;
 };
 

@@ -138,7 +138,7 @@ def test_mixed_cg_reaches_fp64_tolerance(case, sloppy):
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("minb", [1, 3, 4])
+@pytest.mark.parametrize("minb", [1, 3, 4, 6])
 def test_occupancy_forms(case, minb):
     tmq, p, po, U, g, psi = setup(case)
     saved = tmq.tune_export(g)

@@ -231,7 +231,7 @@ def test_autotune_roundtrip_and_parity():
     clov = [e for e in entries if e.split(":")[1] == "c"]
     assert len(single) == 6 and all(len(e.split(":")) == 4 for e in single)
     assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8") for e in multi)
-    assert len(clov) == 3 and all(e.split(":")[2] in ("1", "3", "4") for e in clov)
+    assert len(clov) == 3 and all(e.split(":")[2] in ("1", "3", "4", "6") for e in clov)
     tmq.tune_import(g, table)
     assert tmq.tune_export(g) == table
     for bad in ("f32:0:3:100",   # block not a multiple of 32
