@@ -345,15 +345,15 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * or the staged pipeline).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
- * uses defaults (capped 128 x 4; FP32 without prologue the shared-memory pipeline unless one
- * flavour with 18-real links; 4 right-hand sides per block; clover 1 block per SM for FP64, 3 for
- * FP16 and the FP32 doublet, 4 for FP32 one flavour).
+ * uses defaults (capped 128 x 4; without prologue the shared-memory pipeline for FP32 and for
+ * FP16 one flavour, not for one flavour with 18-real links; 4 right-hand sides per block; clover
+ * 1 block per SM for FP64, 3 for FP16 and the FP32 doublet, 4 for FP32 one flavour).
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text, and back.  Single-RHS entries "f32:0:3:128" = precision:prologue:
  * variant:block (variant 0 plain, 2 pipelined in registers, 3 / 4 / 5 capped at 128 registers with
- * 128 / 64 / 256-thread blocks, 6 pipelined through shared memory with cp.async; 2 and 6 have no
- * prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
+ * 128 / 64 / 256-thread blocks, 6 / 7 pipelined through shared memory with cp.async, two / three
+ * buffers; 2, 6 and 7 have no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline.  Import accepts any subset of the entries; an
  * invalid entry leaves the table unchanged and returns TM_ERR_ARG. */

@@ -467,10 +467,13 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
     for (int i = 0; i < 4; i++) {
-        // measured on GB300 at 32^3x64: the register cap (3) for every storage form, and for FP32
-        // without prologue the shared-memory staged pipeline (6) except one flavour with 18-real links
+        // measured on GB300 at 32^3x64: the register cap (3) for every storage form; without
+        // prologue the shared-memory staged pipeline for FP32 (doublet: 2 buffers, 6; one flavour:
+        // 3 buffers, 7, except with 18-real links) and for FP16 one flavour (7, not with 18-real links)
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};
-        if (i == 1 && (p->recon != 18 || p->flavor == TM_NDEG_DOUBLET)) g->tune[i][0] = tm_tune_entry{6, 128};
+        const bool nd = p->flavor == TM_NDEG_DOUBLET;
+        if (i == 1 && nd) g->tune[i][0] = tm_tune_entry{6, 128};
+        if ((i == 1 || i == 2) && !nd && p->recon != 18) g->tune[i][0] = tm_tune_entry{7, 128};
         g->multi_rpb[i] = 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
@@ -754,8 +757,8 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
         for (int pro = 0; pro < 2 && st == TM_OK; pro++) {
             float best = 1e30f;
             tm_tune_entry bestc = g->tune[pi][pro];
-            const int variants[6] = {0, 2, 3, 4, 5, 6};
-            for (int vi = 0; vi < 6; vi++) {
+            const int variants[7] = {0, 2, 3, 4, 5, 6, 7};
+            for (int vi = 0; vi < 7; vi++) {
                 const int variant = variants[vi];
                 if (pro && (variant == 2 || variant >= 6)) continue;  // the pipelined forms have no prologue
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
@@ -926,7 +929,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 6 || (pro && variant == 6) || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 7 || (pro && variant >= 6) || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

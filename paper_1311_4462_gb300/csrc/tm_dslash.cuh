@@ -622,7 +622,7 @@ __device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[N
     }
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2>
 __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     using T = typename Traits<PREC>::real;
@@ -631,7 +631,6 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
     using SC = typename Traits<PREC>::schunk;
     using H = AsyncHop<PREC, RECON, NF>;
     extern __shared__ __align__(16) char smem_async[];
-    char *buf0 = smem_async, *buf1 = smem_async + H::BUF;
     const int tid = threadIdx.x;
     const int cb = blockIdx.x * H::BS + tid;
     if (cb >= a.Vh) return;
@@ -664,43 +663,47 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
     for (int f = 0; f < NF; f++)
 #pragma unroll
         for (int k = 0; k < 24; k++) acc[f][k] = T(0);
-    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 0 * m2, cb, in, a.in_norm, n0, a.Vh);
-    cp_commit();
-    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 0 * m2, n1, in, a.in_norm, n1, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 0, true>(acc, buf0, tid, spf, one);
-    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 1 * m2, cb, in, a.in_norm, n2, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 0, false>(acc, buf1, tid, spb, one);
-    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 1 * m2, n3, in, a.in_norm, n3, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 1, true>(acc, buf0, tid, spf, one);
-    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 2 * m2, cb, in, a.in_norm, n4, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 1, false>(acc, buf1, tid, spb, one);
-    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 2 * m2, n5, in, a.in_norm, n5, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 2, true>(acc, buf0, tid, spf, one);
-    async_fetch_hop<PREC, RECON, NF>(buf0, tid, Gout + 3 * m2, cb, in, a.in_norm, n6, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 2, false>(acc, buf1, tid, spb, one);
-    async_fetch_hop<PREC, RECON, NF>(buf1, tid, Gin + 3 * m2, n7, in, a.in_norm, n7, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 3, true>(acc, buf0, tid, spf, sgf);
+    // hop h: (mu, forward?) = (h / 2, h even); link at the output site (forward) or at the neighbour
+    const int nbr[8] = {n0, n1, n2, n3, n4, n5, n6, n7};
+    auto fetch = [&](int h) {
+        char *b = smem_async + (h % NB) * H::BUF;
+        const int mu = h >> 1;
+        if ((h & 1) == 0) async_fetch_hop<PREC, RECON, NF>(b, tid, Gout + mu * m2, cb, in, a.in_norm, nbr[h], a.Vh);
+        else async_fetch_hop<PREC, RECON, NF>(b, tid, Gin + mu * m2, nbr[h], in, a.in_norm, nbr[h], a.Vh);
+        cp_commit();
+    };
+#pragma unroll
+    for (int h = 0; h < NB; h++) fetch(h);
     const int epi = a.epilogue;
     const bool needx = epi != EPI_SCALE && epi != EPI_TW;
-    // the epilogue input streams in while the last hop is computed
-    if (needx) async_fetch_x<PREC, RECON, NF>(buf0, tid, reinterpret_cast<const SC *>(a.x), a.x_norm, cb, a.Vh);
-    cp_commit();
-    cp_wait<1>();
-    async_compute_hop<PREC, RECON, NF, 3, false>(acc, buf1, tid, spb, sgb);
+#pragma unroll
+    for (int h = 0; h < 8; h++) {
+        // groups committed after hop h's: the hops up to min(h + NB - 1, 7), and the epilogue
+        // input once hop 8 - NB has been computed; hop h itself must be complete
+        const int later = (h + NB - 1 < 7 ? h + NB - 1 : 7) - h + (h > 8 - NB ? 1 : 0);
+        if (later >= 2) cp_wait<2>();
+        else if (later == 1) cp_wait<1>();
+        else cp_wait<0>();
+        const char *b = smem_async + (h % NB) * H::BUF;
+        switch (h) {
+        case 0: async_compute_hop<PREC, RECON, NF, 0, true>(acc, b, tid, spf, one); break;
+        case 1: async_compute_hop<PREC, RECON, NF, 0, false>(acc, b, tid, spb, one); break;
+        case 2: async_compute_hop<PREC, RECON, NF, 1, true>(acc, b, tid, spf, one); break;
+        case 3: async_compute_hop<PREC, RECON, NF, 1, false>(acc, b, tid, spb, one); break;
+        case 4: async_compute_hop<PREC, RECON, NF, 2, true>(acc, b, tid, spf, one); break;
+        case 5: async_compute_hop<PREC, RECON, NF, 2, false>(acc, b, tid, spb, one); break;
+        case 6: async_compute_hop<PREC, RECON, NF, 3, true>(acc, b, tid, spf, sgf); break;
+        default: async_compute_hop<PREC, RECON, NF, 3, false>(acc, b, tid, spb, sgb); break;
+        }
+        if (h + NB < 8) fetch(h + NB);
+        else if (h + NB == 8) {
+            // the epilogue input streams in, into the buffer hop h used, while the last hops compute
+            if (needx) async_fetch_x<PREC, RECON, NF>(smem_async + (h % NB) * H::BUF, tid,
+                                                     reinterpret_cast<const SC *>(a.x), a.x_norm, cb, a.Vh);
+            cp_commit();
+        }
+    }
+    const char *xbuf = smem_async + ((8 - NB) % NB) * H::BUF;
 
     const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
     if (epi == EPI_SCALE) {
@@ -713,7 +716,7 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
     } else {
         T xv[NF][24];
         cp_wait<0>();
-        async_read_x<PREC, RECON, NF>(buf0, tid, xv);
+        async_read_x<PREC, RECON, NF>(xbuf, tid, xv);
         if (epi == EPI_TWX_AXPY) local_op<PREC, NF, CLOV, false>(a, cb, xv);
         else if (epi == EPI_X_TWAXPY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
@@ -728,14 +731,14 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2>
 cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
 {
-    constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
-    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV>,
+    constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
+    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_dslash_async<PREC, NF, RECON, MINB, CLOV><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -806,9 +809,10 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
 #undef TM_LB1
         return cudaGetLastError();
     }
-    if (variant == 6 && !pro) {
-        // shared-memory staged pipeline, registers for 3 resident blocks per SM
-#define TM_AS(NF, R) return launch_async<PREC, NF, R, 3>(a, s);
+    if ((variant == 6 || variant == 7) && !pro) {
+        // shared-memory staged pipeline, 6: two buffers (hop h+1 in flight while hop h computes,
+        // registers for 3 blocks per SM), 7: three buffers (hops h+1 and h+2 in flight, 2 blocks)
+#define TM_AS(NF, R) return variant == 6 ? launch_async<PREC, NF, R, 3>(a, s) : launch_async<PREC, NF, R, 2, false, 3>(a, s);
 #define TM_ASR(NF)                         \
     switch (recon) {                       \
     case 18: TM_AS(NF, 18)                 \

@@ -52,8 +52,8 @@ def setup(case, recon):
 
 def use_variant(tmq, g, variant, block=128):
     """Force the hopping-kernel launch choice (0 plain, 2 pipelined, 3/4/5 register-capped 128x4/64x8/256x2,
-    6 shared-memory staged pipeline; prologue launches keep 0 for 2 and 6)."""
-    pro_variant = variant if 3 <= variant <= 5 else 0  # 2 and 6 have no prologue form
+    6/7 shared-memory staged pipeline with 2/3 buffers; prologue launches keep 0 for 2, 6, 7)."""
+    pro_variant = variant if 3 <= variant <= 5 else 0  # 2, 6 and 7 have no prologue form
     tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
 
@@ -116,7 +116,7 @@ def test_full_operator(case, prec, dagger):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 @pytest.mark.parametrize("out_parity", [0, 1])
-@pytest.mark.parametrize("variant", [0, 2, 3, 6], ids=["site", "pipe", "cap4", "async"])
+@pytest.mark.parametrize("variant", [0, 2, 3, 6, 7], ids=["site", "pipe", "cap4", "async2", "async3"])
 def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
     """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
     tmq, p, po, U, g, psi, chi = setup(case, 12)
