@@ -20,6 +20,8 @@
 // For the doublet both flavours are computed by the same thread, so each link is loaded once
 // and used for both (sec. 2.1).
 #pragma once
+#include <atomic>
+
 #include "tm_clover.cuh"
 #include "tm_core.cuh"
 #include "tm_internal.h"
@@ -731,13 +733,24 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
+// The shared-memory opt-in is set once per kernel and device: the attribute call is not a
+// stream operation and can wait for work already queued on the device, so it must stay out of
+// the per-launch path (it would serialise copy streams with the compute stream).
 template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2>
 cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
 {
     constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
-    cudaError_t e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    static std::atomic<unsigned long long> opted{0};  // bit d: done on device d (d < 64)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit, std::memory_order_acq_rel);
+    }
     k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
 }
