@@ -337,6 +337,28 @@ def e2e_ours(args, tmq, g, psi_np, dev, flops_step):
         tmq.precond_op(g, out, xe, tmp, tmq.TM_PC_ASYM, False)
         tmq.unpack(g, out, 0, canon=host_out[0])
 
+    # in place on two streams: step k runs on stream k % 2 with its own fields, so the pack of one
+    # step (reading host memory) overlaps the unpack of the other (writing host memory)
+    streams = [cur, torch.cuda.Stream()]
+    fields = [(xe, tmp, out)] + [tuple(tmq.Field(g, prec) for _ in range(3))]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+
+    def run_in_place_overlapped(n):
+        ev_start = torch.cuda.Event()
+        ev_start.record(cur)
+        streams[1].wait_event(ev_start)  # the second stream starts inside the timed region
+        for k in range(n):
+            b = k % 2
+            st = streams[b]
+            fx, ft, fo = fields[b]
+            with torch.cuda.stream(st):
+                tmq.pack(g, host_in, 0, prec, out=fx, stream=st)
+                tmq.precond_op(g, fo, fx, ft, tmq.TM_PC_ASYM, False, stream=st)
+                tmq.unpack(g, fo, 0, canon=host_out[b], stream=st)
+            ev_done[b].record(st)
+        cur.wait_event(ev_done[(n - 1) % 2])
+        cur.wait_event(ev_done[n % 2])
+
     n = max(4, min(20, args.steps))
 
     def timed(fn, steps_fn=None):
@@ -356,15 +378,25 @@ def e2e_ours(args, tmq, g, psi_np, dev, flops_step):
     ms = timed(run_overlapped)
     ms_serial = timed(None, step_serial)
     ms_inplace = timed(None, step_in_place)
+    ms_inplace2 = timed(run_in_place_overlapped)
     full = host_in.numel() * 8
     gf = lambda t: round(flops_step / (t * 1e-3) / 1e9, 1)
-    return {"value": gf(ms), "unit": "GFLOPS", "ms_per_step": round(ms, 4),
-            "h2d_bytes_per_step": full, "d2h_bytes_per_step": full,
-            "path": "pinned host complex64 canonical field -> cudaMemcpy -> tm_pack -> tm_precond_op -> tm_unpack "
-                    "-> cudaMemcpy to pinned host; double-buffered over copy-in / compute / copy-out streams",
-            "serial": {"value": gf(ms_serial), "ms_per_step": round(ms_serial, 4)},
-            "in_place_host_buffers": {"value": gf(ms_inplace), "ms_per_step": round(ms_inplace, 4),
-                                      "h2d_bytes_per_step": full // 2, "d2h_bytes_per_step": full // 2}}
+    copies = {"value": gf(ms), "ms_per_step": round(ms, 4), "h2d_bytes_per_step": full, "d2h_bytes_per_step": full,
+              "path": "pinned host complex64 canonical field -> cudaMemcpy -> tm_pack -> tm_precond_op -> tm_unpack "
+                      "-> cudaMemcpy to pinned host; double-buffered over copy-in / compute / copy-out streams"}
+    in_place = {"value": gf(ms_inplace2), "ms_per_step": round(ms_inplace2, 4), "h2d_bytes_per_step": full // 2,
+                "d2h_bytes_per_step": full // 2,
+                "path": "tm_pack reads the even sites of the pinned host complex64 canonical field in place over the "
+                        "CPU-GPU link -> tm_precond_op -> tm_unpack writes them to pinned host memory in place; "
+                        "consecutive steps on two streams"}
+    best = in_place if ms_inplace2 < ms else copies
+    out_d = {"value": best["value"], "unit": "GFLOPS", "ms_per_step": best["ms_per_step"],
+             "h2d_bytes_per_step": best["h2d_bytes_per_step"], "d2h_bytes_per_step": best["d2h_bytes_per_step"],
+             "path": best["path"],
+             "staged_copies_double_buffered": copies, "in_place_two_streams": in_place,
+             "serial_copies": {"value": gf(ms_serial), "ms_per_step": round(ms_serial, 4)},
+             "in_place_one_stream": {"value": gf(ms_inplace), "ms_per_step": round(ms_inplace, 4)}}
+    return out_d
 
 
 def time_op(fn, reps, flush=None):

@@ -29,6 +29,88 @@ struct Geo {
     int Vh, X1h, Lx, Ly, Lz, nf, nrhs;
 };
 
+// Storage forms whose 16-byte chunks are the canonical field's own bytes (FP32 fields from
+// complex64, FP64 fields from complex128): a block moves 32 sites of one parity through shared
+// memory, reading the canonical sites whole (16-byte loads, consecutive threads on consecutive
+// bytes) and writing each SoA row with consecutive threads on consecutive sites.  Both sides are
+// coalesced, which matters most when the canonical buffer is pinned host memory read over the
+// CPU-GPU link.  NCH = chunks per site = flavours x chunks per flavour.
+template <int NCH>
+__global__ void __launch_bounds__(128) k_pack_chunks(uint4 *out, const uint4 *canon, int parity, Geo g)
+{
+    constexpr int S = 32;
+    __shared__ uint4 sm[S * NCH];
+    const long nsites = (long)g.Vh * g.nrhs;
+    const long V = 2L * g.Vh;
+    // grid-stride over groups of S sites with a grid of at most 4 blocks per SM, so a pack and an
+    // unpack on two streams can be resident together
+    for (long site0 = (long)blockIdx.x * S; site0 < nsites; site0 += (long)gridDim.x * S) {
+        for (int i = threadIdx.x; i < S * NCH; i += blockDim.x) {
+            const int si = i / NCH, j = i % NCH;
+            const long gs = site0 + si;
+            if (gs < nsites) {
+                const long rhs = gs / g.Vh;
+                const int cb = (int)(gs - rhs * g.Vh);
+                const long lex = lex_of(cb, parity, g.X1h, g.Lx, g.Ly, g.Lz);
+                sm[i] = canon[(rhs * V + lex) * NCH + j];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < S * NCH; i += blockDim.x) {
+            const int j = i / S, si = i % S;
+            const long gs = site0 + si;
+            if (gs < nsites) {
+                const long rhs = gs / g.Vh;
+                const int cb = (int)(gs - rhs * g.Vh);
+                out[(rhs * NCH + j) * g.Vh + cb] = sm[si * NCH + j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(128) k_unpack_chunks(uint4 *canon, const uint4 *in, int parity, Geo g)
+{
+    constexpr int S = 32;
+    __shared__ uint4 sm[S * NCH];
+    const long nsites = (long)g.Vh * g.nrhs;
+    const long V = 2L * g.Vh;
+    for (long site0 = (long)blockIdx.x * S; site0 < nsites; site0 += (long)gridDim.x * S) {
+        for (int i = threadIdx.x; i < S * NCH; i += blockDim.x) {
+            const int j = i / S, si = i % S;
+            const long gs = site0 + si;
+            if (gs < nsites) {
+                const long rhs = gs / g.Vh;
+                const int cb = (int)(gs - rhs * g.Vh);
+                sm[si * NCH + j] = in[(rhs * NCH + j) * g.Vh + cb];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < S * NCH; i += blockDim.x) {
+            const int si = i / NCH, j = i % NCH;
+            const long gs = site0 + si;
+            if (gs < nsites) {
+                const long rhs = gs / g.Vh;
+                const int cb = (int)(gs - rhs * g.Vh);
+                const long lex = lex_of(cb, parity, g.X1h, g.Lx, g.Ly, g.Lz);
+                canon[(rhs * V + lex) * NCH + j] = sm[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// number of 16-byte chunks per site when the field's chunks are the canonical bytes (and the
+// canonical buffer is 16-byte aligned), else 0
+static int direct_chunks(const Geo &G, int prec, int ctype, const void *canon)
+{
+    if (((uintptr_t)canon & 15) != 0) return 0;
+    if (prec == TM_PREC_F32 && ctype == TM_C64) return 6 * G.nf;
+    if (prec == TM_PREC_F64 && ctype == TM_C128) return 12 * G.nf;
+    return 0;
+}
+
 // thread per (rhs, flavour, cb)
 template <int PREC, typename CT>
 __global__ void k_pack_spinor(void *out, float *norm, const CT *canon, int parity, Geo g)
@@ -226,6 +308,17 @@ cudaError_t launch_pack_spinor(const tm_gauge *g, const tm_field *f, const void 
                                cudaStream_t s)
 {
     Geo G = geo_of(g, f->nrhs);
+    if (const int nch = direct_chunks(G, f->prec, ctype, canon)) {
+        const long groups = ((long)G.Vh * G.nrhs + 31) / 32;
+        const long cap = g->num_sms > 0 ? 4L * g->num_sms : 608L;
+        const long grid = groups < cap ? groups : cap;
+        uint4 *o = (uint4 *)f->data;
+        const uint4 *c = (const uint4 *)canon;
+        if (nch == 6) k_pack_chunks<6><<<grid, 128, 0, s>>>(o, c, parity, G);
+        else if (nch == 12) k_pack_chunks<12><<<grid, 128, 0, s>>>(o, c, parity, G);
+        else k_pack_chunks<24><<<grid, 128, 0, s>>>(o, c, parity, G);
+        return cudaGetLastError();
+    }
     const long n = (long)G.Vh * G.nf * G.nrhs;
     const int block = 128;
     const long grid = (n + block - 1) / block;
@@ -250,6 +343,17 @@ cudaError_t launch_unpack_spinor(const tm_gauge *g, void *canon, int ctype, cons
                                  cudaStream_t s)
 {
     Geo G = geo_of(g, f->nrhs);
+    if (const int nch = direct_chunks(G, f->prec, ctype, canon)) {
+        const long groups = ((long)G.Vh * G.nrhs + 31) / 32;
+        const long cap = g->num_sms > 0 ? 4L * g->num_sms : 608L;
+        const long grid = groups < cap ? groups : cap;
+        uint4 *c = (uint4 *)canon;
+        const uint4 *i = (const uint4 *)f->data;
+        if (nch == 6) k_unpack_chunks<6><<<grid, 128, 0, s>>>(c, i, parity, G);
+        else if (nch == 12) k_unpack_chunks<12><<<grid, 128, 0, s>>>(c, i, parity, G);
+        else k_unpack_chunks<24><<<grid, 128, 0, s>>>(c, i, parity, G);
+        return cudaGetLastError();
+    }
     const long n = (long)G.Vh * G.nf * G.nrhs;
     const int block = 128;
     const long grid = (n + block - 1) / block;

@@ -270,3 +270,38 @@ def test_pinned_host_canonical_buffers_are_used_in_place(prec):
     assert st == L.TM_ERR_ARG
     st = L.load().tm_pack(g.h, f_dev.ref(), ctypes.c_void_p(pageable.ctypes.data), L.TM_C128, 0, None)
     assert st == L.TM_ERR_ARG
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("where", ["device", "pinned"])
+def test_chunk_copy_pack_matches_the_generic_path(case, nrhs, where):
+    """FP32 fields from complex64 (16-byte aligned) take the shared-memory chunk path; an 8-byte
+    aligned view of the same data takes the per-site path: both give the same bits, both ways."""
+    tmq, p, po, U, g, psi, chi = setup(case, 12)
+    src = np.stack([psi, chi, psi + 1j * chi][:nrhs]) if nrhs > 1 else psi
+    src = torch.from_numpy(src.astype(np.complex64))
+    dev = "cuda" if where == "device" else "cpu"
+
+    def buffers():
+        def one():
+            big = torch.zeros(src.numel() + 1, dtype=torch.complex64, device=dev)
+            return big.pin_memory() if where == "pinned" else big
+        # separate allocations: a 16-byte aligned view and an 8-byte aligned one
+        return one()[: src.numel()].view(src.shape), one()[1:].view(src.shape)
+
+    a_in, m_in = buffers()
+    a_in.copy_(src)
+    m_in.copy_(src)
+    for parity in (0, 1):
+        fa = tmq.pack(g, a_in, parity, 4, nrhs=nrhs)
+        fm = tmq.pack(g, m_in, parity, 4, nrhs=nrhs)
+        torch.cuda.synchronize()
+        assert torch.equal(fa.data, fm.data)
+        a_out, m_out = buffers()
+        tmq.unpack(g, fa, parity, canon=a_out)
+        tmq.unpack(g, fa, parity, canon=m_out)
+        torch.cuda.synchronize()
+        assert torch.equal(a_out.cpu(), m_out.cpu())
+        mask_ = torch.from_numpy(orc.parity_mask(po, parity))[..., None, None, None]
+        assert torch.equal(a_out.cpu(), torch.where(mask_, src, torch.zeros_like(src)))
