@@ -273,6 +273,7 @@ def run_ours(args, rank, world):
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
         result["clover"] = clover_section(tmq, U, psi, dev, args)
+        result["differentiation"] = force_section(tmq, dev, args)
         result["cpu_baseline"] = cpu_baseline(U_np, psi_np, args)
     result["input_generation_s"] = round(gen_s, 2)
     g.close()
@@ -622,6 +623,56 @@ def clover_section(tmq, U, psi, dev, args):
         g.close()
     return {"csw": CLOVER_CSW, "lattice": list(L_FULL), "flops_per_even_site": CLOVER_FLOPS,
             "operators": rows, "cg_nd_asym_tol_1e-10": cg, "launch_tables": tables}
+
+
+def force_section(tmq, dev, args):
+    """The differentiation row at 24^3x48 one flavour (kappa 0.1612, mu 0.004): tm_force (the
+    su(3)-projected link gradient, canonical output) in FP64 and FP32 with its algorithmic bytes
+    and HBM fraction, and the pseudofermion action S = phi^dag (M^dag M)^-1 phi with its
+    U-gradient through torch.autograd (two mixed-precision solves to 1e-10, then the force)."""
+    import torch
+    from paper_1311_4462_gb300 import autograd as tag
+    from paper_1311_4462_gb300 import inputs
+    peak, _ = load_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    L = (24, 24, 24, 48)
+    p = tmq.Params(L, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=12)
+    U = torch.from_numpy(inputs.gauge_field(L, 1003)).to(dev)
+    psi = torch.from_numpy(inputs.spinor_field(L, 1, 2003)).to(dev)
+    gv = torch.from_numpy(inputs.spinor_field(L, 1, 2103)).to(dev)
+    g = tmq.Gauge(p, U)
+    V = 2 * p.Vh
+    rows = []
+    for prec in (tmq.TM_PREC_F64, tmq.TM_PREC_F32):
+        w = REAL_BYTES[prec]
+        pe, po = tmq.pack(g, psi, 0, prec), tmq.pack(g, psi, 1, prec)
+        ge, go = tmq.pack(g, gv, 0, prec), tmq.pack(g, gv, 1, prec)
+        out = torch.empty(p.gauge_shape, dtype=torch.complex128 if prec == 8 else torch.complex64, device=dev)
+        ms = time_op(lambda: tmq.force(g, pe, po, ge, go, coef=1.0, project=True, out=out), 10, flush)
+        # each input field read once, each link once (for the projection), each gradient written once
+        by = 2 * V * 24 * w + 4 * V * 12 * w + 4 * V * 18 * w
+        rows.append({"prec": {8: "f64", 4: "f32"}[prec], "us": round(ms * 1e3, 1),
+                     "gbs": round(by / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(by / (ms * 1e-3) / 1e9 / peak, 3),
+                     "bytes_per_launch": by})
+    g.close()
+    phi = torch.from_numpy(inputs.spinor_field(L, 1, 2203)).to(dev)
+    Ug = U.clone().requires_grad_(True)
+    times = []
+    for _ in range(2):  # the first run warms up
+        Ug.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = tag.PseudofermionAction.apply(Ug, phi, p, 1e-10, "mixed")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        S.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        times.append((t1 - t0, t2 - t1))
+    return {"lattice": list(L), "force": rows,
+            "pseudofermion_action": {"forward_s": round(times[-1][0], 3), "backward_s": round(times[-1][1], 4),
+                                     "solves": "two mixed FP32 CG solves to 1e-10 (M^dag z = phi, M X = z)",
+                                     "S": float(S.detach())}}
 
 
 def batching_section(tmq, U, dev, args):

@@ -353,7 +353,7 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text, and back.  Single-RHS entries "f32:0:3:128" = precision:prologue:
  * variant:block (variant 0 plain, 2 pipelined in registers, 3 / 4 / 5 capped at 128 registers with
  * 128 / 64 / 256-thread blocks, 6 / 7 pipelined through shared memory with cp.async, two / three
- * buffers; 2, 6 and 7 have no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
+ * buffers; 2 has no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline.  Import accepts any subset of the entries; an
  * invalid entry leaves the table unchanged and returns TM_ERR_ARG. */

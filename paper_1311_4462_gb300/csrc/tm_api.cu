@@ -760,7 +760,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             const int variants[7] = {0, 2, 3, 4, 5, 6, 7};
             for (int vi = 0; vi < 7; vi++) {
                 const int variant = variants[vi];
-                if (pro && (variant == 2 || variant >= 6)) continue;  // the pipelined forms have no prologue
+                if (pro && variant == 2) continue;  // the register pipeline has no prologue
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
                     if (variant >= 3 && blocks[bi] != 128) continue;  // capped forms fix their own block
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};
@@ -929,7 +929,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             return TM_ERR_ARG;
         }
         const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 7 || (pro && variant >= 6) || block < 32 || block > 256 ||
+        if (pi < 0 || (pro != 0 && pro != 1) || variant < 0 || variant == 1 || variant > 7 || block < 32 || block > 256 ||
             block % 32) {
             set_error("tm_tune_import: invalid entry '%.32s'", p);
             return TM_ERR_ARG;

@@ -405,18 +405,35 @@ __device__ __forceinline__ void decode_link_raw(const HopRaw<PREC, RECON, NF> &r
     LinkRegLoader<PREC, RECON>::load(tmp, U);
 }
 
-template <int PREC, int RECON, int NF, int MU, bool FWD, typename T>
-__device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC, RECON, NF> &r, T sp, T sg)
+// PRO: twist every neighbour spinor with tw before the projection (the input prologue)
+template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, typename T>
+__device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC, RECON, NF> &r, T sp, T sg,
+                                            const Twist<T> *tw = nullptr)
 {
     Link<T> U;
     decode_link_raw<PREC, RECON, NF>(r, U);
+    if constexpr (PRO) {
+        T v[NF][24];
 #pragma unroll
-    for (int f = 0; f < NF; f++) {
-        T v[24];
-        T scale = sg;
-        spinor_from_chunks<PREC>(r.s[f], v);
-        if constexpr (PREC == P16) scale = sg * r.n[f];
-        hop_one<MU, FWD>(acc[f], U, v, sp, scale);
+        for (int f = 0; f < NF; f++) {
+            spinor_from_chunks<PREC>(r.s[f], v[f]);
+            if constexpr (PREC == P16) {
+#pragma unroll
+                for (int k = 0; k < 24; k++) v[f][k] *= r.n[f];
+            }
+        }
+        apply_twist<T, NF>(*tw, v);
+#pragma unroll
+        for (int f = 0; f < NF; f++) hop_one<MU, FWD>(acc[f], U, v[f], sp, sg);
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            T v[24];
+            T scale = sg;
+            spinor_from_chunks<PREC>(r.s[f], v);
+            if constexpr (PREC == P16) scale = sg * r.n[f];
+            hop_one<MU, FWD>(acc[f], U, v, sp, scale);
+        }
     }
 }
 
@@ -564,8 +581,9 @@ __device__ __forceinline__ void async_fetch_hop(char *buf, int tid, const typena
     }
 }
 
-template <int PREC, int RECON, int NF, int MU, bool FWD, typename T>
-__device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *buf, int tid, T sp, T sg)
+template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, typename T>
+__device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *buf, int tid, T sp, T sg,
+                                                  const Twist<T> *tw = nullptr)
 {
     using H = AsyncHop<PREC, RECON, NF>;
     using LC = typename H::LC;
@@ -584,7 +602,7 @@ __device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *
 #pragma unroll
         for (int f = 0; f < NF; f++) r.n[f] = sn[f * H::BS + tid];
     }
-    compute_hop<PREC, RECON, NF, MU, FWD>(acc, r, sp, sg);
+    compute_hop<PREC, RECON, NF, MU, FWD, PRO>(acc, r, sp, sg, tw);
 }
 
 // the epilogue input x of this thread's site into the spinor / norm area of a buffer
@@ -624,7 +642,7 @@ __device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[N
     }
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
 __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     using T = typename Traits<PREC>::real;
@@ -687,15 +705,16 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         else if (later == 1) cp_wait<1>();
         else cp_wait<0>();
         const char *b = smem_async + (h % NB) * H::BUF;
+        const Twist<T> *tw = &a.tw_pro;
         switch (h) {
-        case 0: async_compute_hop<PREC, RECON, NF, 0, true>(acc, b, tid, spf, one); break;
-        case 1: async_compute_hop<PREC, RECON, NF, 0, false>(acc, b, tid, spb, one); break;
-        case 2: async_compute_hop<PREC, RECON, NF, 1, true>(acc, b, tid, spf, one); break;
-        case 3: async_compute_hop<PREC, RECON, NF, 1, false>(acc, b, tid, spb, one); break;
-        case 4: async_compute_hop<PREC, RECON, NF, 2, true>(acc, b, tid, spf, one); break;
-        case 5: async_compute_hop<PREC, RECON, NF, 2, false>(acc, b, tid, spb, one); break;
-        case 6: async_compute_hop<PREC, RECON, NF, 3, true>(acc, b, tid, spf, sgf); break;
-        default: async_compute_hop<PREC, RECON, NF, 3, false>(acc, b, tid, spb, sgb); break;
+        case 0: async_compute_hop<PREC, RECON, NF, 0, true, PRO>(acc, b, tid, spf, one, tw); break;
+        case 1: async_compute_hop<PREC, RECON, NF, 0, false, PRO>(acc, b, tid, spb, one, tw); break;
+        case 2: async_compute_hop<PREC, RECON, NF, 1, true, PRO>(acc, b, tid, spf, one, tw); break;
+        case 3: async_compute_hop<PREC, RECON, NF, 1, false, PRO>(acc, b, tid, spb, one, tw); break;
+        case 4: async_compute_hop<PREC, RECON, NF, 2, true, PRO>(acc, b, tid, spf, one, tw); break;
+        case 5: async_compute_hop<PREC, RECON, NF, 2, false, PRO>(acc, b, tid, spb, one, tw); break;
+        case 6: async_compute_hop<PREC, RECON, NF, 3, true, PRO>(acc, b, tid, spf, sgf, tw); break;
+        default: async_compute_hop<PREC, RECON, NF, 3, false, PRO>(acc, b, tid, spb, sgb, tw); break;
         }
         if (h + NB < 8) fetch(h + NB);
         else if (h + NB == 8) {
@@ -736,7 +755,7 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
 // The shared-memory opt-in is set once per kernel and device: the attribute call is not a
 // stream operation and can wait for work already queued on the device, so it must stay out of
 // the per-launch path (it would serialise copy streams with the compute stream).
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
 cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
 {
     constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
@@ -746,12 +765,12 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB>,
+        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -822,10 +841,13 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
 #undef TM_LB1
         return cudaGetLastError();
     }
-    if ((variant == 6 || variant == 7) && !pro) {
+    if (variant == 6 || variant == 7) {
         // shared-memory staged pipeline, 6: two buffers (hop h+1 in flight while hop h computes,
         // registers for 3 blocks per SM), 7: three buffers (hops h+1 and h+2 in flight, 2 blocks)
-#define TM_AS(NF, R) return variant == 6 ? launch_async<PREC, NF, R, 3>(a, s) : launch_async<PREC, NF, R, 2, false, 3>(a, s);
+#define TM_AS(NF, R)                                                                                     \
+    if (pro) return variant == 6 ? launch_async<PREC, NF, R, 3, false, 2, true>(a, s)                  \
+                                 : launch_async<PREC, NF, R, 2, false, 3, true>(a, s);                 \
+    return variant == 6 ? launch_async<PREC, NF, R, 3>(a, s) : launch_async<PREC, NF, R, 2, false, 3>(a, s);
 #define TM_ASR(NF)                         \
     switch (recon) {                       \
     case 18: TM_AS(NF, 18)                 \

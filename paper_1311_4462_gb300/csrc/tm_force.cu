@@ -8,8 +8,8 @@
 // (bc = -1 on links across the antiperiodic time boundary), times a caller coefficient.
 // The twist R does not depend on U.  project = 1 returns the component in the tangent space
 // of SU(3) at U: P(G) = TA(G U^dag) U with TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6.
-// One thread per link; the colour outer products are summed over spin and flavour in
-// registers and the 3x3 result is written in the canonical gauge layout.
+// One thread per site computes its four links; the colour outer products are summed over spin
+// and flavour in registers and the 3x3 results are written in the canonical gauge layout.
 #include "tm_blas.cuh"
 #include "tm_core.cuh"
 #include "tm_internal.h"
@@ -72,78 +72,67 @@ __device__ __forceinline__ void load_sp(const void *base, const float *norm, int
         for (int c = 0; c < 3; c++) v[s][c] = {(T)r[2 * (3 * s + c)], (T)r[2 * (3 * s + c) + 1]};
 }
 
-template <int PREC, int MU, typename T>
-__device__ __forceinline__ void accumulate_link(const ForceArgs &a, int par, int cb, int nb, C<T> m[3][3])
+// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
+// of the canonical output): psi(x) and g(x) are loaded once and reused by the four links
+// U_mu(x); each link's 3x3 gradient goes through shared memory so that the block writes its
+// contiguous run of the canonical layout with 16-byte stores.
+template <int PREC, int NF, typename T>
+__device__ __forceinline__ void load_site(const ForceArgs &a, const void *const *fld, const float *const *nrm, int par,
+                                          int cb, C<T> v[NF][4][3])
 {
-    for (int f = 0; f < a.nf; f++) {
-        C<T> gx[4][3], gy[4][3], px[4][3], py[4][3], t[4][3];
-        load_sp<PREC>(a.gv[par], a.gv_norm[par], f, cb, a.Vh, gx);
-        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, py);
-        // w1 = (1 - gamma) g(x): sum_s w1_s psi(x+mu)_s^dag
-        gamma_apply<T, MU>(gx, t);
 #pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) gx[s][c] = csub(gx[s][c], t[s][c]);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(gx[s][i], cconj(py[s][j])));
-        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, gy);
-        load_sp<PREC>(a.psi[par], a.psi_norm[par], f, cb, a.Vh, px);
-        // w2 = (1 + gamma) g(x+mu): sum_s psi(x)_s w2_s^dag
-        gamma_apply<T, MU>(gy, t);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) gy[s][c] = cadd(gy[s][c], t[s][c]);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(px[s][i], cconj(gy[s][j])));
-    }
+    for (int f = 0; f < NF; f++) load_sp<PREC>(fld[par], nrm[par], f, cb, a.Vh, v[f]);
 }
 
-template <int PREC, int RECON, typename CT>
-__global__ void k_force(const ForceArgs a)
+template <int PREC, int RECON, int NF, int MU, typename T>
+__device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int cb, int x, int y, int z, int t,
+                                              const C<T> (&px)[NF][4][3], const C<T> (&gx)[NF][4][3], C<T> m[3][3])
 {
-    using T = typename Traits<PREC>::real;
-    const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= 8L * a.Vh) return;
-    const int cb = (int)(id % a.Vh);
-    const int par = (int)((id / a.Vh) % 2);
-    const int mu = (int)(id / (2L * a.Vh));
-    int r = cb;
-    const int xh = r % a.X1h;
-    r /= a.X1h;
-    const int y = r % a.Ly;
-    r /= a.Ly;
-    const int z = r % a.Lz;
-    const int t = r / a.Lz;
-    const int x = 2 * xh + ((par + y + z + t) & 1);
     int nb;
     T bc = T(1);
-    if (mu == 0) nb = (cb - xh) + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
-    else if (mu == 1) nb = (y == a.Ly - 1) ? cb - (a.Ly - 1) * a.X1h : cb + a.X1h;
-    else if (mu == 2) nb = (z == a.Lz - 1) ? cb - (a.Lz - 1) * a.X1h * a.Ly : cb + a.X1h * a.Ly;
+    const int xh = x >> 1;
+    if (MU == 0) nb = (cb - xh) + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
+    else if (MU == 1) nb = (y == a.Ly - 1) ? cb - (a.Ly - 1) * a.X1h : cb + a.X1h;
+    else if (MU == 2) nb = (z == a.Lz - 1) ? cb - (a.Lz - 1) * a.X1h * a.Ly : cb + a.X1h * a.Ly;
     else {
         const int s = a.X1h * a.Ly * a.Lz;
         nb = (t == a.Lt - 1) ? cb - (a.Lt - 1) * s : cb + s;
         if (t == a.Lt - 1 && a.tbc) bc = T(-1);
     }
-    C<T> m[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) m[i][j] = {T(0), T(0)};
-    if (mu == 0) accumulate_link<PREC, 0>(a, par, cb, nb, m);
-    else if (mu == 1) accumulate_link<PREC, 1>(a, par, cb, nb, m);
-    else if (mu == 2) accumulate_link<PREC, 2>(a, par, cb, nb, m);
-    else accumulate_link<PREC, 3>(a, par, cb, nb, m);
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        C<T> w[4][3], q[4][3], tt[4][3];
+        // (1 - gamma) g(x), outer product with psi(x+mu)
+        gamma_apply<T, MU>(gx[f], tt);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) w[s][c] = csub(gx[f][s][c], tt[s][c]);
+        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, q);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(w[s][i], cconj(q[s][j])));
+        // psi(x), outer product with (1 + gamma) g(x+mu)
+        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, q);
+        gamma_apply<T, MU>(q, tt);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) w[s][c] = cadd(q[s][c], tt[s][c]);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(px[f][s][i], cconj(w[s][j])));
+    }
     const T sc = (T)a.coef * bc;
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -153,7 +142,7 @@ __global__ void k_force(const ForceArgs a)
         using LL = LinkLayout<PREC, RECON>;
         const typename LL::chunk *G = reinterpret_cast<const typename LL::chunk *>(a.gauge);
         Link<T> U;
-        LinkLoader<PREC, RECON>::load(G + (size_t)(mu * 2 + par) * LL::N * a.Vh, cb, a.Vh, U);
+        LinkLoader<PREC, RECON>::load(G + (size_t)(MU * 2 + par) * LL::N * a.Vh, cb, a.Vh, U);
         C<T> zz[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -184,18 +173,69 @@ __global__ void k_force(const ForceArgs a)
                 m[i][j] = s;
             }
     }
-    const long lex = x + (long)a.Lx * (y + (long)a.Ly * (z + (long)a.Lz * t));
+}
+
+// the block's run of sites for direction MU: stage in shared memory, then 16-byte stores
+template <int MU, typename CT, typename T>
+__device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long V, bool valid, const C<T> m[3][3],
+                                           CT *tile)
+{
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                CT v;
+                v.x = m[i][j].r;
+                v.y = m[i][j].i;
+                tile[threadIdx.x * 9 + 3 * i + j] = v;
+            }
+    }
+    __syncthreads();
+    const long nsite = (V - lex0) < (long)blockDim.x ? (V - lex0) : (long)blockDim.x;
+    const long nvec = nsite * 9 * (long)sizeof(CT) / 16;  // 9 complex per site, a multiple of 16 bytes per 2 sites
+    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)MU * V + lex0) * 9);
+    const uint4 *src = reinterpret_cast<const uint4 *>(tile);
+    for (long k = threadIdx.x; k < nvec; k += blockDim.x) dst[k] = src[k];
+    // an odd number of complex64 sites leaves 8 bytes: written element-wise
+    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && threadIdx.x == 0)
+        reinterpret_cast<CT *>(a.out)[((long)MU * V + lex0) * 9 + nsite * 9 - 1] = tile[nsite * 9 - 1];
+    __syncthreads();
+}
+
+template <int PREC, int RECON, int NF, typename CT>
+__global__ void __launch_bounds__(128) k_force(const ForceArgs a)
+{
+    using T = typename Traits<PREC>::real;
+    __shared__ __align__(16) CT tile[128 * 9];
     const long V = 2L * a.Vh;
-    CT *o = reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex) * 9;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            CT v;
-            v.x = m[i][j].r;
-            v.y = m[i][j].i;
-            o[3 * i + j] = v;
-        }
+    const long lex0 = (long)blockIdx.x * blockDim.x;
+    const long lex = lex0 + threadIdx.x;
+    const bool valid = lex < V;  // every thread takes part in the block's barriers
+    int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0;
+    C<T> px[NF][4][3], gx[NF][4][3];
+    if (valid) {
+        long r = lex;
+        x = (int)(r % a.Lx);
+        r /= a.Lx;
+        y = (int)(r % a.Ly);
+        r /= a.Ly;
+        z = (int)(r % a.Lz);
+        t = (int)(r / a.Lz);
+        par = (x + y + z + t) & 1;
+        cb = (int)(lex >> 1);
+        load_site<PREC, NF>(a, a.psi, a.psi_norm, par, cb, px);
+        load_site<PREC, NF>(a, a.gv, a.gv_norm, par, cb, gx);
+    }
+    C<T> m[3][3];
+    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, px, gx, m);
+    store_links<0>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, px, gx, m);
+    store_links<1>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, px, gx, m);
+    store_links<2>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, px, gx, m);
+    store_links<3>(a, lex0, V, valid, m, tile);
 }
 
 }  // namespace tmk
@@ -242,22 +282,24 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     const int pidx = prec_index(psi_e->prec);
     a.gauge = g->links[pidx];
     a.out = F_canon;
-    const long n = 8L * g->Vh;
+    if (((uintptr_t)F_canon & 15) != 0) { set_error("tm_force: the output must be 16-byte aligned"); return TM_ERR_ARG; }
+    const long n = 2L * g->Vh;  // one thread per site
     const int block = 128;
     const long grid = (n + block - 1) / block;
     cudaStream_t s = (cudaStream_t)stream;
     const int recon = g->p.recon;
-#define TM_F(P, R, CT) k_force<P, R, CT><<<grid, block, 0, s>>>(a)
-#define TM_FR(P, CT)                         \
-    if (recon == 18) TM_F(P, 18, CT);         \
-    else if (recon == 12) TM_F(P, 12, CT);    \
-    else TM_F(P, 8, CT);
+#define TM_F1(P, R, CT) \
+    if (g->nf == 1) k_force<P, R, 1, CT><<<grid, block, 0, s>>>(a); else k_force<P, R, 2, CT><<<grid, block, 0, s>>>(a);
+#define TM_FR(P, CT)                              \
+    if (recon == 18) { TM_F1(P, 18, CT) }         \
+    else if (recon == 12) { TM_F1(P, 12, CT) }    \
+    else { TM_F1(P, 8, CT) }
     if (pidx == 0) {
         if (canon_type == TM_C128) { TM_FR(P64, double2) } else { TM_FR(P64, float2) }
     } else {
         if (canon_type == TM_C128) { TM_FR(P32, double2) } else { TM_FR(P32, float2) }
     }
 #undef TM_FR
-#undef TM_F
+#undef TM_F1
     return cuda_check(cudaGetLastError(), "tm_force launch");
 }

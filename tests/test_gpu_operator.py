@@ -52,8 +52,8 @@ def setup(case, recon):
 
 def use_variant(tmq, g, variant, block=128):
     """Force the hopping-kernel launch choice (0 plain, 2 pipelined, 3/4/5 register-capped 128x4/64x8/256x2,
-    6/7 shared-memory staged pipeline with 2/3 buffers; prologue launches keep 0 for 2, 6, 7)."""
-    pro_variant = variant if 3 <= variant <= 5 else 0  # 2, 6 and 7 have no prologue form
+    6/7 shared-memory staged pipeline with 2/3 buffers; prologue launches keep 0 for 2)."""
+    pro_variant = variant if variant >= 3 else 0  # 2 has no prologue form
     tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
 
