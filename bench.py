@@ -148,6 +148,21 @@ def aggregate_ranks(total_ms, units_local, world, device=None):
 
 
 # ------------------------------------------------------------------------------------------- ours
+def headline_config(args, nf, prec, recon, L, world):
+    """The benchmark's workload description, shared by both arms."""
+    flops_site = (CLOVER_FLOPS if args.csw else FLOPS_PER_SITE)[nf]
+    return {"workload": ("M_asym (eq. 2.2 LHS), non-degenerate doublet %s, kappa=0.1612, mu=0.135, eps=0.15"
+                         % "x".join(map(str, L)) if nf == 2 else
+                         "M_asym (eq. 2.2 LHS), one flavour %s, kappa=0.1612, mu=0.004"
+                         % "x".join(map(str, L))) + ", %s storage, recon-%d" % (args.prec.upper(), recon)
+                        + (", clover c_sw=%g" % args.csw if args.csw else ""),
+            "lattice": list(L), "flavours": nf, "storage": args.prec, "recon": recon,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2: links 403 MB, each spinor parity 201 MB, no flush",
+            "flops_per_even_site": flops_site,
+            "bytes_per_even_site": asym_bytes(prec, nf, recon) + (CLOVER_BYTES[prec] if args.csw else 0)}
+
+
 FORMS = {0: "thread per site", 2: "register pipeline", 3: "register cap 128x4", 4: "register cap 64x8",
          5: "register cap 256x2", 6: "shared-memory staged pipeline (cp.async)"}
 
@@ -243,16 +258,7 @@ def run_ours(args, rank, world):
         "value": round(value, 1), "unit": "GFLOPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.prec, "data": "synthetic (seeded SU(3) links exp(0.3 i H), Gaussian spinors)",
-        "config": {"workload": ("M_asym (eq. 2.2 LHS), non-degenerate doublet %s, kappa=0.1612, mu=0.135, eps=0.15"
-                                % "x".join(map(str, L)) if nf == 2 else
-                                "M_asym (eq. 2.2 LHS), one flavour %s, kappa=0.1612, mu=0.004"
-                                % "x".join(map(str, L))) + ", %s storage, recon-%d" % (args.prec.upper(), recon)
-                                + (", clover c_sw=%g" % args.csw if args.csw else ""),
-                   "lattice": list(L), "flavours": nf, "storage": args.prec, "recon": recon,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2: links 403 MB, each spinor parity 201 MB, no flush",
-                   "flops_per_even_site": flops_site,
-                   "bytes_per_even_site": asym_bytes(prec, nf, recon) + (CLOVER_BYTES[prec] if args.csw else 0)},
+        "config": headline_config(args, nf, prec, recon, L, world),
         "gpu_launches": 2 * K,
         "roofline": {"bound": "hbm", "kernel": "%s<%s, %s, recon-%d> (both launches of M_asym; launch form %s)"
                      % ("k_dslash_clov" if args.csw else "k_dslash", args.prec.upper(),
@@ -779,11 +785,11 @@ def run_reference(args):
     sample = ("%s sub-lattice of the 32^3x64 doublet workload (same parameters), one FP64 M_asym application "
               "per step" % "x".join(map(str, L)))
     return {"metric": "TM dslash GFLOPS & % HBM roofline per precision; CG time-to-1e-10 mixed vs FP64",
-            "impl": "reference", "value": round(value, 3), "unit": "GFLOPS", "n_gpus": 0, "steps": K, "warmup": W,
-            "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": "M_asym (eq. 2.2 LHS), non-degenerate doublet, kappa=0.1612, mu=0.135, "
-                                   "eps=0.15", "lattice": list(L)},
+            "impl": "reference", "value": round(value, 3), "unit": "GFLOPS", "n_gpus": args.gpus, "steps": K,
+            "warmup": W, "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SU(3) links exp(0.3 i H), Gaussian spinors)",
+            "device": "host cores (the FP64 CPU oracle)",
+            "config": headline_config(args, 2, 4, 12, L_FULL, 1),
             "cpu_baseline": {"value": round(value, 3), "unit": "GFLOPS", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
