@@ -345,9 +345,10 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * or the staged pipeline).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
- * uses defaults (capped 128 x 4; without prologue the shared-memory pipeline for FP32 and for
- * FP16 one flavour, not for one flavour with 18-real links; 4 right-hand sides per block; clover
- * 1 block per SM for FP64, 3 for FP16 and the FP32 doublet, 4 for FP32 one flavour).
+ * uses defaults (FP64 capped 128 x 4; FP32 and FP16 the shared-memory pipeline, two buffers for
+ * the FP32 doublet and three otherwise, except one flavour with 18-real links, capped; 4
+ * right-hand sides per block; clover 1 block per SM for FP64, 3 for FP16 and the FP32 doublet,
+ * 4 for FP32 one flavour).
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text, and back.  Single-RHS entries "f32:0:3:128" = precision:prologue:

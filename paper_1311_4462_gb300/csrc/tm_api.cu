@@ -467,13 +467,13 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
     for (int i = 0; i < 4; i++) {
-        // measured on GB300 at 32^3x64: the register cap (3) for every storage form; without
-        // prologue the shared-memory staged pipeline for FP32 (doublet: 2 buffers, 6; one flavour:
-        // 3 buffers, 7, except with 18-real links) and for FP16 one flavour (7, not with 18-real links)
+        // measured on GB300 at 32^3x64: the register cap (3) for FP64; for FP32 and FP16 the
+        // shared-memory staged pipeline (doublet FP32: 2 buffers, 6; otherwise 3 buffers, 7),
+        // except one flavour with 18-real links, where the register cap stays ahead
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};
         const bool nd = p->flavor == TM_NDEG_DOUBLET;
-        if (i == 1 && nd) g->tune[i][0] = tm_tune_entry{6, 128};
-        if ((i == 1 || i == 2) && !nd && p->recon != 18) g->tune[i][0] = tm_tune_entry{7, 128};
+        if ((i == 1 || i == 2) && (nd || p->recon != 18))
+            for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(i == 1 && nd) ? 6 : 7, 128};
         g->multi_rpb[i] = 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);

@@ -54,6 +54,25 @@ __device__ __forceinline__ void acc_add(T *a, int k, C<T> w, T q)
     a[k] = fma(q, w.r, a[k]);
     a[k + 1] = fma(q, w.i, a[k + 1]);
 }
+// binary32: both reals of the complex in one packed FMA (Blackwell's f32x2 FMA; the same
+// rounding as two scalar FMAs), halving the issue slots of the accumulation
+__device__ __forceinline__ void acc_add(float *a, int k, C<float> w, float q)
+{
+    const float2 r = __ffma2_rn(make_float2(q, q), make_float2(w.r, w.i), make_float2(a[k], a[k + 1]));
+    a[k] = r.x;
+    a[k + 1] = r.y;
+}
+// c + s b for a real s
+template <typename T>
+__device__ __forceinline__ C<T> cfma_s(T s, C<T> b, C<T> c)
+{
+    return {fma(s, b.r, c.r), fma(s, b.i, c.i)};
+}
+__device__ __forceinline__ C<float> cfma_s(float s, C<float> b, C<float> c)
+{
+    const float2 r = __ffma2_rn(make_float2(s, s), make_float2(b.r, b.i), make_float2(c.r, c.i));
+    return {r.x, r.y};
+}
 // a += q * i * w
 template <typename T>
 __device__ __forceinline__ void acc_addi(T *a, int k, C<T> w, T q)
@@ -94,14 +113,14 @@ __device__ __forceinline__ void hop_one(T *acc, const Link<T> &U, const T *v, T 
             h0[c] = {fma(-sp, p3.i, p0.r), fma(sp, p3.r, p0.i)};
             h1[c] = {fma(-sp, p2.i, p1.r), fma(sp, p2.r, p1.i)};
         } else if (MU == 1) { // h0 = p0 - sp p3,  h1 = p1 + sp p2
-            h0[c] = {fma(-sp, p3.r, p0.r), fma(-sp, p3.i, p0.i)};
-            h1[c] = {fma(sp, p2.r, p1.r), fma(sp, p2.i, p1.i)};
+            h0[c] = cfma_s(-sp, p3, p0);
+            h1[c] = cfma_s(sp, p2, p1);
         } else if (MU == 2) { // h0 = p0 + sp i p2,  h1 = p1 - sp i p3
             h0[c] = {fma(-sp, p2.i, p0.r), fma(sp, p2.r, p0.i)};
             h1[c] = {fma(sp, p3.i, p1.r), fma(-sp, p3.r, p1.i)};
         } else {              // h0 = p0 + sp p2,  h1 = p1 + sp p3
-            h0[c] = {fma(sp, p2.r, p0.r), fma(sp, p2.i, p0.i)};
-            h1[c] = {fma(sp, p3.r, p1.r), fma(sp, p3.i, p1.i)};
+            h0[c] = cfma_s(sp, p2, p0);
+            h1[c] = cfma_s(sp, p3, p1);
         }
     }
     C<T> w0[3], w1[3];
