@@ -356,10 +356,22 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
  * 128 / 64 / 256-thread blocks, 6 / 7 pipelined through shared memory with cp.async, two / three
  * buffers; 2 has no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
- * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline.  Import accepts any subset of the entries; an
+ * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline;
+ * fused-operator entries "f32:p:1" = precision:p:1 when tm_precond_op runs as one fused launch
+ * (FP64 and FP32; see tm_device_status).  Import accepts any subset of the entries; an
  * invalid entry leaves the table unchanged and returns TM_ERR_ARG. */
 tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n);
 tm_status tm_tune_import(tm_gauge *g, const char *text);
+
+/*
+ * Status of the handle's bounded device-side waits.  The fused form of tm_precond_op (tune entry
+ * "<prec>:p:1": both passes of M_pc in one persistent launch whose second-pass tiles wait, with a
+ * time limit, for the first-pass tiles they read) records a wait that gave up in a device word
+ * instead of hanging; the affected sites are left unwritten.  This call synchronises `stream`,
+ * returns TM_ERR_TIMEOUT (and clears the word) if any wait gave up since the last call, TM_OK
+ * otherwise.
+ */
+tm_status tm_device_status(const tm_gauge *g, void *stream);
 
 /* --------------------------------------------------------------------- allocation-free variant */
 /*

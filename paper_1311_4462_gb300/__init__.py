@@ -202,6 +202,11 @@ def local_op(gauge, out: Field, inp: Field, parity: int, inverse=False, dagger=F
     return out
 
 
+def device_status(gauge, stream=None):
+    """tm_device_status: raises TMError (TM_ERR_TIMEOUT) if a bounded device-side wait gave up."""
+    L.check(L.load().tm_device_status(gauge.h, _stream(stream)))
+
+
 def set_clover(gauge, csw: float, stream=None):
     """tm_gauge_set_clover: add the clover term with coefficient c_sw (0 removes it)."""
     L.check(L.load().tm_gauge_set_clover(gauge.h, float(csw), _stream(stream)))

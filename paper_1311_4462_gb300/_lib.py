@@ -86,6 +86,7 @@ _SIGS = {
     "tm_tune_import": [vp, ctypes.c_char_p],
     "tm_gauge_set_clover": [vp, ctypes.c_double, vp],
     "tm_local_op": [vp, FP, FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
+    "tm_device_status": [vp, vp],
 }
 
 

@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "tm_dslash.cuh"
 #include "tm_internal.h"
 
@@ -57,6 +59,10 @@ cudaError_t launch_twist(const tm_gauge *g, const tm_field *out, const tm_field 
 cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm_field *in, const Twist<double> &tw,
                                 const int *act, int nact, cudaStream_t s);
 cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, int minb, cudaStream_t s);
+cudaError_t launch_fused_p64(const DslashArgs<double> &aA, const DslashArgs<double> &aB, int nf, int recon,
+                             const int *items, int nitems, int *sync, int num_sms, cudaStream_t s);
+cudaError_t launch_fused_p32(const DslashArgs<float> &aA, const DslashArgs<float> &aB, int nf, int recon,
+                             const int *items, int nitems, int *sync, int num_sms, cudaStream_t s);
 cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_clover_apply(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, bool inverse,
@@ -402,9 +408,97 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
     }
 }
 
+// Work list of the fused operator (k_mpc_fused): items (tile << 1) | pass, pass 0 = A (odd
+// output), 1 = B (even output).  A site's neighbours lie within one time slice (st sites) of it,
+// or across the periodic wrap in the last / first slice, so: the A tiles touching the last time
+// slice first, then A tiles from 0 up, with each B tile emitted after the A tiles one slice and
+// a resident wave of tiles beyond it.  Every B tile then depends only on A tiles earlier in the
+// list.
+tm_status build_fused_work(tm_gauge *g, cudaStream_t s)
+{
+    // in work items of FUSED_GROUP tiles of 128 sites
+    const long Vh = g->Vh, st = (long)g->X1h * g->p.L[1] * g->p.L[2];
+    const long gs = 128L * FUSED_GROUP;
+    const int ntiles = (int)((Vh + 127) / 128);
+    const int N = (int)((Vh + gs - 1) / gs);
+    const int P = (int)((st + gs - 1) / gs) + 1;
+    const int first = (int)(Vh - st > 0 ? (Vh - st) / gs : 0);  // A groups [first, N) touch the last slice
+    std::vector<int> items;
+    items.reserve(2 * (size_t)N);
+    for (int t = first; t < N; t++) items.push_back(t << 1);
+    int nextA = 0;
+    // A runs ahead of B by one time slice plus the blocks in flight (up to 4 per SM), so the groups a
+    // B group reads have normally finished before it is claimed
+    const int W = P + 3 + (4 * (g->num_sms > 0 ? g->num_sms : 152) + FUSED_GROUP - 1) / FUSED_GROUP;
+    while (nextA < first && nextA < W) items.push_back((nextA++) << 1);
+    for (int i = 0; i < N; i++) {
+        items.push_back((i << 1) | 1);
+        if (nextA < first) items.push_back((nextA++) << 1);
+    }
+    g->fused_nitems = (int)items.size();
+    // flags per 128-site tile, rounded up to whole groups
+    const size_t nflags = (size_t)N * FUSED_GROUP;
+    (void)ntiles;
+    if (cudaMalloc((void **)&g->fused_items, sizeof(int) * items.size()) != cudaSuccess ||
+        cudaMalloc((void **)&g->fused_sync, sizeof(int) * (2 + nflags)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tm_gauge_create: work list allocation failed");
+        return TM_ERR_NOMEM;
+    }
+    TM_TRY(cuda_check(cudaMemcpyAsync(g->fused_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice, s),
+                      "work list copy"));
+    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync, 0, sizeof(int) * (2 + nflags), s), "work list memset"));
+    return cuda_check(cudaStreamSynchronize(s), "work list");
+}
+
+template <typename T>
+static DslashArgs<T> pass_args(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x,
+                               int out_parity, int dagger, int epi, double coef, const Twist<T> &tw, int pidx)
+{
+    DslashArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    fill_common(a, g, out, in, x, out_parity, pidx);
+    a.epilogue = epi;
+    a.sigma = dagger ? T(-1) : T(1);
+    a.coef = (T)coef;
+    a.tw_epi = tw;
+    a.tw_pro = tw;
+    return a;
+}
+
+// M_pc as one fused launch (FP64 / FP32, no clover, one right-hand side, not the adjoint of the
+// symmetric operator): A = (tmp <- Ti_oo H_oe in), B = (out <- epilogue of H_eo tmp)
+static tm_status fused_launch(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
+                              int pc, int dagger, cudaStream_t s)
+{
+    const double k2 = g->p.kappa * g->p.kappa;
+    const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
+    const int epiB = pc == TM_PC_ASYM ? EPI_TWX_AXPY : EPI_X_TWAXPY;
+    const Twist<double> &twB = pc == TM_PC_ASYM ? R : Ri;
+    const size_t nflags = (size_t)((g->Vh + 128L * FUSED_GROUP - 1) / (128L * FUSED_GROUP)) * FUSED_GROUP;
+    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync + 1, 0, sizeof(int) * (1 + nflags), s), "fused reset"));
+    cudaError_t e;
+    if (out_e->prec == TM_PREC_F64) {
+        const DslashArgs<double> aA = pass_args<double>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, Ri, 0);
+        const DslashArgs<double> aB = pass_args<double>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, twB, 0);
+        e = launch_fused_p64(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->num_sms, s);
+    } else {
+        const DslashArgs<float> aA = pass_args<float>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, to_float(Ri), 1);
+        const DslashArgs<float> aB = pass_args<float>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, to_float(twB), 1);
+        e = launch_fused_p32(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->num_sms, s);
+    }
+    return cuda_check(e, "fused operator launch");
+}
+
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact)
 {
+    {
+        const int pidx = prec_index(out_e->prec);
+        if ((pidx == 0 || pidx == 1) && g->fused[pidx] && g->csw == 0.0 && act == nullptr && nact <= 1 &&
+            out_e->nrhs == 1 && !(pc == TM_PC_SYM && dagger) && g->fused_sync)
+            return fused_launch(g, out_e, in_e, tmp_o, pc, dagger, s);
+    }
     const double k2 = g->p.kappa * g->p.kappa;
     const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
     if (g->csw != 0.0 && (out_e->prec == TM_PREC_DF64 || act != nullptr || nact > 1)) {
@@ -515,6 +609,7 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
         set_error("tm_gauge_create: pinned host allocation failed");
         st = TM_ERR_NOMEM;
     }
+    if (st == TM_OK) st = build_fused_work(g, s);
     if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tm_gauge_create sync");
     if (st != TM_OK) {
         tm_gauge_destroy(g);
@@ -531,6 +626,8 @@ tm_status tm_gauge_destroy(tm_gauge *g)
     for (int i = 0; i < 4; i++)
         if (g->links[i]) cudaFree(g->links[i]);
     clover_free(g);
+    if (g->fused_items) cudaFree(g->fused_items);
+    if (g->fused_sync) cudaFree(g->fused_sync);
     if (g->scratch) cudaFree(g->scratch);
     if (g->host_scalars) cudaFreeHost(g->host_scalars);
     delete g;
@@ -728,6 +825,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
         {
             memcpy(dst->tune, src->tune, sizeof(dst->tune));
             memcpy(dst->multi_rpb, src->multi_rpb, sizeof(dst->multi_rpb));
+            memcpy(dst->fused, src->fused, sizeof(dst->fused));
         }
     } copy_back{g0, g};
     cudaStream_t s = (cudaStream_t)stream;
@@ -808,6 +906,37 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             g0->clov_minb[pi] = bestm;
         }
     }
+    // fused operator or two launches, timed on the asymmetric operator (FP64, FP32)
+    for (int pi = 0; pi < 2 && st == TM_OK; pi++) {
+        tm_field_bytes(g, precs[pi], 1, &d, &n);
+        tm_field f[3];
+        for (int k = 0; k < 3; k++) {
+            f[k].data = (char *)buf + k * fb;
+            f[k].norm = nullptr;
+            f[k].prec = precs[pi];
+            f[k].nrhs = 1;
+        }
+        float best = 1e30f;
+        int bestf = 0;
+        for (int fz = 0; fz < 2 && st == TM_OK; fz++) {
+            g->fused[pi] = fz;
+            float ms = 0;
+            for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
+                st = cuda_check(cudaEventRecord(e0, s), "event");
+                if (st == TM_OK) st = precond_core(g, &f[0], &f[1], &f[2], TM_PC_ASYM, 0, s, nullptr, 1);
+                if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+                if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+                float t = 0;
+                if (st == TM_OK) cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;
+            }
+            if (st == TM_OK && ms < best) {
+                best = ms;
+                bestf = fz;
+            }
+        }
+        g->fused[pi] = bestf;
+    }
     // multi-RHS block shape (right-hand sides per block), timed on 8 right-hand sides of the
     // single-RHS buffers' size each: the fields are carved from one allocation of 3 x 8 fields
     for (int pi = 0; pi < 3 && st == TM_OK; pi++) {
@@ -883,6 +1012,11 @@ tm_status tm_tune_export(const tm_gauge *g, char *buf, size_t n)
         if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
         off += (size_t)w;
     }
+    for (int pi = 0; pi < 2; pi++) {
+        int w = snprintf(buf + off, n - off, " %s:p:%d", names[pi], g->fused[pi]);
+        if (w < 0 || (size_t)w >= n - off) { set_error("tm_tune_export: buffer too small"); return TM_ERR_ARG; }
+        off += (size_t)w;
+    }
     return TM_OK;
 }
 
@@ -890,10 +1024,11 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
 {
     if (!g || !text) { set_error("tm_tune_import: null argument"); return TM_ERR_ARG; }
     tm_tune_entry t[3][2];
-    int mr[3], cm[3];
+    int mr[3], cm[3], fu[3];
     memcpy(t, g->tune, sizeof(t));
     memcpy(mr, g->multi_rpb, sizeof(mr));
     memcpy(cm, g->clov_minb, sizeof(cm));
+    memcpy(fu, g->fused, sizeof(fu));
     const char *p = text;
     while (*p) {
         while (*p == ' ') p++;
@@ -908,6 +1043,18 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
                 return TM_ERR_ARG;
             }
             mr[pi] = block;
+            p += used;
+            continue;
+        }
+        used = 0;
+        if (sscanf(p, "%3[a-z0-9]:p:%d%n", name, &block, &used) == 2 && used > 0) {
+            // fused-operator entry "<prec>:p:<0|1>" (FP64 / FP32)
+            const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : -1);
+            if (pi < 0 || (block != 0 && block != 1)) {
+                set_error("tm_tune_import: invalid entry '%.32s'", p);
+                return TM_ERR_ARG;
+            }
+            fu[pi] = block;
             p += used;
             continue;
         }
@@ -940,6 +1087,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
     memcpy(g->tune, t, sizeof(t));
     memcpy(g->multi_rpb, mr, sizeof(mr));
     memcpy(g->clov_minb, cm, sizeof(cm));
+    memcpy(g->fused, fu, sizeof(fu));
     return TM_OK;
 }
 
@@ -975,6 +1123,22 @@ tm_status tm_local_op(const tm_gauge *g, const tm_field *out, const tm_field *in
         return TM_ERR_ARG;
     }
     return cuda_check(launch_clover_apply(g, out, in, parity, inverse != 0, clover_x(g, dagger), s), "tm_local_op");
+}
+
+tm_status tm_device_status(const tm_gauge *g, void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    int err = 0;
+    TM_TRY(cuda_check(cudaMemcpyAsync(&err, g->fused_sync, sizeof(int), cudaMemcpyDeviceToHost, s), "status read"));
+    TM_TRY(cuda_check(cudaStreamSynchronize(s), "status sync"));
+    if (err) {
+        TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync, 0, sizeof(int), s), "status reset"));
+        TM_TRY(cuda_check(cudaStreamSynchronize(s), "status sync"));
+        set_error("a bounded device-side wait gave up (the fused operator's output is incomplete)");
+        return TM_ERR_TIMEOUT;
+    }
+    return TM_OK;
 }
 
 tm_status tm_gauge_set_clover(tm_gauge *g, double csw, void *stream)

@@ -661,18 +661,41 @@ __device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[N
     }
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
-__global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+// Completion flags of the fused operator (below): release after a tile's stores, acquire before
+// a dependent tile's loads.  A wait gives up after about a quarter second, records the failure in
+// *err and reports false (the caller then skips its site).
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool wait_flag(const int *f, int *err)
+{
+    for (int i = 0; i < (1 << 22); i++) {
+        if (ld_acquire_gpu(f) != 0) return true;
+        __nanosleep(64);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+// One site of the staged hop pipeline (launch forms 6 / 7 and the fused operator).  WAIT: the
+// input field is produced by other tiles of the same launch; before its first load the thread
+// waits for the completion flags of the 128-site tiles that hold its 8 neighbours.
+template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT>
+__device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
+                                           char *smem_async, const int *flags, int *err)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
     using LC = typename LL::chunk;
     using SC = typename Traits<PREC>::schunk;
     using H = AsyncHop<PREC, RECON, NF>;
-    extern __shared__ __align__(16) char smem_async[];
-    const int tid = threadIdx.x;
-    const int cb = blockIdx.x * H::BS + tid;
-    if (cb >= a.Vh) return;
     int r = cb;
     const int xh = r % a.X1h;
     r /= a.X1h;
@@ -704,6 +727,12 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         for (int k = 0; k < 24; k++) acc[f][k] = T(0);
     // hop h: (mu, forward?) = (h / 2, h even); link at the output site (forward) or at the neighbour
     const int nbr[8] = {n0, n1, n2, n3, n4, n5, n6, n7};
+    if constexpr (WAIT) {
+        bool ok = true;
+#pragma unroll
+        for (int h = 0; h < 8; h++) ok = ok && wait_flag(flags + (nbr[h] >> 7), err);
+        if (!ok) return;
+    }
     auto fetch = [&](int h) {
         char *b = smem_async + (h % NB) * H::BUF;
         const int mu = h >> 1;
@@ -771,6 +800,69 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
+__global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+{
+    extern __shared__ __align__(16) char smem_async[];
+    const int tid = threadIdx.x;
+    const int cb = blockIdx.x * AsyncHop<PREC, RECON, NF>::BS + tid;
+    if (cb >= a.Vh) return;
+    async_site<PREC, NF, RECON, CLOV, NB, PRO, false>(a, cb, tid, smem_async, nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------------------------------
+// The fused preconditioned operator: both launches of M_pc (A: t = T_oo H_oe in, B: out = ...
+// H_eo t) in one persistent launch.  The 128-site tiles of A and B are claimed from a device
+// work list in an order where every B tile comes after the A tiles its neighbours live in (the
+// A tiles of the last time slice first, then A ahead of B by one time slice and a few tiles), so
+// each t tile is read back by B shortly after A wrote it: the intermediate field and the links
+// both passes read stay in L2 instead of making a second trip through HBM.  A tile's completion
+// is published with a release flag once all its threads' stores are done; a B site acquires the
+// flags of its neighbours' tiles before loading them (bounded waits).  Claiming in list order
+// means a waited-for tile has always been claimed by a running block, so the waits end.
+// sync: [0] error word (kept until read), [1] work counter, [2 + tile] A-tile completion flags;
+// the counter and the flags are zero at launch.
+constexpr int FUSED_GROUP = 4;  // 128-site tiles per work item of the fused operator
+
+template <int PREC, int NF, int RECON, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    k_mpc_fused(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> aA,
+                const __grid_constant__ DslashArgs<typename Traits<PREC>::real> aB, const int *__restrict__ items,
+                int nitems, int *sync)
+{
+    extern __shared__ __align__(16) char smem_async[];
+    __shared__ int s_q;
+    int *err = sync, *counter = sync + 1, *flags = sync + 2;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(counter, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();  // every thread has read s_q before it is claimed again
+        if (q >= nitems) break;
+        const int it = __ldg(items + q);
+        const int grp = it >> 1;  // FUSED_GROUP consecutive 128-site tiles per work item
+        if (it & 1) {
+            for (int sub = 0; sub < FUSED_GROUP; sub++) {
+                const int cb = (grp * FUSED_GROUP + sub) * 128 + tid;
+                if (cb < aB.Vh) async_site<PREC, NF, RECON, false, 2, false, true>(aB, cb, tid, smem_async, flags, err);
+            }
+        } else {
+            for (int sub = 0; sub < FUSED_GROUP; sub++) {
+                const int cb = (grp * FUSED_GROUP + sub) * 128 + tid;
+                if (cb < aA.Vh)
+                    async_site<PREC, NF, RECON, false, 2, false, false>(aA, cb, tid, smem_async, nullptr, nullptr);
+            }
+            // the block's stores happen before one thread's gpu-scope release of the tiles
+            __syncthreads();
+            if (tid < FUSED_GROUP) {
+                __threadfence();
+                st_release_gpu(flags + grp * FUSED_GROUP + tid, 1);
+            }
+        }
+    }
+}
+
 // The shared-memory opt-in is set once per kernel and device: the attribute call is not a
 // stream operation and can wait for work already queued on the device, so it must stay out of
 // the per-launch path (it would serialise copy streams with the compute stream).
@@ -791,6 +883,54 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
     }
     k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
+}
+
+// The fused operator's launch: a resident wave of blocks (occupancy calculator, once per kernel).
+template <int PREC, int NF, int RECON>
+cudaError_t launch_fused_impl(const DslashArgs<typename Traits<PREC>::real> &aA,
+                              const DslashArgs<typename Traits<PREC>::real> &aB, const int *items, int nitems,
+                              int *sync, int num_sms, cudaStream_t s)
+{
+    constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
+    static std::atomic<unsigned long long> opted{0};
+    static std::atomic<int> per_sm{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_mpc_fused<PREC, NF, RECON, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    int b = per_sm.load(std::memory_order_relaxed);
+    if (b == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mpc_fused<PREC, NF, RECON, 3>, 128, bytes);
+        if (e != cudaSuccess) return e;
+        b = b > 0 ? b : 1;
+        per_sm.store(b, std::memory_order_relaxed);
+    }
+    const int grid = (num_sms > 0 ? num_sms : 1) * b;
+    k_mpc_fused<PREC, NF, RECON, 3><<<grid, 128, bytes, s>>>(aA, aB, items, nitems, sync);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_fused_dispatch(const DslashArgs<typename Traits<PREC>::real> &aA,
+                                  const DslashArgs<typename Traits<PREC>::real> &aB, int nf, int recon,
+                                  const int *items, int nitems, int *sync, int num_sms, cudaStream_t s)
+{
+#define TM_FU(NF, R) return launch_fused_impl<PREC, NF, R>(aA, aB, items, nitems, sync, num_sms, s);
+#define TM_FUR(NF)                         \
+    switch (recon) {                       \
+    case 18: TM_FU(NF, 18)                 \
+    case 12: TM_FU(NF, 12)                 \
+    case 8: TM_FU(NF, 8)                   \
+    default: return cudaErrorInvalidValue; \
+    }
+    if (nf == 1) { TM_FUR(1) } else { TM_FUR(2) }
+#undef TM_FUR
+#undef TM_FU
 }
 
 // Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in

@@ -53,6 +53,10 @@ struct tm_gauge {
     void *clov[3];             // per-site local clover operator, FP64 / FP32 / FP16 (tm_clover.cuh)
     float *clov_norm;          // FP16 block scales
     int clov_minb[3];          // clover kernel: resident blocks per SM its registers allow (1, 3, 4), 6: staged
+    int fused[3];              // 1: the preconditioned operator as one fused launch (FP64 / FP32; FP16 unused)
+    int *fused_items;          // device work list of the fused operator (2 x tiles entries)
+    int fused_nitems;
+    int *fused_sync;           // [0] error word, [1] work counter, [2 + tile] A-tile flags
     size_t scratch_bytes;
 };
 
