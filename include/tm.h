@@ -373,6 +373,16 @@ tm_status tm_tune_import(tm_gauge *g, const char *text);
  */
 tm_status tm_device_status(const tm_gauge *g, void *stream);
 
+/*
+ * The fused operator's work list for a lattice (host only, no GPU; for inspection and tests):
+ * entries (group << 1) | pass, pass 0 = first pass (odd output), 1 = second pass (even output),
+ * a group being 4 tiles of 128 consecutive checkerboard sites.  Every second-pass group appears
+ * after the first-pass groups holding its sites' neighbours.  With items = NULL returns the
+ * length; otherwise fills items (capacity entries) and returns the length, or -1 on odd or too
+ * small extents or too small a capacity.
+ */
+int tm_fused_work_list(const int L[4], int num_sms, int *items, int capacity);
+
 /* --------------------------------------------------------------------- allocation-free variant */
 /*
  * |x|^2 of each right-hand side of a parity field (the tm_norm2 reduction), for callers that

@@ -87,6 +87,7 @@ _SIGS = {
     "tm_gauge_set_clover": [vp, ctypes.c_double, vp],
     "tm_local_op": [vp, FP, FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
     "tm_device_status": [vp, vp],
+    "tm_fused_work_list": [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
 }
 
 

@@ -414,12 +414,11 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
 // slice first, then A tiles from 0 up, with each B tile emitted after the A tiles one slice and
 // a resident wave of tiles beyond it.  Every B tile then depends only on A tiles earlier in the
 // list.
-tm_status build_fused_work(tm_gauge *g, cudaStream_t s)
+static std::vector<int> fused_items(const int L[4], int num_sms)
 {
     // in work items of FUSED_GROUP tiles of 128 sites
-    const long Vh = g->Vh, st = (long)g->X1h * g->p.L[1] * g->p.L[2];
+    const long Vh = (long)L[0] * L[1] * L[2] * L[3] / 2, st = (long)(L[0] / 2) * L[1] * L[2];
     const long gs = 128L * FUSED_GROUP;
-    const int ntiles = (int)((Vh + 127) / 128);
     const int N = (int)((Vh + gs - 1) / gs);
     const int P = (int)((st + gs - 1) / gs) + 1;
     const int first = (int)(Vh - st > 0 ? (Vh - st) / gs : 0);  // A groups [first, N) touch the last slice
@@ -429,16 +428,21 @@ tm_status build_fused_work(tm_gauge *g, cudaStream_t s)
     int nextA = 0;
     // A runs ahead of B by one time slice plus the blocks in flight (up to 4 per SM), so the groups a
     // B group reads have normally finished before it is claimed
-    const int W = P + 3 + (4 * (g->num_sms > 0 ? g->num_sms : 152) + FUSED_GROUP - 1) / FUSED_GROUP;
+    const int W = P + 3 + (4 * (num_sms > 0 ? num_sms : 152) + FUSED_GROUP - 1) / FUSED_GROUP;
     while (nextA < first && nextA < W) items.push_back((nextA++) << 1);
     for (int i = 0; i < N; i++) {
         items.push_back((i << 1) | 1);
         if (nextA < first) items.push_back((nextA++) << 1);
     }
+    return items;
+}
+
+tm_status build_fused_work(tm_gauge *g, cudaStream_t s)
+{
+    const std::vector<int> items = fused_items(g->p.L, g->num_sms);
     g->fused_nitems = (int)items.size();
     // flags per 128-site tile, rounded up to whole groups
-    const size_t nflags = (size_t)N * FUSED_GROUP;
-    (void)ntiles;
+    const size_t nflags = (size_t)((g->Vh + 128L * FUSED_GROUP - 1) / (128L * FUSED_GROUP)) * FUSED_GROUP;
     if (cudaMalloc((void **)&g->fused_items, sizeof(int) * items.size()) != cudaSuccess ||
         cudaMalloc((void **)&g->fused_sync, sizeof(int) * (2 + nflags)) != cudaSuccess) {
         cudaGetLastError();
@@ -1123,6 +1127,19 @@ tm_status tm_local_op(const tm_gauge *g, const tm_field *out, const tm_field *in
         return TM_ERR_ARG;
     }
     return cuda_check(launch_clover_apply(g, out, in, parity, inverse != 0, clover_x(g, dagger), s), "tm_local_op");
+}
+
+int tm_fused_work_list(const int L[4], int num_sms, int *items, int capacity)
+{
+    if (!L) return -1;
+    for (int m = 0; m < 4; m++)
+        if (L[m] < 2 || (L[m] & 1)) return -1;
+    const std::vector<int> v = fused_items(L, num_sms);
+    if (items) {
+        if (capacity < (int)v.size()) return -1;
+        memcpy(items, v.data(), sizeof(int) * v.size());
+    }
+    return (int)v.size();
 }
 
 tm_status tm_device_status(const tm_gauge *g, void *stream)
