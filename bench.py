@@ -164,7 +164,9 @@ def headline_config(args, nf, prec, recon, L, world):
 
 
 FORMS = {0: "thread per site", 2: "register pipeline", 3: "register cap 128x4", 4: "register cap 64x8",
-         5: "register cap 256x2", 6: "shared-memory staged pipeline (cp.async)"}
+         5: "register cap 256x2", 6: "shared-memory staged pipeline (cp.async)",
+         7: "shared-memory staged pipeline, 3 buffers", 8: "staged pipeline, flavour-paired hop",
+         9: "staged pipeline, 3 buffers, flavour-paired hop"}
 
 
 def launch_form(table, prec, csw=0.0):

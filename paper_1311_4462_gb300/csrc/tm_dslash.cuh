@@ -21,6 +21,7 @@
 // and used for both (sec. 2.1).
 #pragma once
 #include <atomic>
+#include <type_traits>
 
 #include "tm_clover.cuh"
 #include "tm_core.cuh"
@@ -147,14 +148,139 @@ __device__ __forceinline__ void hop_one(T *acc, const Link<T> &U, const T *v, T 
     }
 }
 
-template <int PREC, int NF, bool PRO, int MU, bool FWD, typename T>
+// ---- The doublet with its flavours paired (binary32 arithmetic; launch forms 8 / 9) ----
+// Both flavours see the same link, so real k of flavour 0 and real k of flavour 1 share one
+// 64-bit register pair: every product with a link element serves both flavours in one packed
+// FMA (a complex product is four of them), and the projection and the accumulation are packed
+// too.  Multiplication by i only renames the real and imaginary pairs.  The sign of the
+// complex products comes from the negated real or imaginary pair of each projected colour (six
+// packed multiplies per hop), and the per-flavour scale (boundary sign times the FP16 site norm)
+// is a pair as well.  Every operation rounds as a binary32 FMA, as in hop_one; the order of the
+// link products differs, so results agree with hop_one to rounding.
+// PACK: pack the projection as well (inputs that come out of conversions or arithmetic land in
+// register pairs for free; 16-byte binary32 loads give four registers of one flavour, which
+// scalar FMAs pair up without moves).
+template <bool PACK>
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
+{
+    if constexpr (PACK) return __ffma2_rn(a, b, c);
+    else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+
+template <int MU, bool FWD, bool PACK>
+__device__ __forceinline__ void hop_pair(float (&acc)[2][24], const Link<float> &U, const float (&v)[2][24], float sp,
+                                         float2 sg)
+{
+    const float2 s = make_float2(sp, sp), ns = make_float2(-sp, -sp);
+    auto V = [&](int k) { return make_float2(v[0][k], v[1][k]); };
+    // projected rows h0, h1 per colour: real and imaginary pairs
+    float2 h0r[3], h0i[3], h1r[3], h1i[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int p0 = 2 * c, p1 = 6 + 2 * c, p2 = 12 + 2 * c, p3 = 18 + 2 * c;
+        if (MU == 0) {        // h0 = p0 + sp i p3,  h1 = p1 + sp i p2
+            h0r[c] = pfma<PACK>(ns, V(p3 + 1), V(p0)); h0i[c] = pfma<PACK>(s, V(p3), V(p0 + 1));
+            h1r[c] = pfma<PACK>(ns, V(p2 + 1), V(p1)); h1i[c] = pfma<PACK>(s, V(p2), V(p1 + 1));
+        } else if (MU == 1) { // h0 = p0 - sp p3,  h1 = p1 + sp p2
+            h0r[c] = pfma<PACK>(ns, V(p3), V(p0)); h0i[c] = pfma<PACK>(ns, V(p3 + 1), V(p0 + 1));
+            h1r[c] = pfma<PACK>(s, V(p2), V(p1)); h1i[c] = pfma<PACK>(s, V(p2 + 1), V(p1 + 1));
+        } else if (MU == 2) { // h0 = p0 + sp i p2,  h1 = p1 - sp i p3
+            h0r[c] = pfma<PACK>(ns, V(p2 + 1), V(p0)); h0i[c] = pfma<PACK>(s, V(p2), V(p0 + 1));
+            h1r[c] = pfma<PACK>(s, V(p3 + 1), V(p1)); h1i[c] = pfma<PACK>(ns, V(p3), V(p1 + 1));
+        } else {              // h0 = p0 + sp p2,  h1 = p1 + sp p3
+            h0r[c] = pfma<PACK>(s, V(p2), V(p0)); h0i[c] = pfma<PACK>(s, V(p2 + 1), V(p0 + 1));
+            h1r[c] = pfma<PACK>(s, V(p3), V(p1)); h1i[c] = pfma<PACK>(s, V(p3 + 1), V(p1 + 1));
+        }
+    }
+    // w = U h:      re = sum ur hr + ui (-hi),  im = sum ur hi + ui hr
+    // w = U^dag h:  re = sum ur hr + ui hi,     im = sum ur hi + ui (-hr)   (u = U[b][a])
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 g0[3], g1[3];  // the negated pair of each colour: -hi (forward) or -hr (backward)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        g0[c] = __fmul2_rn(m1, FWD ? h0i[c] : h0r[c]);
+        g1[c] = __fmul2_rn(m1, FWD ? h1i[c] : h1r[c]);
+    }
+    float2 w0r[3], w0i[3], w1r[3], w1i[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const C<float> u = FWD ? U.u[a][b] : U.u[b][a];
+            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i);
+            const float2 x0 = FWD ? g0[b] : h0i[b], x1 = FWD ? g1[b] : h1i[b];  // partner of ui in re
+            const float2 y0 = FWD ? h0r[b] : g0[b], y1 = FWD ? h1r[b] : g1[b];  // partner of ui in im
+            if (b == 0) {
+                w0r[a] = __fmul2_rn(ur, h0r[b]); w0i[a] = __fmul2_rn(ur, h0i[b]);
+                w1r[a] = __fmul2_rn(ur, h1r[b]); w1i[a] = __fmul2_rn(ur, h1i[b]);
+            } else {
+                w0r[a] = __ffma2_rn(ur, h0r[b], w0r[a]); w0i[a] = __ffma2_rn(ur, h0i[b], w0i[a]);
+                w1r[a] = __ffma2_rn(ur, h1r[b], w1r[a]); w1i[a] = __ffma2_rn(ur, h1i[b], w1i[a]);
+            }
+            w0r[a] = __ffma2_rn(ui, x0, w0r[a]); w0i[a] = __ffma2_rn(ui, y0, w0i[a]);
+            w1r[a] = __ffma2_rn(ui, x1, w1r[a]); w1i[a] = __ffma2_rn(ui, y1, w1i[a]);
+        }
+    }
+    // accumulate the four spin rows (the same reconstruction as hop_one)
+    const float2 q = make_float2(sg.x * sp, sg.y * sp), nq = make_float2(-q.x, -q.y);
+    float2 A[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) A[k] = make_float2(acc[0][k], acc[1][k]);
+    auto add = [&](int k, float2 wr, float2 wi, float2 f) {  // row += f w
+        A[k] = __ffma2_rn(f, wr, A[k]);
+        A[k + 1] = __ffma2_rn(f, wi, A[k + 1]);
+    };
+    auto addi = [&](int k, float2 wr, float2 wi, float2 f, float2 nf) {  // row += f i w
+        A[k] = __ffma2_rn(nf, wi, A[k]);
+        A[k + 1] = __ffma2_rn(f, wr, A[k + 1]);
+    };
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        add(2 * c, w0r[c], w0i[c], sg);
+        add(6 + 2 * c, w1r[c], w1i[c], sg);
+        if (MU == 0) {        // row2 = -sp i h1, row3 = -sp i h0
+            addi(12 + 2 * c, w1r[c], w1i[c], nq, q);
+            addi(18 + 2 * c, w0r[c], w0i[c], nq, q);
+        } else if (MU == 1) { // row2 = sp h1, row3 = -sp h0
+            add(12 + 2 * c, w1r[c], w1i[c], q);
+            add(18 + 2 * c, w0r[c], w0i[c], nq);
+        } else if (MU == 2) { // row2 = -sp i h0, row3 = sp i h1
+            addi(12 + 2 * c, w0r[c], w0i[c], nq, q);
+            addi(18 + 2 * c, w1r[c], w1i[c], q, nq);
+        } else {              // row2 = sp h0, row3 = sp h1
+            add(12 + 2 * c, w0r[c], w0i[c], q);
+            add(18 + 2 * c, w1r[c], w1i[c], q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 24; k++) { acc[0][k] = A[k].x; acc[1][k] = A[k].y; }
+}
+
+template <int PREC, int NF, bool PRO, int MU, bool FWD, bool PAIR = false, typename T>
 __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const DslashArgs<T> &a, int nb, T sg)
 {
     const T sp = FWD ? -a.sigma : a.sigma;
     const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;  // chunks per flavour
     using SC = typename Traits<PREC>::schunk;
     const SC *in = reinterpret_cast<const SC *>(a.in);
-    if (PRO) {
+    if constexpr (PAIR && NF == 2 && std::is_same<T, float>::value) {
+        float v[2][24];
+        if constexpr (PRO) {
+#pragma unroll
+            for (int f = 0; f < 2; f++)
+                load_spinor<PREC>(in + f * fstride, a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr, nb, a.Vh, v[f]);
+            apply_twist<T, NF>(a.tw_pro, v);
+            hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg, sg));
+        } else if constexpr (PREC == P16) {
+            const float n0 = load_spinor_f16_unscaled(in, a.in_norm, nb, a.Vh, v[0]);
+            const float n1 = load_spinor_f16_unscaled(in + fstride, a.in_norm + (size_t)a.Vh, nb, a.Vh, v[1]);
+            hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg * n0, sg * n1));
+        } else {
+            load_spinor<PREC>(in, nullptr, nb, a.Vh, v[0]);
+            load_spinor<PREC>(in + fstride, nullptr, nb, a.Vh, v[1]);
+            hop_pair<MU, FWD, false>(acc, U, v, sp, make_float2(sg, sg));
+        }
+    } else if (PRO) {
         T v[NF][24];
 #pragma unroll
         for (int f = 0; f < NF; f++)
@@ -187,7 +313,7 @@ __device__ __forceinline__ void local_op(const DslashArgs<T> &a, int cb, T v[NF]
     else apply_twist<T, NF>(a.tw_epi, v);
 }
 
-template <int PREC, int NF, int RECON, bool PRO, bool CLOV = false>
+template <int PREC, int NF, int RECON, bool PRO, bool CLOV = false, bool PAIR = false>
 __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs)
 {
     using T = typename Traits<PREC>::real;
@@ -233,30 +359,30 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
     {
         const int nf_ = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
         LinkLoader<PREC, RECON>::load(Gout + 0 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, NF, PRO, 0, true>(acc, U, a, nf_, one);
+        hop<PREC, NF, PRO, 0, true, PAIR>(acc, U, a, nf_, one);
         const int nb_ = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
         LinkLoader<PREC, RECON>::load(Gin + 0 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, NF, PRO, 0, false>(acc, U, a, nb_, one);
+        hop<PREC, NF, PRO, 0, false, PAIR>(acc, U, a, nb_, one);
     }
     // ---- y
     {
         const int s = a.X1h;
         const int nf_ = (y == a.Ly - 1) ? cb - (a.Ly - 1) * s : cb + s;
         LinkLoader<PREC, RECON>::load(Gout + 1 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, NF, PRO, 1, true>(acc, U, a, nf_, one);
+        hop<PREC, NF, PRO, 1, true, PAIR>(acc, U, a, nf_, one);
         const int nb_ = (y == 0) ? cb + (a.Ly - 1) * s : cb - s;
         LinkLoader<PREC, RECON>::load(Gin + 1 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, NF, PRO, 1, false>(acc, U, a, nb_, one);
+        hop<PREC, NF, PRO, 1, false, PAIR>(acc, U, a, nb_, one);
     }
     // ---- z
     {
         const int s = a.X1h * a.Ly;
         const int nf_ = (z == a.Lz - 1) ? cb - (a.Lz - 1) * s : cb + s;
         LinkLoader<PREC, RECON>::load(Gout + 2 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, NF, PRO, 2, true>(acc, U, a, nf_, one);
+        hop<PREC, NF, PRO, 2, true, PAIR>(acc, U, a, nf_, one);
         const int nb_ = (z == 0) ? cb + (a.Lz - 1) * s : cb - s;
         LinkLoader<PREC, RECON>::load(Gin + 2 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, NF, PRO, 2, false>(acc, U, a, nb_, one);
+        hop<PREC, NF, PRO, 2, false, PAIR>(acc, U, a, nb_, one);
     }
     // ---- t (antiperiodic wrap when tbc)
     {
@@ -264,10 +390,10 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
         const bool wf = (t == a.Lt - 1), wb = (t == 0);
         const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
         LinkLoader<PREC, RECON>::load(Gout + 3 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, NF, PRO, 3, true>(acc, U, a, nf_, (wf && a.tbc) ? -one : one);
+        hop<PREC, NF, PRO, 3, true, PAIR>(acc, U, a, nf_, (wf && a.tbc) ? -one : one);
         const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
         LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, NF, PRO, 3, false>(acc, U, a, nb_, (wb && a.tbc) ? -one : one);
+        hop<PREC, NF, PRO, 3, false, PAIR>(acc, U, a, nb_, (wb && a.tbc) ? -one : one);
     }
 
     // ---- fused local epilogue
@@ -424,14 +550,34 @@ __device__ __forceinline__ void decode_link_raw(const HopRaw<PREC, RECON, NF> &r
     LinkRegLoader<PREC, RECON>::load(tmp, U);
 }
 
-// PRO: twist every neighbour spinor with tw before the projection (the input prologue)
-template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, typename T>
+// PRO: twist every neighbour spinor with tw before the projection (the input prologue).
+// PAIR: the doublet in binary32 takes the flavour-paired hop (hop_pair).
+template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, bool PAIR = false, typename T>
 __device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC, RECON, NF> &r, T sp, T sg,
                                             const Twist<T> *tw = nullptr)
 {
     Link<T> U;
     decode_link_raw<PREC, RECON, NF>(r, U);
-    if constexpr (PRO) {
+    if constexpr (PAIR && NF == 2 && std::is_same<T, float>::value) {
+        float v[2][24];
+        spinor_from_chunks<PREC>(r.s[0], v[0]);
+        spinor_from_chunks<PREC>(r.s[1], v[1]);
+        if constexpr (PRO) {
+            if constexpr (PREC == P16) {
+#pragma unroll
+                for (int f = 0; f < 2; f++)
+#pragma unroll
+                    for (int k = 0; k < 24; k++) v[f][k] *= r.n[f];
+            }
+            apply_twist<T, NF>(*tw, v);
+            hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg, sg));
+        } else if constexpr (PREC == P16) {
+            // the site norms fold into the per-flavour scale
+            hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg * r.n[0], sg * r.n[1]));
+        } else {
+            hop_pair<MU, FWD, false>(acc, U, v, sp, make_float2(sg, sg));
+        }
+    } else if constexpr (PRO) {
         T v[NF][24];
 #pragma unroll
         for (int f = 0; f < NF; f++) {
@@ -600,7 +746,7 @@ __device__ __forceinline__ void async_fetch_hop(char *buf, int tid, const typena
     }
 }
 
-template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, typename T>
+template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, bool PAIR = false, typename T>
 __device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *buf, int tid, T sp, T sg,
                                                   const Twist<T> *tw = nullptr)
 {
@@ -621,7 +767,7 @@ __device__ __forceinline__ void async_compute_hop(T (&acc)[NF][24], const char *
 #pragma unroll
         for (int f = 0; f < NF; f++) r.n[f] = sn[f * H::BS + tid];
     }
-    compute_hop<PREC, RECON, NF, MU, FWD, PRO>(acc, r, sp, sg, tw);
+    compute_hop<PREC, RECON, NF, MU, FWD, PRO, PAIR>(acc, r, sp, sg, tw);
 }
 
 // the epilogue input x of this thread's site into the spinor / norm area of a buffer
@@ -687,7 +833,7 @@ __device__ __forceinline__ bool wait_flag(const int *f, int *err)
 // One site of the staged hop pipeline (launch forms 6 / 7 and the fused operator).  WAIT: the
 // input field is produced by other tiles of the same launch; before its first load the thread
 // waits for the completion flags of the 128-site tiles that hold its 8 neighbours.
-template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT>
+template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false>
 __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
                                            char *smem_async, const int *flags, int *err)
 {
@@ -755,14 +901,14 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         const char *b = smem_async + (h % NB) * H::BUF;
         const Twist<T> *tw = &a.tw_pro;
         switch (h) {
-        case 0: async_compute_hop<PREC, RECON, NF, 0, true, PRO>(acc, b, tid, spf, one, tw); break;
-        case 1: async_compute_hop<PREC, RECON, NF, 0, false, PRO>(acc, b, tid, spb, one, tw); break;
-        case 2: async_compute_hop<PREC, RECON, NF, 1, true, PRO>(acc, b, tid, spf, one, tw); break;
-        case 3: async_compute_hop<PREC, RECON, NF, 1, false, PRO>(acc, b, tid, spb, one, tw); break;
-        case 4: async_compute_hop<PREC, RECON, NF, 2, true, PRO>(acc, b, tid, spf, one, tw); break;
-        case 5: async_compute_hop<PREC, RECON, NF, 2, false, PRO>(acc, b, tid, spb, one, tw); break;
-        case 6: async_compute_hop<PREC, RECON, NF, 3, true, PRO>(acc, b, tid, spf, sgf, tw); break;
-        default: async_compute_hop<PREC, RECON, NF, 3, false, PRO>(acc, b, tid, spb, sgb, tw); break;
+        case 0: async_compute_hop<PREC, RECON, NF, 0, true, PRO, PAIR>(acc, b, tid, spf, one, tw); break;
+        case 1: async_compute_hop<PREC, RECON, NF, 0, false, PRO, PAIR>(acc, b, tid, spb, one, tw); break;
+        case 2: async_compute_hop<PREC, RECON, NF, 1, true, PRO, PAIR>(acc, b, tid, spf, one, tw); break;
+        case 3: async_compute_hop<PREC, RECON, NF, 1, false, PRO, PAIR>(acc, b, tid, spb, one, tw); break;
+        case 4: async_compute_hop<PREC, RECON, NF, 2, true, PRO, PAIR>(acc, b, tid, spf, one, tw); break;
+        case 5: async_compute_hop<PREC, RECON, NF, 2, false, PRO, PAIR>(acc, b, tid, spb, one, tw); break;
+        case 6: async_compute_hop<PREC, RECON, NF, 3, true, PRO, PAIR>(acc, b, tid, spf, sgf, tw); break;
+        default: async_compute_hop<PREC, RECON, NF, 3, false, PRO, PAIR>(acc, b, tid, spb, sgb, tw); break;
         }
         if (h + NB < 8) fetch(h + NB);
         else if (h + NB == 8) {
@@ -800,14 +946,14 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false>
 __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     extern __shared__ __align__(16) char smem_async[];
     const int tid = threadIdx.x;
     const int cb = blockIdx.x * AsyncHop<PREC, RECON, NF>::BS + tid;
     if (cb >= a.Vh) return;
-    async_site<PREC, NF, RECON, CLOV, NB, PRO, false>(a, cb, tid, smem_async, nullptr, nullptr);
+    async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR>(a, cb, tid, smem_async, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -832,6 +978,7 @@ __global__ void __launch_bounds__(128, MINB)
 {
     extern __shared__ __align__(16) char smem_async[];
     __shared__ int s_q;
+    constexpr bool FPAIR = NF == 2 && PREC == P32;  // the flavour-paired hop, as launch form 8
     int *err = sync, *counter = sync + 1, *flags = sync + 2;
     const int tid = threadIdx.x;
     for (;;) {
@@ -845,13 +992,13 @@ __global__ void __launch_bounds__(128, MINB)
         if (it & 1) {
             for (int sub = 0; sub < FUSED_GROUP; sub++) {
                 const int cb = (grp * FUSED_GROUP + sub) * 128 + tid;
-                if (cb < aB.Vh) async_site<PREC, NF, RECON, false, 2, false, true>(aB, cb, tid, smem_async, flags, err);
+                if (cb < aB.Vh) async_site<PREC, NF, RECON, false, 2, false, true, FPAIR>(aB, cb, tid, smem_async, flags, err);
             }
         } else {
             for (int sub = 0; sub < FUSED_GROUP; sub++) {
                 const int cb = (grp * FUSED_GROUP + sub) * 128 + tid;
                 if (cb < aA.Vh)
-                    async_site<PREC, NF, RECON, false, 2, false, false>(aA, cb, tid, smem_async, nullptr, nullptr);
+                    async_site<PREC, NF, RECON, false, 2, false, false, FPAIR>(aA, cb, tid, smem_async, nullptr, nullptr);
             }
             // the block's stores happen before one thread's gpu-scope release of the tiles
             __syncthreads();
@@ -866,7 +1013,7 @@ __global__ void __launch_bounds__(128, MINB)
 // The shared-memory opt-in is set once per kernel and device: the attribute call is not a
 // stream operation and can wait for work already queued on the device, so it must stay out of
 // the per-launch path (it would serialise copy streams with the compute stream).
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false>
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false>
 cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
 {
     constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
@@ -876,12 +1023,12 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO>,
+        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -936,12 +1083,13 @@ cudaError_t launch_fused_dispatch(const DslashArgs<typename Traits<PREC>::real> 
 // Clover handles: the same hopping sum with the per-site local operator L = C + X (or L^-1) in
 // the epilogue instead of the constant twist; no input prologue (the operators apply L^-1 to an
 // input as a pass of its own).  The epilogue reads 72 (L) or 144 (L^-1) more reals per site.
+// The binary32 doublet takes the flavour-paired hop (hop_pair) in both clover forms.
 template <int PREC, int NF, int RECON, int MINB = 1>
 __global__ void __launch_bounds__(128, MINB) k_dslash_clov(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= a.Vh) return;
-    dslash_body<PREC, NF, RECON, false, true>(a, cb, 0);
+    dslash_body<PREC, NF, RECON, false, true, true>(a, cb, 0);
 }
 
 template <int PREC>
@@ -953,7 +1101,7 @@ cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real
     if (minb != 1 && minb != 3 && minb != 4 && minb != 6) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((a.Vh + 127) / 128);
 #define TM_CL1(NF, R)                                                               \
-    if (minb == 6) return launch_async<PREC, NF, R, 3, true>(a, s);                 \
+    if (minb == 6) return launch_async<PREC, NF, R, 3, true, 2, false, true>(a, s); \
     if (minb == 1) k_dslash_clov<PREC, NF, R, 1><<<grid, 128, 0, s>>>(a);           \
     else if (minb == 3) k_dslash_clov<PREC, NF, R, 3><<<grid, 128, 0, s>>>(a);      \
     else k_dslash_clov<PREC, NF, R, 4><<<grid, 128, 0, s>>>(a);
@@ -968,6 +1116,17 @@ cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real
 #undef TM_CL
 #undef TM_CL1
     return cudaGetLastError();
+}
+
+// the staged forms: nb3 = three buffers (2 blocks per SM) instead of two (3 blocks per SM)
+template <int PREC, int NF, int RECON, bool PAIR>
+cudaError_t launch_staged(const DslashArgs<typename Traits<PREC>::real> &a, bool pro, bool nb3, cudaStream_t s)
+{
+    if (pro)
+        return nb3 ? launch_async<PREC, NF, RECON, 2, false, 3, true, PAIR>(a, s)
+                   : launch_async<PREC, NF, RECON, 3, false, 2, true, PAIR>(a, s);
+    return nb3 ? launch_async<PREC, NF, RECON, 2, false, 3, false, PAIR>(a, s)
+               : launch_async<PREC, NF, RECON, 3, false, 2, false, PAIR>(a, s);
 }
 
 // variant 0: one thread per site (both flavours); variant 2: the two-stage load pipeline (no
@@ -1000,23 +1159,23 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
 #undef TM_LB1
         return cudaGetLastError();
     }
-    if (variant == 6 || variant == 7) {
+    if (variant >= 6 && variant <= 9) {
         // shared-memory staged pipeline, 6: two buffers (hop h+1 in flight while hop h computes,
-        // registers for 3 blocks per SM), 7: three buffers (hops h+1 and h+2 in flight, 2 blocks)
-#define TM_AS(NF, R)                                                                                     \
-    if (pro) return variant == 6 ? launch_async<PREC, NF, R, 3, false, 2, true>(a, s)                  \
-                                 : launch_async<PREC, NF, R, 2, false, 3, true>(a, s);                 \
-    return variant == 6 ? launch_async<PREC, NF, R, 3>(a, s) : launch_async<PREC, NF, R, 2, false, 3>(a, s);
-#define TM_ASR(NF)                         \
-    switch (recon) {                       \
-    case 18: TM_AS(NF, 18)                 \
-    case 12: TM_AS(NF, 12)                 \
-    case 8: TM_AS(NF, 8)                   \
-    default: return cudaErrorInvalidValue; \
+        // registers for 3 blocks per SM), 7: three buffers (hops h+1 and h+2 in flight, 2 blocks);
+        // 8 / 9: 6 / 7 with the flavour-paired hop for the binary32 doublet (6 / 7 otherwise)
+        const bool nb3 = variant == 7 || variant == 9, pair = variant >= 8;
+        constexpr bool CANPAIR = PREC == P32 || PREC == P16;
+#define TM_ASR(NF, PAIR)                                                   \
+    switch (recon) {                                                       \
+    case 18: return launch_staged<PREC, NF, 18, PAIR>(a, pro, nb3, s);     \
+    case 12: return launch_staged<PREC, NF, 12, PAIR>(a, pro, nb3, s);     \
+    case 8: return launch_staged<PREC, NF, 8, PAIR>(a, pro, nb3, s);       \
+    default: return cudaErrorInvalidValue;                                 \
     }
-        if (nf == 1) { TM_ASR(1) } else { TM_ASR(2) }
+        if (nf == 1) { TM_ASR(1, false) }
+        else if (pair) { TM_ASR(2, CANPAIR) }
+        else { TM_ASR(2, false) }
 #undef TM_ASR
-#undef TM_AS
     }
     const int grid = (a.Vh + block - 1) / block;
     if (variant == 2 && !pro) {

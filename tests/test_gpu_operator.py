@@ -52,7 +52,8 @@ def setup(case, recon):
 
 def use_variant(tmq, g, variant, block=128):
     """Force the hopping-kernel launch choice (0 plain, 2 pipelined, 3/4/5 register-capped 128x4/64x8/256x2,
-    6/7 shared-memory staged pipeline with 2/3 buffers; prologue launches keep 0 for 2)."""
+    6/7 shared-memory staged pipeline with 2/3 buffers, 8/9 the same with the flavour-paired doublet hop;
+    prologue launches keep 0 for 2)."""
     pro_variant = variant if variant >= 3 else 0  # 2 has no prologue form
     tmq.tune_import(g, " ".join(f"{p}:0:{variant}:{block} {p}:1:{pro_variant}:{block}" for p in ("f64", "f32", "f16")))
 
@@ -86,7 +87,8 @@ def test_pack_unpack_roundtrip(case, prec, recon):
 @pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
-@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5], ids=["site", "pipe", "cap128x4", "cap64x8", "cap256x2"])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5, 6, 7, 8, 9],
+                         ids=["site", "pipe", "cap128x4", "cap64x8", "cap256x2", "async2", "async3", "pair2", "pair3"])
 def test_precond_op(case, prec, recon, pc, dagger, variant):
     tmq, p, po, U, g, psi, chi = setup(case, recon)
     use_variant(tmq, g, variant, block=64 if variant == 2 else 128)
@@ -116,7 +118,7 @@ def test_full_operator(case, prec, dagger):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
 @pytest.mark.parametrize("out_parity", [0, 1])
-@pytest.mark.parametrize("variant", [0, 2, 3, 6, 7], ids=["site", "pipe", "cap4", "async2", "async3"])
+@pytest.mark.parametrize("variant", [0, 2, 3, 6, 7, 8, 9], ids=["site", "pipe", "cap4", "async2", "async3", "pair2", "pair3"])
 def test_dslash_epilogues(case, prec, dagger, out_parity, variant):
     """Each fused epilogue of tm_dslash against the oracle's hopping term and twist."""
     tmq, p, po, U, g, psi, chi = setup(case, 12)
@@ -240,7 +242,7 @@ def test_autotune_roundtrip_and_parity():
                 "f32:m:3",       # right-hand sides per block not 2, 4 or 8
                 "f16:c:2",       # clover occupancy not 1, 3 or 4
                 "f16:p:1",       # no fused FP16 operator
-                "f32:0:9:128",   # no such variant
+                "f32:0:10:128",  # no such variant
                 "f99:0:3:128"):  # no such precision
         with pytest.raises(tmq.TMError):
             tmq.tune_import(g, bad)
