@@ -345,9 +345,9 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * or the staged pipeline).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
- * uses defaults (FP64 capped 128 x 4; FP32 and FP16 the shared-memory pipeline: the doublet
- * flavour-paired, two buffers in FP32 (8) and three in FP16 (9); one flavour three buffers (7),
- * except with 18-real links, capped; 4
+ * uses defaults (FP64 capped 128 x 4; FP32 and FP16 the shared-memory pipeline with the paired
+ * hop: two buffers for the FP32 doublet (8), three otherwise (9), except one flavour with
+ * 18-real links, capped; 4
  * right-hand sides per block; clover 1 block per SM for FP64, 3 for FP16 and the FP32 doublet,
  * 4 for FP32 one flavour).
  */
@@ -355,8 +355,9 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
 /* The tuned table as text, and back.  Single-RHS entries "f32:0:3:128" = precision:prologue:
  * variant:block (variant 0 plain, 2 pipelined in registers, 3 / 4 / 5 capped at 128 registers with
  * 128 / 64 / 256-thread blocks, 6 / 7 pipelined through shared memory with cp.async, two / three
- * buffers, 8 / 9 the same as 6 / 7 with the two flavours of an FP32 or FP16 doublet paired in
- * packed FMAs (as 6 / 7 otherwise); 2 has no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
+ * buffers, 8 / 9 the same as 6 / 7 with the hop in packed FMAs over register pairs: the two
+ * flavours of an FP32 or FP16 doublet, the two projected spin rows of one flavour (as 6 / 7 in
+ * FP64); 2 has no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline;
  * fused-operator entries "f32:p:1" = precision:p:1 when tm_precond_op runs as one fused launch

@@ -566,13 +566,13 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
     g->X1h = p->L[0] / 2;
     for (int i = 0; i < 4; i++) {
         // measured on GB300 at 32^3x64: the register cap (3) for FP64; for FP32 and FP16 the
-        // shared-memory staged pipeline: the doublet with its flavours paired (FP32 2 buffers, 8;
-        // FP16 3 buffers, 9), one flavour with 3 buffers (7) except with 18-real links, where
-        // the register cap stays ahead
+        // shared-memory staged pipeline with the paired hop: the doublet's flavours paired (FP32
+        // 2 buffers, 8; FP16 3 buffers, 9), one flavour's spin rows paired (3 buffers, 9) except
+        // with 18-real links, where the register cap stays ahead
         for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{3, 128};
         const bool nd = p->flavor == TM_NDEG_DOUBLET;
         if ((i == 1 || i == 2) && (nd || p->recon != 18))
-            for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{nd ? (i == 1 ? 8 : 9) : 7, 128};
+            for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(nd && i == 1) ? 8 : 9, 128};
         g->multi_rpb[i] = 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
@@ -864,7 +864,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             for (int vi = 0; vi < 9; vi++) {
                 const int variant = variants[vi];
                 if (pro && variant == 2) continue;  // the register pipeline has no prologue
-                if (variant >= 8 && (g->nf != 2 || pi == 0)) continue;  // paired forms: binary32 doublet only
+                if (variant >= 8 && pi == 0) continue;  // paired forms: binary32 only
                 for (int bi = 0; bi < 4 && st == TM_OK; bi++) {
                     if (variant >= 3 && blocks[bi] != 128) continue;  // capped forms fix their own block
                     g->tune[pi][pro] = tm_tune_entry{variant, blocks[bi]};

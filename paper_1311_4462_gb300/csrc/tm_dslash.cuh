@@ -256,6 +256,82 @@ __device__ __forceinline__ void hop_pair(float (&acc)[2][24], const Link<float> 
     for (int k = 0; k < 24; k++) { acc[0][k] = A[k].x; acc[1][k] = A[k].y; }
 }
 
+// ---- One flavour with its two projected spin rows paired (binary32; launch forms 8 / 9) ----
+// The rank-2 projection leaves two spin rows h0, h1 that multiply the same link, so colour c of
+// h0 and of h1 share a register pair and the link products are the packed FMAs of hop_pair.
+// The accumulator pairs rows (0, 1) and (2, 3); the hops whose lower rows take (h1, h0) in
+// swapped order (mu = x, y) accumulate those two rows with scalar FMAs instead of moving pairs.
+template <int MU, bool FWD, bool PACK>
+__device__ __forceinline__ void hop_rows(float (&acc)[24], const Link<float> &U, const float (&v)[24], float sp, float sg)
+{
+    const float2 s = make_float2(sp, sp), ns = make_float2(-sp, -sp);
+    const float2 ms = make_float2(-sp, sp), sm = make_float2(sp, -sp);  // per-row signs
+    auto V = [&](int ra, int rb, int k) { return make_float2(v[6 * ra + k], v[6 * rb + k]); };
+    float2 hr[3], hi[3];  // (h0, h1) of colour c: real and imaginary pairs
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int r = 2 * c, i = 2 * c + 1;
+        if (MU == 0) {        // h0 = p0 + sp i p3,  h1 = p1 + sp i p2
+            hr[c] = pfma<PACK>(ns, V(3, 2, i), V(0, 1, r)); hi[c] = pfma<PACK>(s, V(3, 2, r), V(0, 1, i));
+        } else if (MU == 1) { // h0 = p0 - sp p3,  h1 = p1 + sp p2
+            hr[c] = pfma<PACK>(ms, V(3, 2, r), V(0, 1, r)); hi[c] = pfma<PACK>(ms, V(3, 2, i), V(0, 1, i));
+        } else if (MU == 2) { // h0 = p0 + sp i p2,  h1 = p1 - sp i p3
+            hr[c] = pfma<PACK>(ms, V(2, 3, i), V(0, 1, r)); hi[c] = pfma<PACK>(sm, V(2, 3, r), V(0, 1, i));
+        } else {              // h0 = p0 + sp p2,  h1 = p1 + sp p3
+            hr[c] = pfma<PACK>(s, V(2, 3, r), V(0, 1, r)); hi[c] = pfma<PACK>(s, V(2, 3, i), V(0, 1, i));
+        }
+    }
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 g[3];  // -hi (forward) or -hr (backward)
+#pragma unroll
+    for (int c = 0; c < 3; c++) g[c] = __fmul2_rn(m1, FWD ? hi[c] : hr[c]);
+    float2 wr[3], wi[3];  // (w0, w1) = U (h0, h1) or U^dag (h0, h1)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const C<float> u = FWD ? U.u[a][b] : U.u[b][a];
+            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i);
+            if (b == 0) {
+                wr[a] = __fmul2_rn(ur, hr[b]);
+                wi[a] = __fmul2_rn(ur, hi[b]);
+            } else {
+                wr[a] = __ffma2_rn(ur, hr[b], wr[a]);
+                wi[a] = __ffma2_rn(ur, hi[b], wi[a]);
+            }
+            wr[a] = __ffma2_rn(ui, FWD ? g[b] : hi[b], wr[a]);
+            wi[a] = __ffma2_rn(ui, FWD ? hr[b] : g[b], wi[a]);
+        }
+    }
+    const float q = sg * sp;
+    const float2 sgp = make_float2(sg, sg);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int r = 2 * c;
+        // rows 0 and 1: += sg (w0, w1)
+        float2 a01r = make_float2(acc[r], acc[6 + r]), a01i = make_float2(acc[r + 1], acc[7 + r]);
+        a01r = __ffma2_rn(sgp, wr[c], a01r);
+        a01i = __ffma2_rn(sgp, wi[c], a01i);
+        acc[r] = a01r.x; acc[6 + r] = a01r.y; acc[r + 1] = a01i.x; acc[7 + r] = a01i.y;
+        if (MU == 0) {        // row2 = -sp i h1, row3 = -sp i h0:  re += q wi, im -= q wr
+            acc[12 + r] = fmaf(q, wi[c].y, acc[12 + r]); acc[13 + r] = fmaf(-q, wr[c].y, acc[13 + r]);
+            acc[18 + r] = fmaf(q, wi[c].x, acc[18 + r]); acc[19 + r] = fmaf(-q, wr[c].x, acc[19 + r]);
+        } else if (MU == 1) { // row2 = sp h1, row3 = -sp h0
+            acc[12 + r] = fmaf(q, wr[c].y, acc[12 + r]); acc[13 + r] = fmaf(q, wi[c].y, acc[13 + r]);
+            acc[18 + r] = fmaf(-q, wr[c].x, acc[18 + r]); acc[19 + r] = fmaf(-q, wi[c].x, acc[19 + r]);
+        } else {
+            // MU 2: (row2, row3) = i (-q, q) (w0, w1): re += (q, -q) wi, im += (-q, q) wr
+            // MU 3: (row2, row3) = q (w0, w1)
+            const float2 fr = MU == 2 ? make_float2(q, -q) : make_float2(q, q);
+            const float2 fi = MU == 2 ? make_float2(-q, q) : make_float2(q, q);
+            float2 a23r = make_float2(acc[12 + r], acc[18 + r]), a23i = make_float2(acc[13 + r], acc[19 + r]);
+            a23r = __ffma2_rn(fr, MU == 2 ? wi[c] : wr[c], a23r);
+            a23i = __ffma2_rn(fi, MU == 2 ? wr[c] : wi[c], a23i);
+            acc[12 + r] = a23r.x; acc[18 + r] = a23r.y; acc[13 + r] = a23i.x; acc[19 + r] = a23i.y;
+        }
+    }
+}
+
 template <int PREC, int NF, bool PRO, int MU, bool FWD, bool PAIR = false, typename T>
 __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const DslashArgs<T> &a, int nb, T sg)
 {
@@ -279,6 +355,19 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
             load_spinor<PREC>(in, nullptr, nb, a.Vh, v[0]);
             load_spinor<PREC>(in + fstride, nullptr, nb, a.Vh, v[1]);
             hop_pair<MU, FWD, false>(acc, U, v, sp, make_float2(sg, sg));
+        }
+    } else if constexpr (PAIR && NF == 1 && std::is_same<T, float>::value) {
+        float v[1][24];
+        if constexpr (PRO) {
+            load_spinor<PREC>(in, a.in_norm, nb, a.Vh, v[0]);
+            apply_twist<T, NF>(a.tw_pro, v);
+            hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg);
+        } else if constexpr (PREC == P16) {
+            const float n = load_spinor_f16_unscaled(in, a.in_norm, nb, a.Vh, v[0]);
+            hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg * n);
+        } else {
+            load_spinor<PREC>(in, nullptr, nb, a.Vh, v[0]);
+            hop_rows<MU, FWD, false>(acc[0], U, v[0], sp, sg);
         }
     } else if (PRO) {
         T v[NF][24];
@@ -551,7 +640,7 @@ __device__ __forceinline__ void decode_link_raw(const HopRaw<PREC, RECON, NF> &r
 }
 
 // PRO: twist every neighbour spinor with tw before the projection (the input prologue).
-// PAIR: the doublet in binary32 takes the flavour-paired hop (hop_pair).
+// PAIR: binary32 takes the paired hop (hop_pair for the doublet, hop_rows for one flavour).
 template <int PREC, int RECON, int NF, int MU, bool FWD, bool PRO = false, bool PAIR = false, typename T>
 __device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC, RECON, NF> &r, T sp, T sg,
                                             const Twist<T> *tw = nullptr)
@@ -576,6 +665,21 @@ __device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC,
             hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg * r.n[0], sg * r.n[1]));
         } else {
             hop_pair<MU, FWD, false>(acc, U, v, sp, make_float2(sg, sg));
+        }
+    } else if constexpr (PAIR && NF == 1 && std::is_same<T, float>::value) {
+        float v[1][24];
+        spinor_from_chunks<PREC>(r.s[0], v[0]);
+        if constexpr (PRO) {
+            if constexpr (PREC == P16) {
+#pragma unroll
+                for (int k = 0; k < 24; k++) v[0][k] *= r.n[0];
+            }
+            apply_twist<T, NF>(*tw, v);
+            hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg);
+        } else if constexpr (PREC == P16) {
+            hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg * r.n[0]);
+        } else {
+            hop_rows<MU, FWD, false>(acc[0], U, v[0], sp, sg);
         }
     } else if constexpr (PRO) {
         T v[NF][24];
@@ -978,7 +1082,8 @@ __global__ void __launch_bounds__(128, MINB)
 {
     extern __shared__ __align__(16) char smem_async[];
     __shared__ int s_q;
-    constexpr bool FPAIR = NF == 2 && PREC == P32;  // the flavour-paired hop, as launch form 8
+    // the hop of the default launch form: paired (8 / 9) except one flavour with 18-real links
+    constexpr bool FPAIR = PREC == P32 && (NF == 2 || RECON != 18);
     int *err = sync, *counter = sync + 1, *flags = sync + 2;
     const int tid = threadIdx.x;
     for (;;) {
@@ -1089,7 +1194,7 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_clov(const __grid_constant
 {
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= a.Vh) return;
-    dslash_body<PREC, NF, RECON, false, true, true>(a, cb, 0);
+    dslash_body<PREC, NF, RECON, false, true, NF == 2>(a, cb, 0);
 }
 
 template <int PREC>
@@ -1101,7 +1206,7 @@ cudaError_t launch_dslash_clov_impl(const DslashArgs<typename Traits<PREC>::real
     if (minb != 1 && minb != 3 && minb != 4 && minb != 6) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((a.Vh + 127) / 128);
 #define TM_CL1(NF, R)                                                               \
-    if (minb == 6) return launch_async<PREC, NF, R, 3, true, 2, false, true>(a, s); \
+    if (minb == 6) return launch_async<PREC, NF, R, 3, true, 2, false, NF == 2>(a, s); \
     if (minb == 1) k_dslash_clov<PREC, NF, R, 1><<<grid, 128, 0, s>>>(a);           \
     else if (minb == 3) k_dslash_clov<PREC, NF, R, 3><<<grid, 128, 0, s>>>(a);      \
     else k_dslash_clov<PREC, NF, R, 4><<<grid, 128, 0, s>>>(a);
@@ -1162,7 +1267,8 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
     if (variant >= 6 && variant <= 9) {
         // shared-memory staged pipeline, 6: two buffers (hop h+1 in flight while hop h computes,
         // registers for 3 blocks per SM), 7: three buffers (hops h+1 and h+2 in flight, 2 blocks);
-        // 8 / 9: 6 / 7 with the flavour-paired hop for the binary32 doublet (6 / 7 otherwise)
+        // 8 / 9: 6 / 7 with the paired hop in binary32 (flavours paired for the doublet, spin
+        // rows for one flavour; 6 / 7 in binary64)
         const bool nb3 = variant == 7 || variant == 9, pair = variant >= 8;
         constexpr bool CANPAIR = PREC == P32 || PREC == P16;
 #define TM_ASR(NF, PAIR)                                                   \
@@ -1172,9 +1278,11 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
     case 8: return launch_staged<PREC, NF, 8, PAIR>(a, pro, nb3, s);       \
     default: return cudaErrorInvalidValue;                                 \
     }
-        if (nf == 1) { TM_ASR(1, false) }
-        else if (pair) { TM_ASR(2, CANPAIR) }
-        else { TM_ASR(2, false) }
+        if (nf == 1) {
+            if (pair) { TM_ASR(1, CANPAIR) } else { TM_ASR(1, false) }
+        } else {
+            if (pair) { TM_ASR(2, CANPAIR) } else { TM_ASR(2, false) }
+        }
 #undef TM_ASR
     }
     const int grid = (a.Vh + block - 1) / block;
