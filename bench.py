@@ -7,8 +7,9 @@ to a 32^3 x 64 non-degenerate doublet field (kappa = 0.1612, mu-bar = 0.135,
 eps-bar = 0.15, antiperiodic time), FP32 storage and arithmetic, 12-real links.  The
 step is the two fused launches tm_precond_op makes (tm_dslash with TM_EPI_TWINV, then
 TM_EPI_TWXPAY_ASYM), issued through the C ABI with CUDA events between them on the
-launching stream.  Flop convention: 1320 per hopping site and flavour, twist and xpay
-as counted in the design doc -> 5808 flops per even site for the doublet (2808 one flavour).
+launching stream.  Flop convention: 1320 per hopping site and flavour; the twist R 48
+and R^-1 72 per site and flavour (doublet: 192 and 240 per site), xpay 48 per flavour
+-> 5808 flops per even site for the doublet (2808 one flavour).
 
 Printed: one JSON line (rank 0).  Extra keys: per-precision / per-operator table,
 CG time-to-solution, roofline of the dominant kernel, oracle CPU baseline, clocks.
@@ -30,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 L_FULL = (32, 32, 32, 64)
 KAPPA, MU_ND, EPS_ND, MU_DEG = 0.1612, 0.135, 0.15, 0.004
-FLOPS_PER_SITE = {1: 2808, 2: 5808}          # M_asym per even site (flop convention)
+FLOPS_PER_SITE = {1: 2808, 2: 5808}          # M_asym per even site (flop convention above)
 FLOPS_SYM = {1: 2832, 2: 5856}               # M_sym per even site
 SPINOR_BYTES = {8: 192, 16: 192, 4: 96, 2: 52}  # per site and flavour; FP16 includes the 4-byte norm
 REAL_BYTES = {8: 8, 16: 8, 4: 4, 2: 2}          # storage bytes per real (16 = DF64, a float pair)
@@ -41,7 +42,8 @@ def link_reals(prec, recon):
 
 
 def asym_bytes(prec, nf, recon):
-    """Algorithmic bytes per even site of M_asym: 16 links + 5 spinor passes."""
+    """Algorithmic bytes per even site of M_asym: 16 links + 5 spinor passes (each launch reads 8 links
+    and the input spinor and writes one; the second also reads x)."""
     return 16 * link_reals(prec, recon) * REAL_BYTES[prec] + 5 * SPINOR_BYTES[prec] * nf
 
 
