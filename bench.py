@@ -176,6 +176,8 @@ def launch_form(table, prec, csw=0.0):
     for e in table.split():
         f = e.split(":")
         if csw and f[0] == prec and f[1] == "c":
+            if f[2] == "6":
+                return "clover, shared-memory staged pipeline (3 blocks per SM)"
             return "clover, %s blocks per SM" % f[2]
         if not csw and f[0] == prec and f[1] == "0":
             return "%s (variant %s)" % (FORMS.get(int(f[2]), "?"), f[2])
