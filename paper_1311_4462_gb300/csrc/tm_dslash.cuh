@@ -165,8 +165,8 @@ __device__ __forceinline__ void hop_one(T *acc, const Link<T> &U, const T *v, T 
 // too.  Multiplication by i only renames the real and imaginary pairs.  The sign of the
 // complex products comes from the negated real or imaginary pair of each projected colour (six
 // packed multiplies per hop), and the per-flavour scale (boundary sign times the FP16 site norm)
-// is a pair as well.  Every operation rounds as a binary32 FMA, as in hop_one; the order of the
-// link products differs, so results agree with hop_one to rounding.
+// is a pair as well.  Per value these are the binary32 operations of hop_one in the same order
+// (its link product is the same FMA chain), so the results are bit-identical to hop_one's.
 // PACK: pack the projection as well (inputs that come out of conversions or arithmetic land in
 // register pairs for free; 16-byte binary32 loads give four registers of one flavour, which
 // scalar FMAs pair up without moves).
