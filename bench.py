@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 L_FULL = (32, 32, 32, 64)
 KAPPA, MU_ND, EPS_ND, MU_DEG = 0.1612, 0.135, 0.15, 0.004
 FLOPS_PER_SITE = {1: 2808, 2: 5808}          # M_asym per even site (flop convention above)
+FLOPS_WILSON = 2 * 1320 + 48                 # M_asym at mu = eps = 0 (R = 1): two hops and the xpay
 FLOPS_SYM = {1: 2832, 2: 5856}               # M_sym per even site
 SPINOR_BYTES = {8: 192, 16: 192, 4: 96, 2: 52}  # per site and flavour; FP16 includes the 4-byte norm
 REAL_BYTES = {8: 8, 16: 8, 4: 4, 2: 2}          # storage bytes per real (16 = DF64, a float pair)
@@ -254,6 +255,8 @@ def run_ours(args, rank, world):
     if args.csw:  # launch A reads the four clover blocks of L^-1, launch B the two of L
         la, lb = la + CLOVER_BYTES[prec] * 2 // 3, lb + CLOVER_BYTES[prec] // 3
     avg_launch_ms = (sum(ta) + sum(tb)) / (2 * K)
+    steps_ms = sorted(a + b for a, b in zip(ta, tb))
+    pct = lambda q: round(steps_ms[min(len(steps_ms) - 1, int(q * (len(steps_ms) - 1) + 0.5))], 5)
     achieved = ((la + lb) / 2 * Vh) / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_src = load_peaks()
     traffic = read_traffic("k_dslash%s_%s_%s_r%d_%s" % ("_clov" if args.csw else "", args.prec,
@@ -274,6 +277,8 @@ def run_ours(args, rank, world):
                      "bytes_per_launch_algorithmic": (la + lb) / 2 * Vh,
                      "launch_ms": {"twinv": round(statistics.mean(ta), 5), "twxpay": round(statistics.mean(tb), 5)}},
         "clocks": clocks,
+        "step_ms_percentiles": {"p10": pct(0.1), "p50": pct(0.5), "p90": pct(0.9),
+                                "source": "CUDA events around each step's two launches"},
         "launch_table": tune_table,
     }
     if rank == 0 and not args.quick and (args.prec, nf, recon, L, args.csw) != ("f32", 2, 12, (32, 32, 32, 64), 0.0):
@@ -281,6 +286,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.quick:
         result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
         result["per_precision"] = per_precision(tmq, U, psi, dev, args)
+        result["l2_resident_16x16x16x32"] = l2_resident_section(tmq, dev, args)
         result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
@@ -471,6 +477,32 @@ def per_precision(tmq, U, psi, dev, args):
     return rows
 
 
+def l2_resident_section(tmq, dev, args):
+    """M_asym of the 16^3x32 one-flavour lattice (kappa 0.1612, mu 0.004, recon 12) in FP64, FP32 and
+    FP16.  Its links (25 MB in FP32) and spinors fit in the 129 MB L2, so the times are reported with
+    that label and no HBM fraction; consecutive applications without a flush."""
+    import torch
+    from paper_1311_4462_gb300 import inputs
+    L = (16, 16, 16, 32)
+    p = tmq.Params(L, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=12)
+    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L, 1001)).to(dev))
+    tmq.autotune(g)
+    src = torch.from_numpy(inputs.spinor_field(L, 1, 2001)).to(dev)
+    rows = []
+    for prec in (tmq.TM_PREC_F64, tmq.TM_PREC_F32, tmq.TM_PREC_F16):
+        xe = tmq.pack(g, src, 0, prec)
+        out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+        ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, 0, False), 50)
+        by = asym_bytes(prec, 1, 12) * p.Vh
+        rows.append({"op": "M_asym", "prec": {8: "f64", 4: "f32", 2: "f16"}[prec], "us": round(ms * 1e3, 2),
+                     "gflops": round(FLOPS_PER_SITE[1] * p.Vh / (ms * 1e-3) / 1e9, 1),
+                     "algorithmic_gbs": round(by / (ms * 1e-3) / 1e9, 1), "memory": "L2-resident"})
+        del xe, out, tmp
+    g.close()
+    return {"lattice": list(L), "flavours": 1, "recon": 12, "rows": rows,
+            "note": "working set inside L2 (no HBM roofline); median of 50 back-to-back applications"}
+
+
 # Table 1 of the paper (single GTX Titan, 32^3x64, asymmetric operator, GFLOPS) for context
 PAPER_TABLE1 = {("double", 12): (184, 190, 163), ("double", 8): (179, 183, 115), ("single", 12): (401, 415, 516),
                 ("single", 8): (472, 487, 567), ("half", 12): (732, 759, 879), ("half", 8): (829, 858, 624)}
@@ -498,9 +530,13 @@ def table1_section(tmq, U, psi, dev, args):
                 xe = tmq.pack(g, src, 0, prec)
                 out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
                 ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, 0, False), 3 if prec == 8 else 10, flush)
-                row[name] = round(FLOPS_PER_SITE[nf] * p.Vh / (ms * 1e-3) / 1e9, 1)
+                # the Wilson operator counts no twist work (the kernel still multiplies by R = 1)
+                fl = FLOPS_WILSON if name == "wilson" else FLOPS_PER_SITE[nf]
+                row[name] = round(fl * p.Vh / (ms * 1e-3) / 1e9, 1)
                 del xe, out, tmp
             row["paper_kepler_wilson_deg_nd"] = PAPER_TABLE1[(pname, recon)]
+            row["flops_per_even_site"] = {"wilson": FLOPS_WILSON, "deg_tm": FLOPS_PER_SITE[1],
+                                          "nd_tm": FLOPS_PER_SITE[2]}
             rows.append(row)
         for p, g, nf in handles.values():
             g.close()

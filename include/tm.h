@@ -318,6 +318,16 @@ tm_status tm_g5dot(const tm_gauge *g, const tm_field *a, const tm_field *b, doub
 tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stream);
 tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, void *stream);
 
+/*
+ * out = a x + b y on one parity field (y = NULL: out = a x), every right-hand side, the solvers'
+ * site-wise linear combination (sec. 2.2, the BLAS of CG) offered for callers that combine
+ * solutions, e.g. the gradient 2 X of the pseudofermion action.  out, x, y share a precision
+ * and nrhs; out may alias x or y.  Arithmetic in FP64 for FP64 fields, double-float for DF64,
+ * FP32 otherwise.  Asynchronous on `stream`.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_axpby(const tm_gauge *g, const tm_field *out, double a, const tm_field *x, double b, const tm_field *y,
+                   void *stream);
+
 /* ------------------------------------------------------------------------ differentiation */
 /*
  * Link gradient of L(U) = Re <g, M(U) psi> for every link, in the convention
@@ -368,13 +378,27 @@ tm_status tm_tune_import(tm_gauge *g, const char *text);
 
 /*
  * Status of the handle's bounded device-side waits.  The fused form of tm_precond_op (tune entry
- * "<prec>:p:1": both passes of M_pc in one persistent launch whose second-pass tiles wait, with a
- * time limit, for the first-pass tiles they read) records a wait that gave up in a device word
- * instead of hanging; the affected sites are left unwritten.  This call synchronises `stream`,
- * returns TM_ERR_TIMEOUT (and clears the word) if any wait gave up since the last call, TM_OK
- * otherwise.
+ * "<prec>:p:1": both passes of M_pc in one persistent launch whose second-pass tiles wait for the
+ * first-pass tiles they read) bounds every wait in time: a wait that has not seen its flag after
+ * the handle's limit (1 s by default, measured on the device's nanosecond clock) records the
+ * failure in a device word instead of hanging, and every later wait of the same launch on an
+ * unset flag gives up at once; the affected sites are left unwritten.  This call synchronises
+ * `stream`, returns TM_ERR_TIMEOUT (and clears the word) if any wait gave up since the last call,
+ * TM_OK otherwise.  tm_solve makes the same check before it returns.
  */
 tm_status tm_device_status(const tm_gauge *g, void *stream);
+
+/*
+ * Replace the fused operator's work list of a handle (for tests of the bounded waits and for
+ * experiments with the claim order): items as returned by tm_fused_work_list, 1 <= nitems <= the
+ * length of the handle's own list, every entry naming a group of the lattice ((entry >> 1) below
+ * the number of 512-site groups).  Nothing else is checked: a list that leaves out first-pass
+ * work makes the second-pass waits on it give up after wait_limit_ns (1 ms ... 60 s) with
+ * TM_ERR_TIMEOUT reported by tm_device_status, never a hang.  items = NULL restores the handle's
+ * own list.  Synchronises `stream`.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_fused_set_work_list(tm_gauge *g, const int *items, int nitems, unsigned long long wait_limit_ns,
+                                 void *stream);
 
 /*
  * The fused operator's work list for a lattice (host only, no GPU; for inspection and tests):
@@ -397,7 +421,9 @@ int tm_fused_work_list(const int L[4], int num_sms, int *items, int capacity);
  * The reduction's scratch (256 x 64 partial sums and a completion ticket, about 128 KB) is one
  * static device array per loaded copy of the library, kept on every GPU that uses it until the
  * process exits.  The first call on a device (with that device current) looks up the array's
- * device address and caches it; make that first call before any stream capture.  Every call
+ * device address and caches it; make that first call before any stream capture.  The cached
+ * address belongs to the device's primary context: do not reset the device (cudaDeviceReset)
+ * between calls while the library stays loaded.  Every call
  * shares the array: calls that overlap on the GPU (different streams, or different host threads
  * without ordering) race and give wrong results; calls ordered on one stream are safe.
  * Errors: TM_ERR_ARG (null pointers, nrhs > 64, nf not 1 or 2, bad Vh), TM_ERR_CUDA.

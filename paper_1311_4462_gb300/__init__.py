@@ -228,6 +228,13 @@ def dot(gauge, a: Field, b: Field, stream=None) -> float:
     return out.value
 
 
+def axpby(gauge, out: Field, a: float, x: Field, b: float = 0.0, y: Field = None, stream=None) -> Field:
+    """tm_axpby: out = a x + b y (y None: out = a x) on one parity field."""
+    L.check(L.load().tm_axpby(gauge.h, out.ref(), float(a), x.ref(), float(b), y.ref() if y is not None else None,
+                              _stream(stream)))
+    return out
+
+
 # reliable-update thresholds: the sloppy residual may fall by this factor between FP64 updates
 # (FP16 storage keeps about 3 digits, FP32 about 7).  Chosen from a sweep on the 32^3x64
 # doublet to 1e-10: FP32 1e-5 needs 2 updates (141 ms) where 1e-3 needs 4 (184 ms) at the same

@@ -72,6 +72,7 @@ _SIGS = {
                  vp],
     "tm_norm2": [vp, FP, ctypes.POINTER(ctypes.c_double), vp],
     "tm_dot": [vp, FP, FP, ctypes.POINTER(ctypes.c_double), vp],
+    "tm_axpby": [vp, FP, ctypes.c_double, FP, ctypes.c_double, FP, vp],
     "tm_force": [vp, vp, ctypes.c_int, FP, FP, FP, FP, ctypes.c_double, ctypes.c_int, vp],
     "tm_norm2_noalloc": [FP, ctypes.c_int, ctypes.c_int, vp, vp],
     "tm_autotune": [vp, vp],
@@ -88,6 +89,7 @@ _SIGS = {
     "tm_local_op": [vp, FP, FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
     "tm_device_status": [vp, vp],
     "tm_fused_work_list": [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
+    "tm_fused_set_work_list": [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_ulonglong, vp],
 }
 
 

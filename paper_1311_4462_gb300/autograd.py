@@ -3,19 +3,53 @@
 TMApply:            y = M(U) psi (eq. 2.1, full lattice).  backward: grad_psi = M^dag g (tm_mat with
                     dagger), grad_U = the su(3)-projected link gradient (tm_force, coef 1).
 PseudofermionAction: S = phi^dag (M^dag M)^-1 phi.  X = M^-1 M^-dag phi from two even-odd solves
-                    (M^dag z = phi, then M X = z, so Y = M X = z); backward: grad_U from tm_force with
-                    psi = X, g = Y, coef = -2; grad_phi = 2 X.
+                    (M^dag Y = phi, then M X = Y, so Y = M X); S = Re<phi, X> from tm_dot on the two
+                    parities; backward: grad_U from tm_force with psi = X, g = Y and coef = -2 dS;
+                    grad_phi = 2 dS X from tm_axpby.
 
 Canonical complex128 tensors run in FP64, complex64 in FP32 (the solves inside the action always run
 in FP64 CG or mixed CG with an FP64 result).  Gradients follow torch's convention for complex
-tensors (the conjugate Wirtinger derivative times two, so dL = Re sum conj(grad) dz).
+tensors (the conjugate Wirtinger derivative times two, so dL = Re sum conj(grad) dz).  Every step
+on field values is a library call; this module only packs, unpacks and sequences them.
+
+Gauge handles are reused while U is unchanged: a handle is kept per parameter set together with a
+weak reference to its U and U's version counter, so repeated calls with the same (unmodified) U pack
+the links once.  A handle dropped from the cache stays alive while an autograd graph still holds it.
 """
 from __future__ import annotations
 
+import weakref
+
 import torch
 
-from . import (TM_PC_ASYM, TM_PREC_F32, TM_PREC_F64, Field, Gauge, Params, force, mat, pack, prepare_rhs,
-               reconstruct_odd, solve, unpack)
+from . import (TM_PC_ASYM, TM_PREC_F32, TM_PREC_F64, Field, Gauge, Params, axpby, dot, force, mat, pack,
+               prepare_rhs, reconstruct_odd, solve, unpack)
+
+_CACHE: dict = {}   # params key -> (weakref to U, U._version, Gauge)
+_CACHE_MAX = 2
+
+
+def _key(params: Params, U):
+    return (params.L, params.kappa, params.mu, params.eps, params.flavor, params.t_antiperiodic, params.recon,
+            U.device.index)
+
+
+def gauge_for(U, params: Params) -> Gauge:
+    """The cached handle of (U, params), created when U is new or was modified in place."""
+    k = _key(params, U)
+    hit = _CACHE.get(k)
+    if hit is not None and hit[0]() is U and hit[1] == U._version:
+        return hit[2]
+    g = Gauge(params, U.detach())
+    _CACHE.pop(k, None)
+    while len(_CACHE) >= _CACHE_MAX:
+        _CACHE.pop(next(iter(_CACHE)))
+    _CACHE[k] = (weakref.ref(U), U._version, g)
+    return g
+
+
+def clear_cache():
+    _CACHE.clear()
 
 
 def _prec(t):
@@ -37,10 +71,10 @@ class TMApply(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, U, psi, params: Params):
-        g = Gauge(params, U.detach())
+        g = gauge_for(U, params)
         y = _apply_full(g, psi.detach(), False, _prec(psi))
         ctx.save_for_backward(psi)
-        ctx.g = g
+        ctx.g, ctx.U_dtype = g, U.dtype
         return y
 
     @staticmethod
@@ -54,15 +88,16 @@ class TMApply(torch.autograd.Function):
         if ctx.needs_input_grad[0]:
             pe, po = pack(g, psi.detach(), 0, prec), pack(g, psi.detach(), 1, prec)
             ge, go = pack(g, gy, 0, prec), pack(g, gy, 1, prec)
-            grad_U = force(g, pe, po, ge, go, coef=1.0, project=True)
+            out = torch.empty(g.params.gauge_shape, dtype=ctx.U_dtype, device=psi.device)
+            grad_U = force(g, pe, po, ge, go, coef=1.0, project=True, out=out)
         ctx.g = None
-        g.close()
         return grad_U, grad_psi, None
 
 
-def solve_full(g: Gauge, b, dagger=False, tol=1e-12, solver="cg", sloppy_prec=TM_PREC_F32, maxiter=50000):
-    """psi with M psi = b (or M^dag psi = b): asymmetric even-odd solve + odd reconstruction, FP64 result."""
-    be, bo = pack(g, b, 0, TM_PREC_F64), pack(g, b, 1, TM_PREC_F64)
+def solve_fields(g: Gauge, be: Field, bo: Field, dagger=False, tol=1e-12, solver="cg", sloppy_prec=TM_PREC_F32,
+                 maxiter=50000):
+    """(psi_e, psi_o) with M psi = b (or M^dag psi = b) for FP64 parity fields b: the asymmetric
+    even-odd solve (eq. 2.2) and the odd reconstruction (eq. 2.4)."""
     bp = Field(g, TM_PREC_F64)
     prepare_rhs(g, bp, be, bo, TM_PC_ASYM, dagger)
     xe = Field(g, TM_PREC_F64)
@@ -70,6 +105,13 @@ def solve_full(g: Gauge, b, dagger=False, tol=1e-12, solver="cg", sloppy_prec=TM
                   maxiter=maxiter)
     xo = Field(g, TM_PREC_F64)
     reconstruct_odd(g, xo, bo, xe, dagger)
+    return xe, xo, stats
+
+
+def solve_full(g: Gauge, b, dagger=False, tol=1e-12, solver="cg", sloppy_prec=TM_PREC_F32, maxiter=50000):
+    """psi with M psi = b (or M^dag psi = b) for a canonical b: solve_fields, FP64 canonical result."""
+    be, bo = pack(g, b, 0, TM_PREC_F64), pack(g, b, 1, TM_PREC_F64)
+    xe, xo, stats = solve_fields(g, be, bo, dagger, tol, solver, sloppy_prec, maxiter)
     out = torch.zeros(b.shape, dtype=torch.complex128, device=b.device)
     unpack(g, xe, 0, canon=out)
     unpack(g, xo, 1, canon=out)
@@ -81,26 +123,31 @@ class PseudofermionAction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, U, phi, params: Params, tol=1e-12, solver="cg"):
-        g = Gauge(params, U.detach())
+        g = gauge_for(U, params)
         phi64 = phi.detach().to(torch.complex128)
-        z, _ = solve_full(g, phi64, dagger=True, tol=tol, solver=solver)  # z = M^-dag phi = Y
-        X, _ = solve_full(g, z, dagger=False, tol=tol, solver=solver)    # X = M^-1 z
-        S = torch.vdot(phi64.reshape(-1), X.reshape(-1)).real
-        ctx.save_for_backward(X, z)
+        pe, po = pack(g, phi64, 0, TM_PREC_F64), pack(g, phi64, 1, TM_PREC_F64)
+        ye, yo, _ = solve_fields(g, pe, po, dagger=True, tol=tol, solver=solver)  # Y = M^-dag phi
+        xe, xo, _ = solve_fields(g, ye, yo, dagger=False, tol=tol, solver=solver)  # X = M^-1 Y
+        S = dot(g, pe, xe) + dot(g, po, xo)  # Re<phi, X>, FP64 reductions on the device
+        ctx.fields = (xe, xo, ye, yo)
         ctx.g, ctx.phi_dtype, ctx.U_dtype = g, phi.dtype, U.dtype
-        return S.to(torch.float64)
+        return torch.tensor(S, dtype=torch.float64, device=phi.device)
 
     @staticmethod
     def backward(ctx, gS):
-        X, Y = ctx.saved_tensors
+        xe, xo, ye, yo = ctx.fields
         g = ctx.g
+        dS = float(gS)
         grad_U = grad_phi = None
         if ctx.needs_input_grad[0]:
-            xe, xo = pack(g, X, 0, TM_PREC_F64), pack(g, X, 1, TM_PREC_F64)
-            ye, yo = pack(g, Y, 0, TM_PREC_F64), pack(g, Y, 1, TM_PREC_F64)
-            grad_U = (force(g, xe, xo, ye, yo, coef=-2.0, project=True) * gS).to(ctx.U_dtype)
+            out = torch.empty(g.params.gauge_shape, dtype=ctx.U_dtype, device=xe.data.device)
+            grad_U = force(g, xe, xo, ye, yo, coef=-2.0 * dS, project=True, out=out)
         if ctx.needs_input_grad[1]:
-            grad_phi = (2.0 * X * gS).to(ctx.phi_dtype)
-        ctx.g = None
-        g.close()
+            ge, go = Field(g, TM_PREC_F64), Field(g, TM_PREC_F64)
+            axpby(g, ge, 2.0 * dS, xe)
+            axpby(g, go, 2.0 * dS, xo)
+            grad_phi = torch.zeros(g.params.spinor_shape, dtype=ctx.phi_dtype, device=xe.data.device)
+            unpack(g, ge, 0, canon=grad_phi)
+            unpack(g, go, 1, canon=grad_phi)
+        ctx.g = ctx.fields = None
         return grad_U, grad_phi, None, None, None

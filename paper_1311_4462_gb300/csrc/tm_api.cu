@@ -60,9 +60,11 @@ cudaError_t launch_twist_active(const tm_gauge *g, const tm_field *out, const tm
                                 const int *act, int nact, cudaStream_t s);
 cudaError_t launch_dslash_clov_p64(const DslashArgs<double> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_fused_p64(const DslashArgs<double> &aA, const DslashArgs<double> &aB, int nf, int recon,
-                             const int *items, int nitems, int *sync, int num_sms, cudaStream_t s);
+                             const int *items, int nitems, int *sync, unsigned long long limit_ns, int num_sms,
+                             cudaStream_t s);
 cudaError_t launch_fused_p32(const DslashArgs<float> &aA, const DslashArgs<float> &aB, int nf, int recon,
-                             const int *items, int nitems, int *sync, int num_sms, cudaStream_t s);
+                             const int *items, int nitems, int *sync, unsigned long long limit_ns, int num_sms,
+                             cudaStream_t s);
 cudaError_t launch_dslash_clov_p32(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon, int minb, cudaStream_t s);
 cudaError_t launch_clover_apply(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, bool inverse,
@@ -437,21 +439,25 @@ static std::vector<int> fused_items(const int L[4], int num_sms)
     return items;
 }
 
+// flags per 128-site tile of the fused operator, rounded up to whole groups
+static size_t fused_nflags(long Vh) { return (size_t)((Vh + 128L * FUSED_GROUP - 1) / (128L * FUSED_GROUP)) * FUSED_GROUP; }
+
 tm_status build_fused_work(tm_gauge *g, cudaStream_t s)
 {
     const std::vector<int> items = fused_items(g->p.L, g->num_sms);
     g->fused_nitems = (int)items.size();
-    // flags per 128-site tile, rounded up to whole groups
-    const size_t nflags = (size_t)((g->Vh + 128L * FUSED_GROUP - 1) / (128L * FUSED_GROUP)) * FUSED_GROUP;
+    g->fused_capacity = (int)items.size();
+    g->wait_limit_ns = 1000000000ull;  // one second per bounded wait
+    const size_t nflags = fused_nflags(g->Vh);
     if (cudaMalloc((void **)&g->fused_items, sizeof(int) * items.size()) != cudaSuccess ||
-        cudaMalloc((void **)&g->fused_sync, sizeof(int) * (2 + nflags)) != cudaSuccess) {
+        cudaMalloc((void **)&g->fused_sync, sizeof(int) * (3 + nflags)) != cudaSuccess) {
         cudaGetLastError();
         set_error("tm_gauge_create: work list allocation failed");
         return TM_ERR_NOMEM;
     }
     TM_TRY(cuda_check(cudaMemcpyAsync(g->fused_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice, s),
                       "work list copy"));
-    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync, 0, sizeof(int) * (2 + nflags), s), "work list memset"));
+    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync, 0, sizeof(int) * (3 + nflags), s), "work list memset"));
     return cuda_check(cudaStreamSynchronize(s), "work list");
 }
 
@@ -479,17 +485,19 @@ static tm_status fused_launch(const tm_gauge *g, const tm_field *out_e, const tm
     const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
     const int epiB = pc == TM_PC_ASYM ? EPI_TWX_AXPY : EPI_X_TWAXPY;
     const Twist<double> &twB = pc == TM_PC_ASYM ? R : Ri;
-    const size_t nflags = (size_t)((g->Vh + 128L * FUSED_GROUP - 1) / (128L * FUSED_GROUP)) * FUSED_GROUP;
-    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync + 1, 0, sizeof(int) * (1 + nflags), s), "fused reset"));
+    // work counter, abort word and tile flags start at zero; the error word is kept until read
+    TM_TRY(cuda_check(cudaMemsetAsync(g->fused_sync + 1, 0, sizeof(int) * (2 + fused_nflags(g->Vh)), s), "fused reset"));
     cudaError_t e;
     if (out_e->prec == TM_PREC_F64) {
         const DslashArgs<double> aA = pass_args<double>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, Ri, 0);
         const DslashArgs<double> aB = pass_args<double>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, twB, 0);
-        e = launch_fused_p64(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->num_sms, s);
+        e = launch_fused_p64(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
+                             g->num_sms, s);
     } else {
         const DslashArgs<float> aA = pass_args<float>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, to_float(Ri), 1);
         const DslashArgs<float> aB = pass_args<float>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, to_float(twB), 1);
-        e = launch_fused_p32(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->num_sms, s);
+        e = launch_fused_p32(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
+                             g->num_sms, s);
     }
     return cuda_check(e, "fused operator launch");
 }
@@ -554,6 +562,7 @@ tm_status tm_last_error(char *buf, size_t n)
 
 tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out)
 {
+    TM_NVTX("tm_gauge_create");
     TM_TRY(check_params(p));
     if (!U_canon || !out) { set_error("tm_gauge_create: null pointer"); return TM_ERR_ARG; }
     *out = nullptr;
@@ -651,6 +660,7 @@ tm_status tm_field_bytes(const tm_gauge *g, int prec, int nrhs, size_t *data_byt
 
 tm_status tm_pack(const tm_gauge *g, const tm_field *out, const void *canon, int canon_type, int parity, void *stream)
 {
+    TM_NVTX("tm_pack");
     if (!g || !canon) { set_error("tm_pack: null pointer"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out, "out"));
     if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
@@ -662,6 +672,7 @@ tm_status tm_pack(const tm_gauge *g, const tm_field *out, const void *canon, int
 
 tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_field *in, int parity, void *stream)
 {
+    TM_NVTX("tm_unpack");
     if (!g || !canon) { set_error("tm_unpack: null pointer"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, in, "in"));
     if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
@@ -673,6 +684,7 @@ tm_status tm_unpack(const tm_gauge *g, void *canon, int canon_type, const tm_fie
 
 tm_status tm_noise_z2(const tm_gauge *g, const tm_field *out, int parity, unsigned long long seed, void *stream)
 {
+    TM_NVTX("tm_noise_z2");
     if (!g) { set_error("tm_noise_z2: null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out, "out"));
     if (parity != 0 && parity != 1) { set_error("parity must be 0 or 1"); return TM_ERR_ARG; }
@@ -682,18 +694,21 @@ tm_status tm_noise_z2(const tm_gauge *g, const tm_field *out, int parity, unsign
 tm_status tm_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
                     const tm_field *x, void *stream)
 {
+    TM_NVTX("tm_dslash");
     return dslash_api(g, out, in, out_parity, epilogue, x, stream, 0);
 }
 
 tm_status tm_dslash_dagger(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
                            const tm_field *x, void *stream)
 {
+    TM_NVTX("tm_dslash_dagger");
     return dslash_api(g, out, in, out_parity, epilogue, x, stream, 1);
 }
 
 tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                         int dagger, void *stream)
 {
+    TM_NVTX("tm_precond_op");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, in_e, "in_e"));
@@ -712,6 +727,7 @@ tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field
 tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
                                int pc, int dagger, const int *active_dev, int nactive, void *stream)
 {
+    TM_NVTX("tm_precond_op_active");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, in_e, "in_e"));
@@ -733,6 +749,7 @@ tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const t
 tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,
                  const tm_field *in_o, int dagger, void *stream)
 {
+    TM_NVTX("tm_mat");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, out_o, "out_o"));
@@ -757,6 +774,7 @@ tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o
 tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_field *b_e, const tm_field *b_o, int pc,
                          int dagger, void *stream)
 {
+    TM_NVTX("tm_prepare_rhs");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, bprime_e, "bprime_e"));
     TM_TRY(check_field(g, b_e, "b_e"));
@@ -804,6 +822,7 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
 tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_field *b_o, const tm_field *psi_e,
                              int dagger, void *stream)
 {
+    TM_NVTX("tm_reconstruct_odd");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, psi_o, "psi_o"));
     TM_TRY(check_field(g, b_o, "b_o"));
@@ -817,6 +836,7 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
 
 tm_status tm_autotune(tm_gauge *g0, void *stream)
 {
+    TM_NVTX("tm_autotune");
     if (!g0) { set_error("null gauge handle"); return TM_ERR_ARG; }
     // the tune table chooses among the twisted-mass kernels; a clover handle's kernels have one
     // launch form, so the table is tuned on a shallow copy of the handle without the clover term
@@ -1099,6 +1119,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
 
 tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, int inverse, int dagger, void *stream)
 {
+    TM_NVTX("tm_twist");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out, "out"));
     TM_TRY(check_field(g, in, "in"));
@@ -1114,6 +1135,7 @@ tm_status tm_twist(const tm_gauge *g, const tm_field *out, const tm_field *in, i
 tm_status tm_local_op(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, int inverse, int dagger,
                       void *stream)
 {
+    TM_NVTX("tm_local_op");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     TM_TRY(check_field(g, out, "out"));
     TM_TRY(check_field(g, in, "in"));
@@ -1144,6 +1166,43 @@ int tm_fused_work_list(const int L[4], int num_sms, int *items, int capacity)
     return (int)v.size();
 }
 
+tm_status tm_fused_set_work_list(tm_gauge *g, const int *items, int nitems, unsigned long long wait_limit_ns,
+                                 void *stream)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    if (!g->fused_items) { set_error("tm_fused_set_work_list: the handle has no work list"); return TM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> v;
+    if (items) {
+        // every entry names a group of the lattice and a pass; nothing else is checked, so a list
+        // may omit work (the waits that depend on it then give up at the limit)
+        const int ngroups = (int)(fused_nflags(g->Vh) / FUSED_GROUP);
+        if (nitems < 1 || nitems > g->fused_capacity) {
+            set_error("tm_fused_set_work_list: need 1 <= nitems <= %d", g->fused_capacity);
+            return TM_ERR_ARG;
+        }
+        for (int i = 0; i < nitems; i++)
+            if (items[i] < 0 || (items[i] >> 1) >= ngroups) {
+                set_error("tm_fused_set_work_list: entry %d = %d names no group (%d groups)", i, items[i], ngroups);
+                return TM_ERR_ARG;
+            }
+        v.assign(items, items + nitems);
+    } else {
+        v = fused_items(g->p.L, g->num_sms);
+    }
+    if (wait_limit_ns < 1000000ull || wait_limit_ns > 60000000000ull) {
+        set_error("tm_fused_set_work_list: wait limit must be 1 ms ... 60 s");
+        return TM_ERR_ARG;
+    }
+    TM_TRY(cuda_check(cudaStreamSynchronize(s), "tm_fused_set_work_list sync"));
+    TM_TRY(cuda_check(cudaMemcpyAsync(g->fused_items, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s),
+                      "work list copy"));
+    TM_TRY(cuda_check(cudaStreamSynchronize(s), "tm_fused_set_work_list sync"));
+    g->fused_nitems = (int)v.size();
+    g->wait_limit_ns = wait_limit_ns;
+    return TM_OK;
+}
+
 tm_status tm_device_status(const tm_gauge *g, void *stream)
 {
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
@@ -1162,6 +1221,7 @@ tm_status tm_device_status(const tm_gauge *g, void *stream)
 
 tm_status tm_gauge_set_clover(tm_gauge *g, double csw, void *stream)
 {
+    TM_NVTX("tm_gauge_set_clover");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
     if (!isfinite(csw)) { set_error("tm_gauge_set_clover: c_sw must be finite"); return TM_ERR_ARG; }
     if (csw == 0.0) {

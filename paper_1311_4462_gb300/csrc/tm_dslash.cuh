@@ -922,25 +922,48 @@ __device__ __forceinline__ void async_read_x(const char *buf, int tid, T (&xv)[N
 }
 
 // Completion flags of the fused operator (below): release after a tile's stores, acquire before
-// a dependent tile's loads.  A wait gives up after about a quarter second, records the failure in
-// *err and reports false (the caller then skips its site).
+// a dependent tile's loads.  A wait is bounded in time: it gives up once the device's nanosecond
+// clock (%globaltimer) shows more than `limit_ns` since it began, records the failure in the
+// handle's error word (sync[0], kept until tm_device_status reads it) and in the launch's abort
+// word (sync[2], cleared at every launch), and reports false; the caller then skips its site.  A
+// wait also gives up at once when the abort word is set, so after a first failure no other site
+// of the launch waits out a second limit (a flag that is set is still taken).  An iteration cap
+// (2^24 polls, each at least one L2 round trip) backs the clock up.
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
 {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int ld_relaxed_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release_gpu(int *p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ bool wait_flag(const int *f, int *err)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int i = 0; i < (1 << 22); i++) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// sync: [0] error word, [2] abort word of this launch
+__device__ __forceinline__ bool wait_flag(const int *f, int *sync, unsigned long long limit_ns)
+{
+    if (ld_acquire_gpu(f) != 0) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < (1 << 24); i++) {
+        if (ld_relaxed_gpu(sync + 2) != 0) return false;  // another wait of this launch gave up
+        __nanosleep(200);
         if (ld_acquire_gpu(f) != 0) return true;
-        __nanosleep(64);
+        if (global_ns() - t0 > limit_ns) break;
     }
-    atomicExch(err, 1);
+    atomicExch(sync + 2, 1);
+    atomicExch(sync, 1);
     return false;
 }
 
@@ -949,7 +972,8 @@ __device__ __forceinline__ bool wait_flag(const int *f, int *err)
 // waits for the completion flags of the 128-site tiles that hold its 8 neighbours.
 template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false>
 __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
-                                           char *smem_async, const int *flags, int *err)
+                                           char *smem_async, const int *flags, int *sync,
+                                           unsigned long long limit_ns = 0)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
@@ -990,7 +1014,7 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
     if constexpr (WAIT) {
         bool ok = true;
 #pragma unroll
-        for (int h = 0; h < 8; h++) ok = ok && wait_flag(flags + (nbr[h] >> 7), err);
+        for (int h = 0; h < 8; h++) ok = ok && wait_flag(flags + (nbr[h] >> 7), sync, limit_ns);
         if (!ok) return;
     }
     auto fetch = [&](int h) {
@@ -1080,21 +1104,21 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
 // is published with a release flag once all its threads' stores are done; a B site acquires the
 // flags of its neighbours' tiles before loading them (bounded waits).  Claiming in list order
 // means a waited-for tile has always been claimed by a running block, so the waits end.
-// sync: [0] error word (kept until read), [1] work counter, [2 + tile] A-tile completion flags;
-// the counter and the flags are zero at launch.
+// sync: [0] error word (kept until read), [1] work counter, [2] abort word of the launch,
+// [3 + tile] A-tile completion flags; the counter, the abort word and the flags are zero at launch.
 constexpr int FUSED_GROUP = 4;  // 128-site tiles per work item of the fused operator
 
 template <int PREC, int NF, int RECON, int MINB>
 __global__ void __launch_bounds__(128, MINB)
     k_mpc_fused(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> aA,
                 const __grid_constant__ DslashArgs<typename Traits<PREC>::real> aB, const int *__restrict__ items,
-                int nitems, int *sync)
+                int nitems, int *sync, unsigned long long limit_ns)
 {
     extern __shared__ __align__(16) char smem_async[];
     __shared__ int s_q;
     // the hop of the default launch form: paired (8 / 9) except one flavour with 18-real links
     constexpr bool FPAIR = PREC == P32 && (NF == 2 || RECON != 18);
-    int *err = sync, *counter = sync + 1, *flags = sync + 2;
+    int *counter = sync + 1, *flags = sync + 3;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_q = atomicAdd(counter, 1);
@@ -1107,7 +1131,7 @@ __global__ void __launch_bounds__(128, MINB)
         if (it & 1) {
             for (int sub = 0; sub < FUSED_GROUP; sub++) {
                 const int cb = (grp * FUSED_GROUP + sub) * 128 + tid;
-                if (cb < aB.Vh) async_site<PREC, NF, RECON, false, 2, false, true, FPAIR>(aB, cb, tid, smem_async, flags, err);
+                if (cb < aB.Vh) async_site<PREC, NF, RECON, false, 2, false, true, FPAIR>(aB, cb, tid, smem_async, flags, sync, limit_ns);
             }
         } else {
             for (int sub = 0; sub < FUSED_GROUP; sub++) {
@@ -1151,7 +1175,7 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
 template <int PREC, int NF, int RECON>
 cudaError_t launch_fused_impl(const DslashArgs<typename Traits<PREC>::real> &aA,
                               const DslashArgs<typename Traits<PREC>::real> &aB, const int *items, int nitems,
-                              int *sync, int num_sms, cudaStream_t s)
+                              int *sync, unsigned long long limit_ns, int num_sms, cudaStream_t s)
 {
     constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
     static std::atomic<unsigned long long> opted{0};
@@ -1173,16 +1197,17 @@ cudaError_t launch_fused_impl(const DslashArgs<typename Traits<PREC>::real> &aA,
         per_sm.store(b, std::memory_order_relaxed);
     }
     const int grid = (num_sms > 0 ? num_sms : 1) * b;
-    k_mpc_fused<PREC, NF, RECON, 3><<<grid, 128, bytes, s>>>(aA, aB, items, nitems, sync);
+    k_mpc_fused<PREC, NF, RECON, 3><<<grid, 128, bytes, s>>>(aA, aB, items, nitems, sync, limit_ns);
     return cudaGetLastError();
 }
 
 template <int PREC>
 cudaError_t launch_fused_dispatch(const DslashArgs<typename Traits<PREC>::real> &aA,
                                   const DslashArgs<typename Traits<PREC>::real> &aB, int nf, int recon,
-                                  const int *items, int nitems, int *sync, int num_sms, cudaStream_t s)
+                                  const int *items, int nitems, int *sync, unsigned long long limit_ns, int num_sms,
+                                  cudaStream_t s)
 {
-#define TM_FU(NF, R) return launch_fused_impl<PREC, NF, R>(aA, aB, items, nitems, sync, num_sms, s);
+#define TM_FU(NF, R) return launch_fused_impl<PREC, NF, R>(aA, aB, items, nitems, sync, limit_ns, num_sms, s);
 #define TM_FUR(NF)                         \
     switch (recon) {                       \
     case 18: TM_FU(NF, 18)                 \

@@ -246,6 +246,7 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
                               const tm_field *psi_o, const tm_field *g_e, const tm_field *g_o, double coef,
                               int project, void *stream)
 {
+    TM_NVTX("tm_force");
     if (!g || !F_canon || !psi_e || !psi_o || !g_e || !g_o) { set_error("tm_force: null argument"); return TM_ERR_ARG; }
     if (g->csw != 0.0) {
         set_error("tm_force: the link derivative of the clover term is not implemented");

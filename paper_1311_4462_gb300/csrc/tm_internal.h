@@ -1,11 +1,20 @@
 // tm_internal.h -- declarations shared by the library's translation units (not installed).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 
 #include "../../include/tm.h"
 
 namespace tmk {
+
+// NVTX range around a C-ABI call, named after the entry point (shown by Nsight tools; a push and a
+// pop of a few nanoseconds when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define TM_NVTX(name) ::tmk::NvtxRange tm_nvtx_range_(name)
 
 // kernel-level epilogue codes (see tm_dslash.cuh)
 enum Epilogue {
@@ -56,7 +65,9 @@ struct tm_gauge {
     int fused[3];              // 1: the preconditioned operator as one fused launch (FP64 / FP32; FP16 unused)
     int *fused_items;          // device work list of the fused operator (2 x tiles entries)
     int fused_nitems;
-    int *fused_sync;           // [0] error word, [1] work counter, [2 + tile] A-tile flags
+    int fused_capacity;        // entries the device work list holds
+    int *fused_sync;           // [0] error word, [1] work counter, [2] abort word, [3 + tile] A-tile flags
+    unsigned long long wait_limit_ns;  // time limit of one bounded wait of the fused operator
     size_t scratch_bytes;
 };
 

@@ -326,6 +326,12 @@ done:
         const tm_status cst = V.copy(x_user, x);  // DF64 -> FP64
         if (st == TM_OK) st = cst;
     }
+    if (st != TM_ERR_ARG && st != TM_ERR_NOMEM && st != TM_ERR_CUDA && g->fused_sync && (g->fused[0] || g->fused[1])) {
+        // the fused operator may have run: a bounded wait that gave up left some output sites
+        // unwritten, so the solution (and a residual computed from them) cannot be trusted
+        const tm_status dst = tm_device_status(g, s);
+        if (dst != TM_OK) st = dst;
+    }
     if (stats) {
         stats->iterations = it;
         stats->reliable_updates = nrel;
@@ -352,6 +358,7 @@ tm_status tm_solve_workspace_bytes(const tm_gauge *g, const tm_solver_params *sp
 tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
                    tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream)
 {
+    TM_NVTX("tm_solve");
     tm_status st = check_solver_params(g, sp);
     if (st != TM_OK) return st;
     if (!x_e || !b_e || !workspace) { set_error("tm_solve: null field or workspace"); return TM_ERR_ARG; }
@@ -367,6 +374,7 @@ tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, 
 
 tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stream)
 {
+    TM_NVTX("tm_norm2");
     if (!g || !x || !x->data || !out) { set_error("tm_norm2: null argument"); return TM_ERR_ARG; }
     Solver V;
     V.g = g;
@@ -379,8 +387,41 @@ tm_status tm_norm2(const tm_gauge *g, const tm_field *x, double *out, void *stre
     return V.read(SL_TMP2, out);
 }
 
+tm_status tm_axpby(const tm_gauge *g, const tm_field *out, double a, const tm_field *x, double b, const tm_field *y,
+                   void *stream)
+{
+    TM_NVTX("tm_axpby");
+    if (!g || !out || !x || !out->data || !x->data) { set_error("tm_axpby: null argument"); return TM_ERR_ARG; }
+    const bool hasy = y != nullptr;
+    if (hasy && !y->data) { set_error("tm_axpby: null y data"); return TM_ERR_ARG; }
+    if (out->prec != x->prec || (hasy && y->prec != x->prec)) {
+        set_error("tm_axpby: out, x and y must share a precision");
+        return TM_ERR_ARG;
+    }
+    if (prec_index(x->prec) < 0) { set_error("tm_axpby: unknown precision %d", x->prec); return TM_ERR_ARG; }
+    if ((x->prec == TM_PREC_F16) && (!out->norm || !x->norm || (hasy && !y->norm))) {
+        set_error("tm_axpby: FP16 fields need their norm arrays");
+        return TM_ERR_ARG;
+    }
+    if (out->nrhs != x->nrhs || (hasy && y->nrhs != x->nrhs) || x->nrhs < 1 || x->nrhs > 65535) {
+        set_error("tm_axpby: fields must share nrhs in [1, 65535]");
+        return TM_ERR_ARG;
+    }
+    if (!isfinite(a) || !isfinite(b)) { set_error("tm_axpby: coefficients must be finite"); return TM_ERR_ARG; }
+    SiteOpArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.op = OP_AXPBY;
+    sa.A = fref(x);
+    sa.B = hasy ? fref(y) : fnone();
+    sa.C = fref(out);
+    sa.ca = sv(a);
+    sa.cb = sv(b);
+    return cuda_check(launch_site_op(g, sa, x->nrhs, (cudaStream_t)stream), "tm_axpby");
+}
+
 tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, void *stream)
 {
+    TM_NVTX("tm_dot");
     if (!g || !a || !b || !a->data || !b->data || !re_out) { set_error("tm_dot: null argument"); return TM_ERR_ARG; }
     Solver V;
     V.g = g;
@@ -727,6 +768,7 @@ extern "C" {
 tm_status tm_g5dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, double *im_out,
                    void *stream)
 {
+    TM_NVTX("tm_g5dot");
     if (!g || !a || !b || !a->data || !b->data || !re_out || !im_out) { set_error("tm_g5dot: null argument"); return TM_ERR_ARG; }
     if (a->nrhs != b->nrhs || a->nrhs < 1 || a->nrhs > TM_MAX_RHS) {
         set_error("tm_g5dot: fields must share nrhs in [1, %d]", TM_MAX_RHS);
@@ -766,6 +808,7 @@ tm_status tm_solve_multi_workspace_bytes(const tm_gauge *g, const tm_solver_para
 tm_status tm_solve_multi(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, const tm_solver_params *sp,
                          tm_solver_stats *stats, void *workspace, size_t workspace_bytes, void *stream)
 {
+    TM_NVTX("tm_solve_multi");
     tm_status st = check_solver_params(g, sp);
     if (st != TM_OK) return st;
     if (!x_e || !b_e || !workspace || !x_e->data || !b_e->data) {

@@ -59,6 +59,8 @@ def test_flop_convention():
     assert b.FLOPS_PER_SITE[1] == 2 * hop + 48 + 72 + 48
     # doublet: both flavours hop, the flavour-mixing R (192) and R^-1 (240) per site, xpay per flavour
     assert b.FLOPS_PER_SITE[2] == 2 * 2 * hop + 192 + 240 + 2 * 48
+    # the Wilson limit (R = 1): two hopping terms and the xpay, no twist
+    assert b.FLOPS_WILSON == 2 * hop + 48
 
 
 def test_launch_form_names():

@@ -121,3 +121,36 @@ def test_pseudofermion_force_vs_oracle():
     F_ref = orc.force(po, U, X, Y, coef=-2.0, project=True)
     assert rel(tU.grad.cpu().numpy(), F_ref) < 1e-6
     assert rel(tphi.grad.cpu().numpy(), 2 * X) < 1e-6
+
+
+def test_autograd_reuses_the_handle_while_U_is_unchanged():
+    """Repeated calls with the same, unmodified U share one gauge handle (the links are packed once);
+    an in-place change of U makes a new one.  The upstream gradient scales the results."""
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import autograd as tag
+    from paper_1311_4462_gb300.autograd import PseudofermionAction, TMApply
+    name, L, flavor, kappa, mu, eps = CASES[1]
+    p = tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=12)
+    U = inputs.gauge_field(L, 1304)
+    psi, phi = inputs.spinor_field(L, p.nf, 2408), inputs.spinor_field(L, p.nf, 2409)
+    tU = torch.from_numpy(U).to("cuda").requires_grad_(True)
+    tpsi = torch.from_numpy(psi).to("cuda")
+    y1 = TMApply.apply(tU, tpsi, p)
+    g1 = tag.gauge_for(tU, p)
+    y2 = TMApply.apply(tU, tpsi, p)
+    assert tag.gauge_for(tU, p) is g1
+    assert torch.equal(y1, y2)
+    tphi = torch.from_numpy(phi).to("cuda").requires_grad_(True)
+    S = PseudofermionAction.apply(tU, tphi, p, 1e-11)
+    assert tag.gauge_for(tU, p) is g1
+    (0.5 * S).backward()
+    gU_half, gphi_half = tU.grad.clone(), tphi.grad.clone()
+    tU.grad, tphi.grad = None, None
+    S = PseudofermionAction.apply(tU, tphi, p, 1e-11)
+    S.backward()
+    assert torch.allclose(2 * gU_half, tU.grad, rtol=1e-12, atol=0)
+    assert torch.allclose(2 * gphi_half, tphi.grad, rtol=1e-12, atol=0)
+    with torch.no_grad():
+        tU.mul_(1.0)  # an in-place change bumps U's version: the cached links are stale
+    assert tag.gauge_for(tU, p) is not g1
+    tag.clear_cache()

@@ -23,6 +23,9 @@ CASES = [
     ("plus_2x4x6x8", (2, 4, 6, 8), 1, 0.1612, 0.004, 0.0),
     ("minus_8x6x4x10", (8, 6, 4, 10), -1, 0.1612, 0.004, 0.0),
     ("nd_2^4", (2, 2, 2, 2), 2, 0.16, 0.135, 0.15),
+    # the Wilson limit mu = eps = 0 (the "Wilson" column of Table 1): R = 1, one flavour and a doublet
+    ("wilson_4x2x6x4", (4, 2, 6, 4), 1, 0.1612, 0.0, 0.0),
+    ("wilson_nd_6x4x4x2", (6, 4, 4, 2), 2, 0.16, 0.0, 0.0),
 ]
 PRECS = [8, 16, 4, 2]
 RECONS = [18, 12, 8]
