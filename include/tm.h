@@ -85,7 +85,8 @@ typedef enum {
     TM_EPI_TWXPAY_ASYM = 2, /* out = R x - kappa^2 D t    the fused R_ee - kappa^2 D_eo      */
     TM_EPI_TWXPAY_SYM = 3,  /* out = x - kappa^2 R^-1 D t (eq. 2.3)                         */
     TM_EPI_XPAY = 4,        /* out = x + kappa D t                                          */
-    TM_EPI_TWINV_XPAY = 5   /* out = R^-1 (x + kappa D t)  odd-site reconstruction          */
+    TM_EPI_TWINV_XPAY = 5,  /* out = R^-1 (x + kappa D t)  odd-site reconstruction          */
+    TM_EPI_XMAY_K2 = 6      /* out = x - kappa^2 D t      second launch of the adjoint of eq. 2.3 */
 } tm_epilogue;
 
 typedef struct {
@@ -409,6 +410,62 @@ tm_status tm_fused_set_work_list(tm_gauge *g, const int *items, int nitems, unsi
  * small extents or too small a capacity.
  */
 int tm_fused_work_list(const int L[4], int num_sms, int *items, int capacity);
+
+/* ------------------------------------------------------- domain decomposition in time (sec. 2.1) */
+/*
+ * The multi-GPU parallelisation of sec. 2.1 (Figs. 1-2): the lattice is cut into time slabs, one
+ * per rank, and every hopping launch exchanges one face per neighbour: the spin-projected
+ * half-spinors of the boundary slice (2 spin rows x 3 colours = 12 reals per site and flavour,
+ * both flavours of the doublet in one message).  A rank holds its slab in an ordinary handle
+ * (tm_gauge_create with L[3] = its slab's time extent, t_antiperiodic of the whole lattice, the
+ * links of its own sites) and marks it with tm_gauge_set_partition.  A hopping launch then runs as
+ *   1. tm_dd_pack_faces   the faces of the input field for the previous and the next slab;
+ *   2. (the caller's transport) send them; receive the neighbours' faces;
+ *   3. tm_dd_dslash       the interior slices (region TM_DD_INTERIOR, needs no face, may start
+ *                         before the faces arrive) and the first and last slice (TM_DD_BOUNDARY).
+ * The composed operators (eq. 2.2-2.4) are two such launches; reductions of a solver are sums of
+ * the ranks' tm_dot / tm_norm2 (one FP64 allreduce each).  Faces are kept in the arithmetic
+ * precision (FP64 fields: doubles, FP32 / FP16 fields: floats, FP16 with the input's site norm),
+ * so a decomposed operator gives the same bits as the undecomposed one.  A slab handle refuses
+ * the other hopping calls (tm_dslash, tm_precond_op, tm_mat, tm_prepare_rhs, tm_reconstruct_odd,
+ * tm_solve, tm_solve_multi, tm_force) with TM_ERR_ARG; site-local calls work as before.
+ * Decomposed operators take single-RHS FP64 / FP32 / FP16 fields and no clover term.
+ */
+typedef enum { TM_DD_ALL = 0, TM_DD_INTERIOR = 1, TM_DD_BOUNDARY = 2 } tm_dd_region;
+
+/* Mark the handle as the slab of time slices [t_offset, t_offset + L[3]) of a lattice with
+ * Lt_global slices (t_offset even, t_offset + L[3] <= Lt_global, Lt_global even); the faces that
+ * cross the time boundary of the whole lattice take the antiperiodic sign.  Lt_global = 0 removes
+ * the mark.  One slab covering the whole lattice (t_offset 0, Lt_global = L[3]) whose faces go
+ * back to itself gives the undecomposed operator.  Host only.  Errors: TM_ERR_ARG. */
+tm_status tm_gauge_set_partition(tm_gauge *g, int t_offset, int Lt_global);
+
+/* Bytes of one face buffer for fields of `prec` (both flavours of a doublet). */
+tm_status tm_dd_face_bytes(const tm_gauge *g, int prec, size_t *bytes);
+
+/*
+ * Pack the two faces of the input `in` of a hopping launch with output parity out_parity (in has
+ * parity 1 - out_parity): face_prev (for the previous slab) = (1 - s gamma_4) in at the first
+ * slice; face_next (for the next slab) = U_4^dag (1 + s gamma_4) in at the last slice; s = +1 for
+ * H, -1 for H^dag (dagger = 1).  twist_in = 1 applies R^-1 (R^-dag when dagger) to in first, as
+ * the input prologue of tm_dd_dslash does.  Device buffers of tm_dd_face_bytes, 16-byte aligned.
+ * Asynchronous on `stream`.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_dd_pack_faces(const tm_gauge *g, void *face_prev, void *face_next, const tm_field *in, int out_parity,
+                           int dagger, int twist_in, void *stream);
+
+/*
+ * tm_dslash (dagger = 0) or tm_dslash_dagger (dagger = 1) on a slab: out(out_parity) =
+ * epilogue(H in) with the epilogues of tm_dslash (x as there), twist_in = 1 applying R^-1 (R^-dag)
+ * to every neighbour first.  ghost_prev / ghost_next: the faces received from the previous /
+ * next slab (their face_next / face_prev), needed by TM_DD_ALL and TM_DD_BOUNDARY; TM_DD_INTERIOR
+ * reads none (NULL allowed).  The interior slices run in the handle's tuned launch form, the
+ * boundary slices in a register-capped form.  Asynchronous on `stream`.
+ * Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_dd_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                       const tm_field *x, int dagger, int twist_in, const void *ghost_prev, const void *ghost_next,
+                       int region, void *stream);
 
 /* --------------------------------------------------------------------- allocation-free variant */
 /*

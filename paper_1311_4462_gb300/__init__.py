@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib as L
-from ._lib import (TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT, TM_SOLVER_CG, TM_SOLVER_MIXED, TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM,
+from ._lib import (TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT, TM_SOLVER_CG, TM_SOLVER_MIXED, TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM, TM_EPI_XMAY_K2,
                    TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_NDEG_DOUBLET, TM_PC_ASYM, TM_PC_SYM, TM_PREC_F16, TM_PREC_F32,
                    TM_PREC_F64, TM_PREC_DF64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
 

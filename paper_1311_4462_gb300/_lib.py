@@ -14,9 +14,10 @@ TM_TWIST_PLUS, TM_TWIST_MINUS, TM_NDEG_DOUBLET = 1, -1, 2
 TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64 = 8, 4, 2, 16
 TM_PC_ASYM, TM_PC_SYM = 0, 1
 TM_C128, TM_C64 = 0, 1
-TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_EPI_TWINV_XPAY = range(6)
+TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_EPI_TWINV_XPAY, TM_EPI_XMAY_K2 = range(7)
 TM_SOLVER_CG, TM_SOLVER_MIXED = 0, 1
 TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT = 0, 1
+TM_DD_ALL, TM_DD_INTERIOR, TM_DD_BOUNDARY = 0, 1, 2
 
 
 class tm_params(ctypes.Structure):
@@ -90,6 +91,10 @@ _SIGS = {
     "tm_device_status": [vp, vp],
     "tm_fused_work_list": [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "tm_fused_set_work_list": [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_ulonglong, vp],
+    "tm_gauge_set_partition": [vp, ctypes.c_int, ctypes.c_int],
+    "tm_dd_face_bytes": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+    "tm_dd_pack_faces": [vp, vp, vp, FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp],
+    "tm_dd_dslash": [vp, FP, FP, ctypes.c_int, ctypes.c_int, FP, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp],
 }
 
 

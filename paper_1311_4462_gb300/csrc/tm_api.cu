@@ -70,6 +70,14 @@ cudaError_t launch_dslash_clov_p16(const DslashArgs<float> &a, int nf, int recon
 cudaError_t launch_clover_apply(const tm_gauge *g, const tm_field *out, const tm_field *in, int parity, bool inverse,
                                 const Twist<double> &X, cudaStream_t s);
 
+cudaError_t launch_dd_p64(const DslashArgs<double> &a, const DDArgs<double> *dd, void *face_prev, void *face_next,
+                          int nf, int recon, bool pro, cudaStream_t s);
+cudaError_t launch_dd_p32(const DslashArgs<float> &a, const DDArgs<float> *dd, void *face_prev, void *face_next,
+                          int nf, int recon, bool pro, cudaStream_t s);
+cudaError_t launch_dd_p16(const DslashArgs<float> &a, const DDArgs<float> *dd, void *face_prev, void *face_next,
+                          int nf, int recon, bool pro, cudaStream_t s);
+size_t dd_face_bytes(int prec, int nf, int st);
+
 static thread_local char g_err[512];
 constexpr int TM_MAX_RHS_API = 64;
 
@@ -264,6 +272,8 @@ static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out
     a.x_norm = x ? x->norm : nullptr;
     a.gauge = g->links[pidx];
     a.Vh = g->Vh;
+    a.cb0 = 0;
+    a.ncb = g->Vh;
     a.X1h = g->X1h;
     a.Lx = g->p.L[0];
     a.Ly = g->p.L[1];
@@ -279,7 +289,7 @@ static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out
 // right-hand-side indices) the multi-RHS kernel processes those right-hand sides of the fields.
 tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x, int out_parity,
                         int dagger, int epi, double coef, const Twist<double> *tw_epi, const Twist<double> *tw_pro,
-                        cudaStream_t s, const int *act, int nact)
+                        cudaStream_t s, const int *act, int nact, int cb0 = 0, int ncb = 0)
 {
     const int pidx = prec_index(in->prec);
     const bool pro = tw_pro != nullptr;
@@ -318,9 +328,11 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         }
         return cuda_check(e, "clover dslash launch");
     }
+    if (ncb > 0 && (multi || pidx == 3)) { set_error("internal: site ranges are single-RHS FP64 / FP32 / FP16"); return TM_ERR_ARG; }
     if (pidx == 0) {
         DslashArgs<double> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
+        if (ncb > 0) { a.cb0 = cb0; a.ncb = ncb; }
         a.epilogue = epi;
         a.sigma = dagger ? -1.0 : 1.0;
         a.coef = coef;
@@ -346,6 +358,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
     } else {
         DslashArgs<float> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
+        if (ncb > 0) { a.cb0 = cb0; a.ncb = ncb; }
         a.epilogue = epi;
         a.sigma = dagger ? -1.0f : 1.0f;
         a.coef = (float)coef;
@@ -376,6 +389,16 @@ static tm_status same_prec(const tm_field *a, const tm_field *b, const char *wha
     return TM_OK;
 }
 
+static tm_status refuse_slab(const tm_gauge *g, const char *what)
+{
+    if (g && g->dd) {
+        set_error("%s: the handle holds one time slab of a decomposed lattice; its hops need the neighbours' faces "
+                  "(tm_dd_pack_faces / tm_dd_dslash)", what);
+        return TM_ERR_ARG;
+    }
+    return TM_OK;
+}
+
 #define TM_TRY(x)                     \
     do {                              \
         tm_status _st = (x);          \
@@ -386,6 +409,7 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
                             const tm_field *x, void *stream, int dagger)
 {
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_dslash"));
     TM_TRY(check_field(g, out, "out"));
     TM_TRY(check_field(g, in, "in"));
     TM_TRY(same_prec(out, in, "tm_dslash"));
@@ -394,7 +418,7 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
     const double k = g->p.kappa;
     const Twist<double> R = make_twist(g, TW_R, dagger), Ri = make_twist(g, TW_RINV, dagger);
     const bool needx = epilogue >= TM_EPI_TWXPAY_ASYM;
-    if (epilogue < TM_EPI_NONE || epilogue > TM_EPI_TWINV_XPAY) { set_error("unknown epilogue %d", epilogue); return TM_ERR_ARG; }
+    if (epilogue < TM_EPI_NONE || epilogue > TM_EPI_XMAY_K2) { set_error("unknown epilogue %d", epilogue); return TM_ERR_ARG; }
     if (needx) {
         TM_TRY(check_field(g, x, "x"));
         TM_TRY(same_prec(out, x, "tm_dslash"));
@@ -406,6 +430,7 @@ static tm_status dslash_api(const tm_gauge *g, const tm_field *out, const tm_fie
     case TM_EPI_TWXPAY_ASYM: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_TWX_AXPY, -k * k, &R, nullptr, s);
     case TM_EPI_TWXPAY_SYM: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_X_TWAXPY, -k * k, &Ri, nullptr, s);
     case TM_EPI_XPAY: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_XPAY, k, nullptr, nullptr, s);
+    case TM_EPI_XMAY_K2: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_XPAY, -k * k, nullptr, nullptr, s);
     default: return dslash_launch(g, out, in, x, out_parity, dagger, EPI_TW_XPAY, k, &Ri, nullptr, s);
     }
 }
@@ -542,6 +567,77 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
     }
     TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s, act, nact));
     return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
+}
+
+// The kernel epilogue, coefficient and local operator of a tm_epilogue code (tm_dslash's mapping)
+static tm_status epilogue_of(const tm_gauge *g, int epilogue, int dagger, int *epi, double *coef, Twist<double> *tw,
+                             bool *has_tw)
+{
+    const double k = g->p.kappa;
+    *has_tw = true;
+    switch (epilogue) {
+    case TM_EPI_NONE: *epi = EPI_SCALE; *coef = 1.0; *has_tw = false; break;
+    case TM_EPI_TWINV: *epi = EPI_TW; *coef = 1.0; *tw = make_twist(g, TW_RINV, dagger); break;
+    case TM_EPI_TWXPAY_ASYM: *epi = EPI_TWX_AXPY; *coef = -k * k; *tw = make_twist(g, TW_R, dagger); break;
+    case TM_EPI_TWXPAY_SYM: *epi = EPI_X_TWAXPY; *coef = -k * k; *tw = make_twist(g, TW_RINV, dagger); break;
+    case TM_EPI_XPAY: *epi = EPI_XPAY; *coef = k; *has_tw = false; break;
+    case TM_EPI_XMAY_K2: *epi = EPI_XPAY; *coef = -k * k; *has_tw = false; break;
+    case TM_EPI_TWINV_XPAY: *epi = EPI_TW_XPAY; *coef = k; *tw = make_twist(g, TW_RINV, dagger); break;
+    default: set_error("unknown epilogue %d", epilogue); return TM_ERR_ARG;
+    }
+    return TM_OK;
+}
+
+static tm_status check_dd(const tm_gauge *g, const tm_field *f, const char *what)
+{
+    if (!g->dd) { set_error("%s: the handle holds no slab (tm_gauge_set_partition)", what); return TM_ERR_ARG; }
+    if (f->prec == TM_PREC_DF64 || f->nrhs != 1) {
+        set_error("%s: decomposed operators take single-RHS FP64 / FP32 / FP16 fields", what);
+        return TM_ERR_ARG;
+    }
+    return TM_OK;
+}
+
+
+// face pack (ghost == NULL) or boundary-slice launch of a slab
+template <typename T>
+static cudaError_t dd_launch_t(const tm_gauge *g, DslashArgs<T> &a, const DDArgs<T> *dd, void *fp, void *fn, bool pro,
+                               int pidx, cudaStream_t s)
+{
+    if constexpr (std::is_same<T, double>::value) return launch_dd_p64(a, dd, fp, fn, g->nf, g->p.recon, pro, s);
+    else return pidx == 1 ? launch_dd_p32(a, dd, fp, fn, g->nf, g->p.recon, pro, s)
+                          : launch_dd_p16(a, dd, fp, fn, g->nf, g->p.recon, pro, s);
+}
+
+template <typename T>
+static tm_status dd_call(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x, int out_parity,
+                         int dagger, int epi, double coef, const Twist<double> &tw_epi, const Twist<double> *tw_pro,
+                         const void *ghost_prev, const void *ghost_next, void *face_prev, void *face_next, cudaStream_t s)
+{
+    const int pidx = prec_index(in->prec);
+    DslashArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    fill_common(a, g, out ? out : in, in, x, out_parity, pidx);
+    a.epilogue = epi;
+    a.sigma = dagger ? T(-1) : T(1);
+    a.coef = (T)coef;
+    Twist<double> z;
+    memset(&z, 0, sizeof(z));
+    if constexpr (std::is_same<T, double>::value) {
+        a.tw_epi = tw_epi;
+        a.tw_pro = tw_pro ? *tw_pro : z;
+    } else {
+        a.tw_epi = to_float(tw_epi);
+        a.tw_pro = to_float(tw_pro ? *tw_pro : z);
+    }
+    if (!ghost_prev && !ghost_next) return cuda_check(dd_launch_t<T>(g, a, nullptr, face_prev, face_next, tw_pro != nullptr, pidx, s), "tm_dd_pack_faces");
+    DDArgs<T> dd;
+    dd.ghost_b = ghost_prev;
+    dd.ghost_f = ghost_next;
+    dd.st = g->X1h * g->p.L[1] * g->p.L[2];
+    dd.sign_b = (T)g->dd_sign_b;
+    dd.sign_f = (T)g->dd_sign_f;
+    return cuda_check(dd_launch_t<T>(g, a, &dd, nullptr, nullptr, tw_pro != nullptr, pidx, s), "tm_dd_dslash boundary");
 }
 
 }  // namespace tmk
@@ -710,6 +806,7 @@ tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field
 {
     TM_NVTX("tm_precond_op");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_precond_op"));
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, in_e, "in_e"));
     TM_TRY(check_field(g, tmp_o, "tmp_o"));
@@ -729,6 +826,7 @@ tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const t
 {
     TM_NVTX("tm_precond_op_active");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_precond_op_active"));
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, in_e, "in_e"));
     TM_TRY(check_field(g, tmp_o, "tmp_o"));
@@ -751,6 +849,7 @@ tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o
 {
     TM_NVTX("tm_mat");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_mat"));
     TM_TRY(check_field(g, out_e, "out_e"));
     TM_TRY(check_field(g, out_o, "out_o"));
     TM_TRY(check_field(g, in_e, "in_e"));
@@ -776,6 +875,7 @@ tm_status tm_prepare_rhs(const tm_gauge *g, const tm_field *bprime_e, const tm_f
 {
     TM_NVTX("tm_prepare_rhs");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_prepare_rhs"));
     TM_TRY(check_field(g, bprime_e, "bprime_e"));
     TM_TRY(check_field(g, b_e, "b_e"));
     TM_TRY(check_field(g, b_o, "b_o"));
@@ -824,6 +924,7 @@ tm_status tm_reconstruct_odd(const tm_gauge *g, const tm_field *psi_o, const tm_
 {
     TM_NVTX("tm_reconstruct_odd");
     if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_reconstruct_odd"));
     TM_TRY(check_field(g, psi_o, "psi_o"));
     TM_TRY(check_field(g, b_o, "b_o"));
     TM_TRY(check_field(g, psi_e, "psi_e"));
@@ -1230,6 +1331,103 @@ tm_status tm_gauge_set_clover(tm_gauge *g, double csw, void *stream)
         return TM_OK;
     }
     return clover_build(g, csw, (cudaStream_t)stream);
+}
+
+
+/* ------------------------------------------------------------------ domain decomposition in t */
+tm_status tm_gauge_set_partition(tm_gauge *g, int t_offset, int Lt_global)
+{
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    if (Lt_global == 0) {
+        g->dd = 0;
+        return TM_OK;
+    }
+    const int Lt = g->p.L[3];
+    if (g->csw != 0.0) { set_error("tm_gauge_set_partition: no decomposed clover operator"); return TM_ERR_ARG; }
+    if (t_offset < 0 || (t_offset & 1) || Lt_global < Lt || (Lt_global & 1) || t_offset + Lt > Lt_global) {
+        set_error("tm_gauge_set_partition: need an even offset t0 >= 0 and t0 + %d <= Lt_global (even)", Lt);
+        return TM_ERR_ARG;
+    }
+    g->dd = 1;
+    g->dd_t0 = t_offset;
+    g->dd_Lt = Lt_global;
+    g->dd_sign_b = (t_offset == 0 && g->p.t_antiperiodic) ? -1.0 : 1.0;
+    g->dd_sign_f = (t_offset + Lt == Lt_global && g->p.t_antiperiodic) ? -1.0 : 1.0;
+    return TM_OK;
+}
+
+tm_status tm_dd_face_bytes(const tm_gauge *g, int prec, size_t *bytes)
+{
+    if (!g || !bytes) { set_error("tm_dd_face_bytes: null argument"); return TM_ERR_ARG; }
+    const size_t b = dd_face_bytes(prec, g->nf, g->X1h * g->p.L[1] * g->p.L[2]);
+    if (!b) { set_error("tm_dd_face_bytes: faces exist for FP64, FP32 and FP16 fields"); return TM_ERR_ARG; }
+    *bytes = b;
+    return TM_OK;
+}
+
+tm_status tm_dd_pack_faces(const tm_gauge *g, void *face_prev, void *face_next, const tm_field *in, int out_parity,
+                           int dagger, int twist_in, void *stream)
+{
+    TM_NVTX("tm_dd_pack_faces");
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, in, "in"));
+    TM_TRY(check_dd(g, in, "tm_dd_pack_faces"));
+    if (!face_prev || !face_next || ((uintptr_t)face_prev & 15) || ((uintptr_t)face_next & 15)) {
+        set_error("tm_dd_pack_faces: faces must be 16-byte aligned device buffers");
+        return TM_ERR_ARG;
+    }
+    if (out_parity != 0 && out_parity != 1) { set_error("out_parity must be 0 or 1"); return TM_ERR_ARG; }
+    const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
+    const Twist<double> *pro = twist_in ? &Ri : nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (in->prec == TM_PREC_F64)
+        return dd_call<double>(g, nullptr, in, nullptr, out_parity, dagger, EPI_SCALE, 1.0, Ri, pro, nullptr, nullptr,
+                               face_prev, face_next, s);
+    return dd_call<float>(g, nullptr, in, nullptr, out_parity, dagger, EPI_SCALE, 1.0, Ri, pro, nullptr, nullptr, face_prev,
+                          face_next, s);
+}
+
+tm_status tm_dd_dslash(const tm_gauge *g, const tm_field *out, const tm_field *in, int out_parity, int epilogue,
+                       const tm_field *x, int dagger, int twist_in, const void *ghost_prev, const void *ghost_next,
+                       int region, void *stream)
+{
+    TM_NVTX("tm_dd_dslash");
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(check_field(g, out, "out"));
+    TM_TRY(check_field(g, in, "in"));
+    TM_TRY(same_prec(out, in, "tm_dd_dslash"));
+    TM_TRY(check_dd(g, in, "tm_dd_dslash"));
+    if (out_parity != 0 && out_parity != 1) { set_error("out_parity must be 0 or 1"); return TM_ERR_ARG; }
+    if (out->data == in->data) { set_error("tm_dd_dslash: out must not alias in"); return TM_ERR_ARG; }
+    if (region < TM_DD_ALL || region > TM_DD_BOUNDARY) { set_error("tm_dd_dslash: unknown region %d", region); return TM_ERR_ARG; }
+    if (region != TM_DD_INTERIOR && (!ghost_prev || !ghost_next)) {
+        set_error("tm_dd_dslash: the boundary slices need both received faces");
+        return TM_ERR_ARG;
+    }
+    int epi;
+    double coef;
+    Twist<double> tw;
+    bool has_tw;
+    TM_TRY(epilogue_of(g, epilogue, dagger, &epi, &coef, &tw, &has_tw));
+    if (epilogue >= TM_EPI_TWXPAY_ASYM) {
+        TM_TRY(check_field(g, x, "x"));
+        TM_TRY(same_prec(out, x, "tm_dd_dslash"));
+    } else {
+        x = nullptr;
+    }
+    if (!has_tw) memset(&tw, 0, sizeof(tw));
+    const Twist<double> Ri = make_twist(g, TW_RINV, dagger);
+    const Twist<double> *pro = twist_in ? &Ri : nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int st = g->X1h * g->p.L[1] * g->p.L[2], Lt = g->p.L[3];
+    if (region != TM_DD_BOUNDARY && Lt > 2)  // interior slices: the handle's tuned launch form over a site range
+        TM_TRY(dslash_launch(g, out, in, x, out_parity, dagger, epi, coef, has_tw ? &tw : nullptr, pro, s, nullptr, 1,
+                             st, (Lt - 2) * st));
+    if (region == TM_DD_INTERIOR) return TM_OK;
+    if (in->prec == TM_PREC_F64)
+        return dd_call<double>(g, out, in, x, out_parity, dagger, epi, coef, tw, pro, ghost_prev, ghost_next, nullptr,
+                               nullptr, s);
+    return dd_call<float>(g, out, in, x, out_parity, dagger, epi, coef, tw, pro, ghost_prev, ghost_next, nullptr, nullptr, s);
 }
 
 }  // extern "C"

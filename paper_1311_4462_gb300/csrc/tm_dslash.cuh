@@ -39,6 +39,7 @@ struct DslashArgs {
     const float *x_norm;
     const void *gauge;  // [mu][parity][chunk][Vh] of this precision / recon
     int Vh, X1h, Lx, Ly, Lz, Lt;
+    int cb0, ncb;       // output sites [cb0, cb0 + ncb) of the single-RHS launch forms (all: 0, Vh)
     int out_parity;
     int tbc;
     int epilogue;
@@ -412,8 +413,115 @@ __device__ __forceinline__ void local_op(const DslashArgs<T> &a, int cb, T v[NF]
     else apply_twist<T, NF>(a.tw_epi, v);
 }
 
-template <int PREC, int NF, int RECON, bool PRO, bool CLOV = false, bool PAIR = false>
-__device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs)
+// ---- Domain decomposition in time (the multi-GPU parallelisation of sec. 2.1) ----
+// A handle may hold one time slab [t0, t0 + Lt) of a lattice split over ranks in t.  The hops
+// that leave the slab read a face that the neighbouring rank packed (k_dd_pack below): for the
+// forward hop out of the last slice, the spin-projected half-spinor (1 - s g_4) in(x + t) of the
+// next rank (2 spin rows x 3 colours, 12 reals per flavour), multiplied here by the local link
+// U_t(x); for the backward hop out of the first slice, U_t(x - t)^dag (1 + s g_4) in(x - t) of the
+// previous rank, the link being that rank's.  Faces hold the values in the arithmetic precision
+// (binary64, or binary32 for FP32 / FP16 storage; FP16 faces keep the input's site norm beside
+// them), so a decomposed operator performs the same operations in the same order as the one-slab
+// kernel and gives the same bits.  Face layout: [flavour][16-byte chunk][site of the slice] with
+// the 12 reals ordered (row * 3 + colour) * 2 + re/im, then (FP16) float norms [flavour][site].
+// The time-boundary sign of the whole lattice is applied by the receiving slab.
+template <typename T>
+struct DDArgs {
+    const void *ghost_b;  // from the previous slab: U^dag-multiplied rows for the first slice
+    const void *ghost_f;  // from the next slab: projected rows for the last slice
+    int st;               // sites of one time slice of one parity
+    T sign_b, sign_f;     // -1 where the hop crosses the antiperiodic boundary of the whole lattice
+};
+
+template <int PREC>
+struct FaceGeo {
+    using T = typename Traits<PREC>::real;
+    using FC = typename std::conditional<std::is_same<T, double>::value, double2, float4>::type;
+    static constexpr int CH = 12 * (int)sizeof(T) / 16;  // chunks per flavour: 6 (double), 3 (float)
+    static constexpr bool NORM = PREC == P16;
+    static size_t bytes(int nf, int st) { return (size_t)nf * st * (12 * sizeof(T) + (NORM ? sizeof(float) : 0)); }
+};
+
+template <int PREC, typename T>
+__device__ __forceinline__ void face_load(const void *face, int nf, int f, int st, int i, C<T> r0[3], C<T> r1[3], T &n)
+{
+    using G = FaceGeo<PREC>;
+    using FC = typename G::FC;
+    const FC *p = reinterpret_cast<const FC *>(face) + (size_t)f * G::CH * st + i;
+    T v[12];
+#pragma unroll
+    for (int k = 0; k < G::CH; k++) {
+        const FC c = ldg(p + (size_t)k * st);
+        if constexpr (G::CH == 6) { v[2 * k] = c.x; v[2 * k + 1] = c.y; }
+        else { v[4 * k] = c.x; v[4 * k + 1] = c.y; v[4 * k + 2] = c.z; v[4 * k + 3] = c.w; }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) { r0[c] = {v[2 * c], v[2 * c + 1]}; r1[c] = {v[6 + 2 * c], v[7 + 2 * c]}; }
+    n = T(1);
+    if constexpr (G::NORM) {
+        const float *nrm = reinterpret_cast<const float *>(reinterpret_cast<const char *>(face) +
+                                                           (size_t)nf * st * 12 * sizeof(T));
+        n = __ldg(nrm + (size_t)f * st + i);
+    }
+}
+
+template <int PREC, typename T>
+__device__ __forceinline__ void face_store(void *face, int nf, int f, int st, int i, const C<T> r0[3], const C<T> r1[3],
+                                           float n)
+{
+    using G = FaceGeo<PREC>;
+    using FC = typename G::FC;
+    FC *p = reinterpret_cast<FC *>(face) + (size_t)f * G::CH * st + i;
+    T v[12];
+#pragma unroll
+    for (int c = 0; c < 3; c++) { v[2 * c] = r0[c].r; v[2 * c + 1] = r0[c].i; v[6 + 2 * c] = r1[c].r; v[7 + 2 * c] = r1[c].i; }
+#pragma unroll
+    for (int k = 0; k < G::CH; k++) {
+        FC c;
+        if constexpr (G::CH == 6) { c.x = v[2 * k]; c.y = v[2 * k + 1]; }
+        else { c.x = v[4 * k]; c.y = v[4 * k + 1]; c.z = v[4 * k + 2]; c.w = v[4 * k + 3]; }
+        p[(size_t)k * st] = c;
+    }
+    if constexpr (G::NORM) {
+        float *nrm = reinterpret_cast<float *>(reinterpret_cast<char *>(face) + (size_t)nf * st * 12 * sizeof(T));
+        nrm[(size_t)f * st + i] = n;
+    }
+}
+
+// The t hop of a slab-boundary site from a face: forward (FWD, rows = projected half-spinor,
+// multiplied by the local link U) or backward (rows = the neighbour's U^dag-multiplied rows).
+// The accumulation is hop_one's for mu = t, with the scale sign * (FP16) site norm.
+template <int PREC, int NF, bool FWD, typename T>
+__device__ __forceinline__ void ghost_hop(T (&acc)[NF][24], const Link<T> &U, const void *face, int st, int i, T sp,
+                                          T sign)
+{
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        C<T> r0[3], r1[3], w0[3], w1[3];
+        T n;
+        face_load<PREC, T>(face, NF, f, st, i, r0, r1, n);
+        if constexpr (FWD) {
+            link_mul<T, true>(U, r0, w0);
+            link_mul<T, true>(U, r1, w1);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { w0[c] = r0[c]; w1[c] = r1[c]; }
+        }
+        const T sg = (PREC == P16) ? sign * n : sign;
+        const T q = sg * sp;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            acc_add(acc[f], 2 * c, w0[c], sg);
+            acc_add(acc[f], 6 + 2 * c, w1[c], sg);
+            acc_add(acc[f], 12 + 2 * c, w0[c], q);
+            acc_add(acc[f], 18 + 2 * c, w1[c], q);
+        }
+    }
+}
+
+template <int PREC, int NF, int RECON, bool PRO, bool CLOV = false, bool PAIR = false, bool DD = false>
+__device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PREC>::real> &a0, int cb, int rhs,
+                                            const DDArgs<typename Traits<PREC>::real> *dd = nullptr)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
@@ -483,16 +591,24 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
         LinkLoader<PREC, RECON>::load(Gin + 2 * 2 * gpar, nb_, a.Vh, U);
         hop<PREC, NF, PRO, 2, false, PAIR>(acc, U, a, nb_, one);
     }
-    // ---- t (antiperiodic wrap when tbc)
+    // ---- t (antiperiodic wrap when tbc; a slab of a decomposed lattice reads faces instead)
     {
         const int s = a.X1h * a.Ly * a.Lz;
         const bool wf = (t == a.Lt - 1), wb = (t == 0);
-        const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
         LinkLoader<PREC, RECON>::load(Gout + 3 * 2 * gpar, cb, a.Vh, U);
-        hop<PREC, NF, PRO, 3, true, PAIR>(acc, U, a, nf_, (wf && a.tbc) ? -one : one);
-        const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
-        LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
-        hop<PREC, NF, PRO, 3, false, PAIR>(acc, U, a, nb_, (wb && a.tbc) ? -one : one);
+        if (DD && wf) {
+            if constexpr (DD) ghost_hop<PREC, NF, true>(acc, U, dd->ghost_f, s, cb - (a.Lt - 1) * s, -a.sigma, dd->sign_f);
+        } else {
+            const int nf_ = wf ? cb - (a.Lt - 1) * s : cb + s;
+            hop<PREC, NF, PRO, 3, true, PAIR>(acc, U, a, nf_, (wf && a.tbc) ? -one : one);
+        }
+        if (DD && wb) {
+            if constexpr (DD) ghost_hop<PREC, NF, false>(acc, U, dd->ghost_b, s, cb, a.sigma, dd->sign_b);
+        } else {
+            const int nb_ = wb ? cb + (a.Lt - 1) * s : cb - s;
+            LinkLoader<PREC, RECON>::load(Gin + 3 * 2 * gpar, nb_, a.Vh, U);
+            hop<PREC, NF, PRO, 3, false, PAIR>(acc, U, a, nb_, (wb && a.tbc) ? -one : one);
+        }
     }
 
     // ---- fused local epilogue
@@ -541,8 +657,8 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
 template <int PREC, int NF, int RECON, bool PRO>
 __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= a.Vh) return;
+    const int cb = a.cb0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.cb0 + a.ncb) return;
     dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
 }
 
@@ -552,9 +668,108 @@ __global__ void __launch_bounds__(256) k_dslash(const __grid_constant__ DslashAr
 template <int PREC, int NF, int RECON, bool PRO, int MINB, int BS = 128>
 __global__ void __launch_bounds__(BS, MINB) k_dslash_lb(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
 {
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= a.Vh) return;
+    const int cb = a.cb0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.cb0 + a.ncb) return;
     dslash_body<PREC, NF, RECON, PRO>(a, cb, 0);
+}
+
+// The boundary slices of a slab (decomposed lattice): thread i < st takes site i of the first
+// time slice, the others site i - st of the last one (Lt = 2: the whole slab).
+template <int PREC, int NF, int RECON, bool PRO>
+__global__ void __launch_bounds__(128, 4) k_dslash_dd(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a,
+                                                      const __grid_constant__ DDArgs<typename Traits<PREC>::real> dd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * dd.st) return;
+    const int cb = i < dd.st ? i : (a.Lt - 1) * dd.st + (i - dd.st);
+    dslash_body<PREC, NF, RECON, PRO, false, false, true>(a, cb, 0, &dd);
+}
+
+// Faces of a slab for its neighbours (blockIdx.y = 0: to the previous slab, from the first slice,
+// the projection (1 - s g_4) of the forward hop; 1: to the next slab, from the last slice,
+// U_t^dag (1 + s g_4) of the backward hop).  `a` describes the hopping launch the faces feed: its
+// input field (one parity), links, sigma and input twist (PRO); out_parity is the launch's.
+template <int PREC, int NF, int RECON, bool PRO>
+__global__ void __launch_bounds__(128) k_dd_pack(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a,
+                                                 void *face_prev, void *face_next)
+{
+    using T = typename Traits<PREC>::real;
+    using LL = LinkLayout<PREC, RECON>;
+    using LC = typename LL::chunk;
+    using SC = typename Traits<PREC>::schunk;
+    const int st = a.X1h * a.Ly * a.Lz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st) return;
+    const bool next = blockIdx.y == 1;
+    const int y = next ? (a.Lt - 1) * st + i : i;  // site of the input parity in this slab
+    const T sp = next ? a.sigma : -a.sigma;         // the receiver's backward / forward hop
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    const SC *in = reinterpret_cast<const SC *>(a.in);
+    T v[NF][24];
+    float n[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        n[f] = 1.f;
+        if constexpr (PRO) {
+            load_spinor<PREC>(in + f * fstride, a.in_norm ? a.in_norm + (size_t)f * a.Vh : nullptr, y, a.Vh, v[f]);
+        } else if constexpr (PREC == P16) {
+            n[f] = load_spinor_f16_unscaled(in + f * fstride, a.in_norm + (size_t)f * a.Vh, y, a.Vh, v[f]);
+        } else {
+            load_spinor<PREC>(in + f * fstride, nullptr, y, a.Vh, v[f]);
+        }
+    }
+    if constexpr (PRO) apply_twist<T, NF>(a.tw_pro, v);
+    Link<T> U;
+    if (next) {
+        const size_t gpar = (size_t)LL::N * a.Vh;
+        const LC *G = reinterpret_cast<const LC *>(a.gauge);
+        LinkLoader<PREC, RECON>::load(G + (size_t)(3 * 2 + (1 - a.out_parity)) * gpar, y, a.Vh, U);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        C<T> h0[3], h1[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {  // the projection of hop_one for mu = t
+            const C<T> p0 = {v[f][2 * c], v[f][2 * c + 1]}, p1 = {v[f][6 + 2 * c], v[f][7 + 2 * c]};
+            const C<T> p2 = {v[f][12 + 2 * c], v[f][13 + 2 * c]}, p3 = {v[f][18 + 2 * c], v[f][19 + 2 * c]};
+            h0[c] = cfma_s(sp, p2, p0);
+            h1[c] = cfma_s(sp, p3, p1);
+        }
+        if (next) {
+            C<T> w0[3], w1[3];
+            link_mul<T, false>(U, h0, w0);
+            link_mul<T, false>(U, h1, w1);
+            face_store<PREC, T>(face_next, NF, f, st, i, w0, w1, n[f]);
+        } else {
+            face_store<PREC, T>(face_prev, NF, f, st, i, h0, h1, n[f]);
+        }
+    }
+}
+
+template <int PREC>
+cudaError_t launch_dd_impl(const DslashArgs<typename Traits<PREC>::real> &a, const DDArgs<typename Traits<PREC>::real> *dd,
+                           void *face_prev, void *face_next, int nf, int recon, bool pro, cudaStream_t s)
+{
+    // dd != NULL: the boundary launch; else the face pack of the launch described by a
+    const int st = a.X1h * a.Ly * a.Lz;
+#define TM_DD1(NF, R, P)                                                                          \
+    if (dd) k_dslash_dd<PREC, NF, R, P><<<(2 * st + 127) / 128, 128, 0, s>>>(a, *dd);              \
+    else k_dd_pack<PREC, NF, R, P><<<dim3((st + 127) / 128, 2), 128, 0, s>>>(a, face_prev, face_next);
+#define TM_DDR(NF, P)                          \
+    switch (recon) {                           \
+    case 18: { TM_DD1(NF, 18, P) } break;      \
+    case 12: { TM_DD1(NF, 12, P) } break;      \
+    case 8: { TM_DD1(NF, 8, P) } break;        \
+    default: return cudaErrorInvalidValue;     \
+    }
+    if (nf == 1) {
+        if (pro) { TM_DDR(1, true) } else { TM_DDR(1, false) }
+    } else {
+        if (pro) { TM_DDR(2, true) } else { TM_DDR(2, false) }
+    }
+#undef TM_DDR
+#undef TM_DD1
+    return cudaGetLastError();
 }
 
 // Several right-hand sides in one launch (multi-RHS, sources share the gauge field).  A block
@@ -723,8 +938,8 @@ __global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ Dsl
     using LL = LinkLayout<PREC, RECON>;
     using LC = typename LL::chunk;
     using SC = typename Traits<PREC>::schunk;
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= a.Vh) return;
+    const int cb = a.cb0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= a.cb0 + a.ncb) return;
     int r = cb;
     const int xh = r % a.X1h;
     r /= a.X1h;
@@ -1089,8 +1304,8 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
 {
     extern __shared__ __align__(16) char smem_async[];
     const int tid = threadIdx.x;
-    const int cb = blockIdx.x * AsyncHop<PREC, RECON, NF>::BS + tid;
-    if (cb >= a.Vh) return;
+    const int cb = a.cb0 + blockIdx.x * AsyncHop<PREC, RECON, NF>::BS + tid;
+    if (cb >= a.cb0 + a.ncb) return;
     async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR>(a, cb, tid, smem_async, nullptr, nullptr);
 }
 
@@ -1167,7 +1382,7 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
         if (e != cudaSuccess) return e;
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR><<<(a.Vh + 127) / 128, 128, bytes, s>>>(a);
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR><<<(a.ncb + 127) / 128, 128, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1278,7 +1493,7 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
     if (variant == 3 || variant == 4 || variant == 5) {
         // register-capped launches, 128 registers per thread: 128 x 4, 64 x 8 or 256 x 2 blocks per SM
         const int bs = variant == 3 ? 128 : (variant == 4 ? 64 : 256);
-        const int gb = (a.Vh + bs - 1) / bs;
+        const int gb = (a.ncb + bs - 1) / bs;
 #define TM_LB1(NF, R, P)                                                                        \
     if (variant == 3) k_dslash_lb<PREC, NF, R, P, 4, 128><<<gb, 128, 0, s>>>(a);                 \
     else if (variant == 4) k_dslash_lb<PREC, NF, R, P, 8, 64><<<gb, 64, 0, s>>>(a);              \
@@ -1320,7 +1535,7 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
         }
 #undef TM_ASR
     }
-    const int grid = (a.Vh + block - 1) / block;
+    const int grid = (a.ncb + block - 1) / block;
     if (variant == 2 && !pro) {
 #define TM_PIPE(NF)                                                                 \
     switch (recon) {                                                                \

@@ -252,6 +252,7 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
         set_error("tm_force: the link derivative of the clover term is not implemented");
         return TM_ERR_ARG;
     }
+    if (g->dd) { set_error("tm_force: the handle holds one time slab of a decomposed lattice"); return TM_ERR_ARG; }
     const tm_field *fs[4] = {psi_e, psi_o, g_e, g_o};
     for (auto f : fs) {
         if (!f->data || f->prec != psi_e->prec || f->nrhs != 1 || (f->prec == TM_PREC_F16 && !f->norm)) {

@@ -68,6 +68,9 @@ struct tm_gauge {
     int fused_capacity;        // entries the device work list holds
     int *fused_sync;           // [0] error word, [1] work counter, [2] abort word, [3 + tile] A-tile flags
     unsigned long long wait_limit_ns;  // time limit of one bounded wait of the fused operator
+    int dd;                    // 1: the handle holds the time slab [dd_t0, dd_t0 + L[3]) of a decomposed lattice
+    int dd_t0, dd_Lt;          // slab offset and time extent of the whole lattice
+    double dd_sign_b, dd_sign_f;  // boundary signs of the faces from the previous / next slab
     size_t scratch_bytes;
 };
 

@@ -367,6 +367,7 @@ tm_status tm_solve(const tm_gauge *g, const tm_field *x_e, const tm_field *b_e, 
         return TM_ERR_ARG;
     }
     if (x_e->data == b_e->data) { set_error("tm_solve: x must not alias b"); return TM_ERR_ARG; }
+    if (g->dd) { set_error("tm_solve: the handle holds one time slab of a decomposed lattice"); return TM_ERR_ARG; }
     if (((uintptr_t)workspace & 255) != 0) { set_error("tm_solve: workspace must be 256-byte aligned"); return TM_ERR_ARG; }
     if (stats) memset(stats, 0, sizeof(*stats));
     return solve(g, x_e, b_e, sp, stats, workspace, workspace_bytes, (cudaStream_t)stream);
@@ -821,6 +822,7 @@ tm_status tm_solve_multi(const tm_gauge *g, const tm_field *x_e, const tm_field 
         return TM_ERR_ARG;
     }
     if (x_e->data == b_e->data) { set_error("tm_solve_multi: x must not alias b"); return TM_ERR_ARG; }
+    if (g->dd) { set_error("tm_solve_multi: the handle holds one time slab of a decomposed lattice"); return TM_ERR_ARG; }
     if (((uintptr_t)workspace & 255) != 0) { set_error("tm_solve_multi: workspace must be 256-byte aligned"); return TM_ERR_ARG; }
     const size_t need = multi_workspace_need(g, sp, x_e->nrhs);
     if (workspace_bytes < need) {
