@@ -182,6 +182,20 @@ tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const t
                                int pc, int dagger, const int *active_dev, int nactive, void *stream);
 
 /*
+ * Normal operator of the even-even system: out = A^dag A in with A = M_pc of tm_precond_op (pc),
+ * or A = M_pc^dag when dagger = 1 -- the operator CG iterates with (sec. 2.2, NORMOP).  Four fused
+ * launches.  For TM_PC_SYM without dagger (and no clover term) it is evaluated as
+ *   M_sym^dag M_sym = M_asym^dag (R_ee R_ee^dag)^-1 M_asym
+ * (M_sym = R_ee^-1 M_asym, eq. 2.2/2.3), so no launch needs the input-twist prologue that
+ * M_sym^dag alone has: (R R^dag)^-1 = ((1 + a^2 + b^2) + 2 b tau1 - 2 a b gamma5 tau2)^-1 for the
+ * doublet (a = 2 kappa mu, b = 2 kappa eps), 1 / (1 + a^2) for one flavour, is applied in the
+ * epilogue of the first M_asym.  tmp_e and tmp_o are overwritten.  Fields share a precision and
+ * nrhs (<= 64) and are distinct.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ */
+tm_status tm_normal_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_e,
+                       const tm_field *tmp_o, int pc, int dagger, void *stream);
+
+/*
  * Full unpreconditioned operator (eq. 2.1) on both parities: out = M in (dagger = 0) or
  * M^dag in.  Two fused launches; out must not alias in.
  */

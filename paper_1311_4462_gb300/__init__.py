@@ -173,6 +173,13 @@ def precond_op(gauge, out_e: Field, in_e: Field, tmp_o: Field, pc=TM_PC_ASYM, da
     return out_e
 
 
+def normal_op(gauge, out_e: Field, in_e: Field, tmp_e: Field, tmp_o: Field, pc=TM_PC_ASYM, dagger=False, stream=None):
+    """tm_normal_op: out_e = A^dag A in_e, A = M_pc (or M_pc^dag)."""
+    L.check(L.load().tm_normal_op(gauge.h, out_e.ref(), in_e.ref(), tmp_e.ref(), tmp_o.ref(), int(pc), int(dagger),
+                                  _stream(stream)))
+    return out_e
+
+
 def mat(gauge, out_e: Field, out_o: Field, in_e: Field, in_o: Field, dagger=False, stream=None):
     L.check(L.load().tm_mat(gauge.h, out_e.ref(), out_o.ref(), in_e.ref(), in_o.ref(), int(dagger), _stream(stream)))
     return out_e, out_o

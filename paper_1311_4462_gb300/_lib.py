@@ -65,6 +65,7 @@ _SIGS = {
     "tm_dslash_dagger": [vp, FP, FP, ctypes.c_int, ctypes.c_int, FP, vp],
     "tm_precond_op": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
     "tm_mat": [vp, FP, FP, FP, FP, ctypes.c_int, vp],
+    "tm_normal_op": [vp, FP, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
     "tm_prepare_rhs": [vp, FP, FP, FP, ctypes.c_int, ctypes.c_int, vp],
     "tm_reconstruct_odd": [vp, FP, FP, FP, ctypes.c_int, vp],
     "tm_twist": [vp, FP, FP, ctypes.c_int, ctypes.c_int, vp],

@@ -289,13 +289,14 @@ static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out
 // right-hand-side indices) the multi-RHS kernel processes those right-hand sides of the fields.
 tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x, int out_parity,
                         int dagger, int epi, double coef, const Twist<double> *tw_epi, const Twist<double> *tw_pro,
-                        cudaStream_t s, const int *act, int nact, int cb0 = 0, int ncb = 0)
+                        cudaStream_t s, const int *act, int nact, int cb0 = 0, int ncb = 0,
+                        const Twist<double> *tw_acc = nullptr)
 {
     const int pidx = prec_index(in->prec);
     const bool pro = tw_pro != nullptr;
     Twist<double> z;
     memset(&z, 0, sizeof(z));
-    const Twist<double> &te = tw_epi ? *tw_epi : z, &tp = tw_pro ? *tw_pro : z;
+    const Twist<double> &te = tw_epi ? *tw_epi : z, &tp = tw_pro ? *tw_pro : z, &ta = tw_acc ? *tw_acc : z;
     const tm_tune_entry tu = g->tune[pidx][pro ? 1 : 0];
     const bool multi = act != nullptr || nact > 1;
     cudaError_t e;
@@ -338,6 +339,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.coef = coef;
         a.tw_epi = te;
         a.tw_pro = tp;
+        a.tw_acc = ta;
         e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[0], s)
                   : launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
     } else if (pidx == 3) {
@@ -348,6 +350,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.coef = df64(coef);
         a.tw_epi = to_df64(te);
         a.tw_pro = to_df64(tp);
+        a.tw_acc = to_df64(ta);
         const int r = g->p.recon == 18 ? 18 : 12;
         if (pro) {
             set_error("DF64 has no input-twist prologue kernel (the operators apply that twist separately)");
@@ -364,6 +367,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.coef = (float)coef;
         a.tw_epi = to_float(te);
         a.tw_pro = to_float(tp);
+        a.tw_acc = to_float(ta);
         if (multi)
             e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[1], s)
                             : launch_dslash_multi_p16(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[2], s);
@@ -567,6 +571,59 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
     }
     TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 1, EPI_TW, 1.0, &Ri, &Ri, s, act, nact));
     return dslash_launch(g, out_e, tmp_o, in_e, 0, 1, EPI_XPAY, -k2, nullptr, nullptr, s, act, nact);
+}
+
+// Q = (R R^dag)^-1 per gamma5 block: a flavour matrix for the doublet,
+// (1 + a^2 + b^2) + 2 b tau1 - 2 a b gamma5 tau2 inverted; a real number 1 / (1 + a^2) for one flavour
+static Twist<double> rrdag_inverse(const tm_gauge *g)
+{
+    const Twist<double> R = make_twist(g, TW_R, 0);
+    Twist<double> Q;
+    memset(&Q, 0, sizeof(Q));
+    for (int gi = 0; gi < 2; gi++) {
+        const int n = g->nf;
+        C<double> P[2][2] = {};
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++)
+                for (int k = 0; k < n; k++) {  // P = R R^dag
+                    const C<double> r = R.m[gi][i][k], rc = {R.m[gi][j][k].r, -R.m[gi][j][k].i};
+                    P[i][j].r += r.r * rc.r - r.i * rc.i;
+                    P[i][j].i += r.r * rc.i + r.i * rc.r;
+                }
+        if (n == 1) {
+            Q.m[gi][0][0] = {1.0 / P[0][0].r, 0.0};  // R R^dag = |r|^2 is real
+        } else {
+            const C<double> det = {P[0][0].r * P[1][1].r - P[0][0].i * P[1][1].i - (P[0][1].r * P[1][0].r - P[0][1].i * P[1][0].i),
+                                   P[0][0].r * P[1][1].i + P[0][0].i * P[1][1].r - (P[0][1].r * P[1][0].i + P[0][1].i * P[1][0].r)};
+            const double d2 = det.r * det.r + det.i * det.i;
+            const C<double> inv = {det.r / d2, -det.i / d2};
+            auto mul = [&](C<double> a, double sgn) { return C<double>{sgn * (a.r * inv.r - a.i * inv.i), sgn * (a.r * inv.i + a.i * inv.r)}; };
+            Q.m[gi][0][0] = mul(P[1][1], 1.0);
+            Q.m[gi][1][1] = mul(P[0][0], 1.0);
+            Q.m[gi][0][1] = mul(P[0][1], -1.0);
+            Q.m[gi][1][0] = mul(P[1][0], -1.0);
+        }
+    }
+    return Q;
+}
+
+// out = A^dag A in with A = M_pc, or A = M_pc^dag when dagger (tm_normal_op).  For the symmetric
+// operator (no dagger, no clover term) M_sym = R_ee^-1 M_asym gives
+//   M_sym^dag M_sym = M_asym^dag (R_ee R_ee^dag)^-1 M_asym,
+// four launches without the input-twist prologue: M_asym with Q = (R R^dag)^-1 applied in the
+// epilogue of its second launch, then M_asym^dag.  te_e is overwritten with that intermediate.
+tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
+                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact)
+{
+    if (pc == TM_PC_SYM && !dagger && g->csw == 0.0) {
+        const double k2 = g->p.kappa * g->p.kappa;
+        const Twist<double> R = make_twist(g, TW_R, 0), Ri = make_twist(g, TW_RINV, 0), Q = rrdag_inverse(g);
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s, act, nact));
+        TM_TRY(dslash_launch(g, te_e, tmp_o, in_e, 0, 0, EPI_TWX_AXPY_TW, -k2, &R, nullptr, s, act, nact, 0, 0, &Q));
+        return precond_core(g, out_e, te_e, tmp_o, TM_PC_ASYM, 1, s, act, nact);
+    }
+    TM_TRY(precond_core(g, te_e, in_e, tmp_o, pc, dagger, s, act, nact));
+    return precond_core(g, out_e, te_e, tmp_o, pc, !dagger, s, act, nact);
 }
 
 // The kernel epilogue, coefficient and local operator of a tm_epilogue code (tm_dslash's mapping)
@@ -842,6 +899,28 @@ tm_status tm_precond_op_active(const tm_gauge *g, const tm_field *out_e, const t
         return TM_ERR_ARG;
     }
     return precond_core(g, out_e, in_e, tmp_o, pc, dagger, (cudaStream_t)stream, active_dev, nactive);
+}
+
+tm_status tm_normal_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_e,
+                       const tm_field *tmp_o, int pc, int dagger, void *stream)
+{
+    TM_NVTX("tm_normal_op");
+    if (!g) { set_error("null gauge handle"); return TM_ERR_ARG; }
+    TM_TRY(refuse_slab(g, "tm_normal_op"));
+    TM_TRY(check_field(g, out_e, "out_e"));
+    TM_TRY(check_field(g, in_e, "in_e"));
+    TM_TRY(check_field(g, tmp_e, "tmp_e"));
+    TM_TRY(check_field(g, tmp_o, "tmp_o"));
+    TM_TRY(same_prec(out_e, in_e, "tm_normal_op"));
+    TM_TRY(same_prec(out_e, tmp_e, "tm_normal_op"));
+    TM_TRY(same_prec(out_e, tmp_o, "tm_normal_op"));
+    if (out_e->nrhs > TM_MAX_RHS_API) { set_error("tm_normal_op: at most %d right-hand sides", TM_MAX_RHS_API); return TM_ERR_ARG; }
+    if (pc != TM_PC_ASYM && pc != TM_PC_SYM) { set_error("unknown pc %d", pc); return TM_ERR_ARG; }
+    const void *d[4] = {out_e->data, in_e->data, tmp_e->data, tmp_o->data};
+    for (int i = 0; i < 4; i++)
+        for (int j = i + 1; j < 4; j++)
+            if (d[i] == d[j]) { set_error("tm_normal_op: out_e, in_e, tmp_e and tmp_o must be distinct"); return TM_ERR_ARG; }
+    return normal_core(g, out_e, in_e, tmp_e, tmp_o, pc, dagger, (cudaStream_t)stream, nullptr, out_e->nrhs);
 }
 
 tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,

@@ -15,6 +15,8 @@
 //   EPI_X_TWAXPY   out = x + c T acc               x - kappa^2 R^-1_ee D_eo t  (eq. 2.3 LHS)
 //   EPI_XPAY       out = x + c acc
 //   EPI_TW_XPAY    out = T (x + c acc)             odd reconstruction, symmetric RHS
+//   EPI_TWX_AXPY_TW out = Q (T x + c acc)          (R R^dag)^-1 M_asym: the first factor of the
+//                                                  symmetric normal operator (Q = tw_acc)
 // and, as a compile-time option, a prologue that twists every neighbour spinor before the
 // projection (in -> T_pro in), which the adjoint of the symmetric operator needs.
 // For the doublet both flavours are computed by the same thread, so each link is loaded once
@@ -46,6 +48,7 @@ struct DslashArgs {
     T sigma;  // +1: H, -1: H^dag
     T coef;
     Twist<T> tw_epi, tw_pro;
+    Twist<T> tw_acc;         // Q of EPI_TWX_AXPY_TW
     const void *clov;        // clover handles: per-site local operator of this precision (tm_clover.cuh)
     const float *clov_norm;  // FP16 block scales
 };
@@ -628,12 +631,13 @@ __device__ __forceinline__ void dslash_body(const DslashArgs<typename Traits<PRE
 #pragma unroll
         for (int f = 0; f < NF; f++)
             load_spinor<PREC>(X + f * fstride, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv[f]);
-        if (epi == EPI_TWX_AXPY) {
+        if (epi == EPI_TWX_AXPY || epi == EPI_TWX_AXPY_TW) {
             local_op<PREC, NF, CLOV, false>(a, cb, xv);
 #pragma unroll
             for (int f = 0; f < NF; f++)
 #pragma unroll
                 for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
+            if (epi == EPI_TWX_AXPY_TW) apply_twist<T, NF>(a.tw_acc, acc);
         } else if (epi == EPI_X_TWAXPY) {
             local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
@@ -1003,7 +1007,7 @@ __global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ Dsl
 #pragma unroll
         for (int f = 0; f < NF; f++)
             load_spinor<PREC>(X + f * fstride, a.x_norm ? a.x_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, xv[f]);
-        if (epi == EPI_TWX_AXPY) {
+        if (epi == EPI_TWX_AXPY || epi == EPI_TWX_AXPY_TW) {
             apply_twist<T, NF>(a.tw_epi, xv);
         } else if (epi == EPI_X_TWAXPY) {
             apply_twist<T, NF>(a.tw_epi, acc);
@@ -1013,6 +1017,7 @@ __global__ void __launch_bounds__(256) k_dslash_pipe(const __grid_constant__ Dsl
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
         if (epi == EPI_TW_XPAY) apply_twist<T, NF>(a.tw_epi, acc);
+        else if (epi == EPI_TWX_AXPY_TW) apply_twist<T, NF>(a.tw_acc, acc);
     }
     SC *O = reinterpret_cast<SC *>(a.out);
 #pragma unroll
@@ -1285,13 +1290,14 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         T xv[NF][24];
         cp_wait<0>();
         async_read_x<PREC, RECON, NF>(xbuf, tid, xv);
-        if (epi == EPI_TWX_AXPY) local_op<PREC, NF, CLOV, false>(a, cb, xv);
+        if (epi == EPI_TWX_AXPY || epi == EPI_TWX_AXPY_TW) local_op<PREC, NF, CLOV, false>(a, cb, xv);
         else if (epi == EPI_X_TWAXPY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
         for (int f = 0; f < NF; f++)
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
         if (epi == EPI_TW_XPAY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
+        else if (epi == EPI_TWX_AXPY_TW) apply_twist<T, NF>(a.tw_acc, acc);
     }
     SC *O = reinterpret_cast<SC *>(a.out);
 #pragma unroll

@@ -23,7 +23,8 @@ enum Epilogue {
     EPI_TWX_AXPY = 2,  // out = T x + c acc
     EPI_X_TWAXPY = 3,  // out = x + c T acc
     EPI_XPAY = 4,      // out = x + c acc
-    EPI_TW_XPAY = 5    // out = T (x + c acc)
+    EPI_TW_XPAY = 5,   // out = T (x + c acc)
+    EPI_TWX_AXPY_TW = 6  // out = Q (T x + c acc), Q a second constant local matrix
 };
 
 // twist selector for host-built coefficient tables
@@ -36,6 +37,8 @@ size_t clover_bytes(int pidx, long Vh);
 // operator composition shared by the API and the solvers (tm_api.cu)
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact);
+tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
+                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact);
 }  // namespace tmk
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
@@ -88,4 +91,6 @@ size_t clover_bytes(int pidx, long Vh);
 // operator composition shared by the API and the solvers (tm_api.cu)
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact);
+tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
+                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact);
 }  // namespace tmk

@@ -131,9 +131,7 @@ class Solver {
     // out = A^dag A in with A = M_pc (or M_pc^dag when dagger)
     tm_status normal_op(const tm_field *out, const tm_field *in, const tm_field *te, const tm_field *to)
     {
-        tm_status st = tm_precond_op(g, te, in, to, sp->pc, sp->dagger, s);
-        if (st != TM_OK) return st;
-        return tm_precond_op(g, out, te, to, sp->pc, !sp->dagger, s);
+        return normal_core(g, out, in, te, to, sp->pc, sp->dagger, s, nullptr, 1);
     }
 };
 
@@ -544,9 +542,7 @@ class MultiSolver {
     }
     tm_status normal_op(const tm_field *out, const tm_field *in, const tm_field *te, const tm_field *to, int nact)
     {
-        tm_status st = precond_core(g, te, in, to, sp->pc, sp->dagger, s, d_list, nact);
-        if (st != TM_OK) return st;
-        return precond_core(g, out, te, to, sp->pc, !sp->dagger, s, d_list, nact);
+        return normal_core(g, out, in, te, to, sp->pc, sp->dagger, s, d_list, nact);
     }
 };
 

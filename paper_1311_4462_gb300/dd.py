@@ -159,6 +159,7 @@ class TorchDistTransport:
         torch = _torch()
         if t.device.type == "cpu":
             return t
+        key = (key, t.numel())  # one pinned buffer per role and size (faces of FP64, FP32, FP16 fields)
         if key not in self._stage:
             self._stage[key] = torch.empty(t.numel(), dtype=t.dtype).pin_memory()
         return self._stage[key]
