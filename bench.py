@@ -289,6 +289,7 @@ def run_ours(args, rank, world):
         result["l2_resident_16x16x16x32"] = l2_resident_section(tmq, dev, args)
         result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
+        result["multi_rhs"] = multi_rhs_section(tmq, U, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
         result["clover"] = clover_section(tmq, U, psi, dev, args)
         result["differentiation"] = force_section(tmq, dev, args)
@@ -721,6 +722,42 @@ def force_section(tmq, dev, args):
             "pseudofermion_action": {"forward_s": round(times[-1][0], 3), "backward_s": round(times[-1][1], 4),
                                      "solves": "two mixed FP32 CG solves to 1e-10 (M^dag z = phi, M X = z)",
                                      "S": float(S.detach())}}
+
+
+def multi_rhs_section(tmq, U, dev, args):
+    """The multi-RHS operator: M_asym on N = 16 right-hand sides (Z2 noise) in one launch per factor,
+    32^3x64, one flavour (kappa 0.1612, mu 0.004) and the doublet, FP32 and FP16 storage, recon 12,
+    autotuned launch shape; time per source against the single-RHS application.  Amortised bytes per
+    even site and source: 16 links x L x w / N + 5 spinor passes x S x N_f (the links are read once
+    per site for all N sources)."""
+    import torch
+    peak, _ = load_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    N = 16
+    rows, tables = [], {}
+    for nf, mu, eps in [(1, MU_DEG, 0.0), (2, MU_ND, EPS_ND)]:
+        p = tmq.Params(L_FULL, KAPPA, mu, eps, flavor=(tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS),
+                       recon=12)
+        g = tmq.Gauge(p, U)
+        tables["flavours_%d" % nf] = tmq.autotune(g)
+        for prec in (tmq.TM_PREC_F32, tmq.TM_PREC_F16):
+            xe = tmq.noise_z2(g, tmq.Field(g, prec, N), 0, 5000)
+            out, tmp = tmq.Field(g, prec, N), tmq.Field(g, prec, N)
+            ms = time_op(lambda: tmq.precond_op(g, out, xe, tmp, 0, False), 5, flush)
+            x1 = tmq.noise_z2(g, tmq.Field(g, prec), 0, 5000)
+            o1, t1 = tmq.Field(g, prec), tmq.Field(g, prec)
+            ms1 = time_op(lambda: tmq.precond_op(g, o1, x1, t1, 0, False), 10, flush)
+            by = (16 * link_reals(prec, 12) * REAL_BYTES[prec] / N + 5 * SPINOR_BYTES[prec] * nf) * p.Vh
+            gbs = by / (ms / N * 1e-3) / 1e9
+            rows.append({"flavours": nf, "prec": {4: "f32", 2: "f16"}[prec], "nrhs": N,
+                         "us_per_source": round(ms / N * 1e3, 1), "single_rhs_us": round(ms1 * 1e3, 1),
+                         "amortised_bytes_per_source": by, "amortised_gbs": round(gbs, 1),
+                         "hbm_frac": round(gbs / peak, 3),
+                         "gflops_per_source": round(FLOPS_PER_SITE[nf] * p.Vh / (ms / N * 1e-3) / 1e9, 1)})
+            del xe, out, tmp, x1, o1, t1
+        g.close()
+    return {"lattice": list(L_FULL), "operator": "M_asym (eq. 2.2 LHS), recon 12", "rows": rows,
+            "launch_tables": tables}
 
 
 def batching_section(tmq, U, dev, args):

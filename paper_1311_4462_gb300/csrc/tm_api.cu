@@ -1163,10 +1163,10 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             f[k].nrhs = nr;
         }
         const Twist<double> Ri = make_twist(g, TW_RINV, 0);
-        const int rpbs[3] = {2, 4, 8};
+        const int rpbs[5] = {2, 4, 8, 12, 14};
         float best = 1e30f;
         int bestr = g->multi_rpb[pi];
-        for (int ri = 0; ri < 3 && st == TM_OK; ri++) {
+        for (int ri = 0; ri < 5 && st == TM_OK; ri++) {
             g->multi_rpb[pi] = rpbs[ri];
             float ms = 0;
             for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -1244,7 +1244,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
         if (sscanf(p, "%3[a-z0-9]:m:%d%n", name, &block, &used) == 2 && used > 0) {
             // multi-RHS entry "<prec>:m:<right-hand sides per block>"
             const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-            if (pi < 0 || (block != 2 && block != 4 && block != 8)) {
+            if (pi < 0 || (block != 2 && block != 4 && block != 8 && block != 12 && block != 14)) {
                 set_error("tm_tune_import: invalid entry '%.32s'", p);
                 return TM_ERR_ARG;
             }

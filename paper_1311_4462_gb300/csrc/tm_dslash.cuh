@@ -801,31 +801,6 @@ __global__ void __launch_bounds__(32 * RPB, (PREC == PDF ? 1 : 16 / RPB))
     dslash_body<PREC, NF, RECON, PRO>(a, (int)cb, rhs);
 }
 
-template <int PREC>
-cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
-                                     const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
-{
-    if (rpb != 2 && rpb != 4 && rpb != 8) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + rpb - 1) / rpb));
-#define TM_M1(NF, R, P, B) k_dslash_multi<PREC, NF, R, P, B><<<grid, 32 * B, 0, s>>>(a, act, nact, nrhs)
-#define TM_M(NF, R, P)                     \
-    if (rpb == 2) TM_M1(NF, R, P, 2);      \
-    else if (rpb == 4) TM_M1(NF, R, P, 4); \
-    else TM_M1(NF, R, P, 8);
-#define TM_MR(NF, P)                                          \
-    if (recon == 18) { TM_M(NF, 18, P) }                      \
-    else if (recon == 12) { TM_M(NF, 12, P) }                 \
-    else { TM_M(NF, 8, P) }
-    if (nf == 1) {
-        if (pro) { TM_MR(1, true) } else { TM_MR(1, false) }
-    } else {
-        if (pro) { TM_MR(2, true) } else { TM_MR(2, false) }
-    }
-#undef TM_MR
-#undef TM_M
-#undef TM_M1
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------------------------------
 // Variant 2: the same computation as k_dslash with an explicit two-stage software pipeline:
@@ -1055,11 +1030,19 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem)
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(g), "n"(N) : "memory");
 }
+// the same copy allocating in L1 (links shared by the warps of a multi-RHS block)
+template <int N>
+__device__ __forceinline__ void cp_async_l1(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const size_t g = __cvta_generic_to_global(gmem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(g), "n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int PREC, int RECON, int NF>
+template <int PREC, int RECON, int NF, bool L1LINK = false>
 __device__ __forceinline__ void async_fetch_hop(char *buf, int tid, const typename LinkLayout<PREC, RECON>::chunk *g,
                                                 int lcb, const typename Traits<PREC>::schunk *in, const float *in_norm,
                                                 int nb, int Vh)
@@ -1070,7 +1053,10 @@ __device__ __forceinline__ void async_fetch_hop(char *buf, int tid, const typena
     LC *sl = reinterpret_cast<LC *>(buf);
     SC *ss = reinterpret_cast<SC *>(buf + H::LBYTES);
 #pragma unroll
-    for (int k = 0; k < H::NL; k++) cp_async<(int)sizeof(LC)>(sl + k * H::BS + tid, g + (size_t)k * Vh + lcb);
+    for (int k = 0; k < H::NL; k++) {
+        if constexpr (L1LINK) cp_async_l1<(int)sizeof(LC)>(sl + k * H::BS + tid, g + (size_t)k * Vh + lcb);
+        else cp_async<(int)sizeof(LC)>(sl + k * H::BS + tid, g + (size_t)k * Vh + lcb);
+    }
 #pragma unroll
     for (int k = 0; k < H::NS; k++) cp_async<16>(ss + k * H::BS + tid, in + (size_t)k * Vh + nb);
     if constexpr (H::NN > 0) {
@@ -1190,10 +1176,10 @@ __device__ __forceinline__ bool wait_flag(const int *f, int *sync, unsigned long
 // One site of the staged hop pipeline (launch forms 6 / 7 and the fused operator).  WAIT: the
 // input field is produced by other tiles of the same launch; before its first load the thread
 // waits for the completion flags of the 128-site tiles that hold its 8 neighbours.
-template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false>
+template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false, bool L1LINK = false>
 __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
                                            char *smem_async, const int *flags, int *sync,
-                                           unsigned long long limit_ns = 0)
+                                           unsigned long long limit_ns = 0, int rhs = 0)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
@@ -1213,7 +1199,10 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
     const size_t gpar = (size_t)LL::N * a.Vh;
     const LC *G = reinterpret_cast<const LC *>(a.gauge);
     const LC *Gout = G + (size_t)op * gpar, *Gin = G + (size_t)(1 - op) * gpar;
-    const SC *in = reinterpret_cast<const SC *>(a.in);
+    // right-hand side `rhs` of a multi-RHS field: its flavour blocks start at rhs * NF
+    const size_t boff = (size_t)rhs * NF * Traits<PREC>::SCHUNKS * a.Vh, noff = (size_t)rhs * NF * a.Vh;
+    const SC *in = reinterpret_cast<const SC *>(a.in) + boff;
+    const float *in_norm = a.in_norm ? a.in_norm + noff : nullptr;
     const int sy = a.X1h, sz = a.X1h * a.Ly, st = a.X1h * a.Ly * a.Lz;
     const int n0 = row + (((x == a.Lx - 1) ? 0 : x + 1) >> 1), n1 = row + (((x == 0) ? a.Lx - 1 : x - 1) >> 1);
     const int n2 = (y == a.Ly - 1) ? cb - (a.Ly - 1) * sy : cb + sy, n3 = (y == 0) ? cb + (a.Ly - 1) * sy : cb - sy;
@@ -1240,8 +1229,8 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
     auto fetch = [&](int h) {
         char *b = smem_async + (h % NB) * H::BUF;
         const int mu = h >> 1;
-        if ((h & 1) == 0) async_fetch_hop<PREC, RECON, NF>(b, tid, Gout + mu * m2, cb, in, a.in_norm, nbr[h], a.Vh);
-        else async_fetch_hop<PREC, RECON, NF>(b, tid, Gin + mu * m2, nbr[h], in, a.in_norm, nbr[h], a.Vh);
+        if ((h & 1) == 0) async_fetch_hop<PREC, RECON, NF, L1LINK>(b, tid, Gout + mu * m2, cb, in, in_norm, nbr[h], a.Vh);
+        else async_fetch_hop<PREC, RECON, NF, L1LINK>(b, tid, Gin + mu * m2, nbr[h], in, in_norm, nbr[h], a.Vh);
         cp_commit();
     };
 #pragma unroll
@@ -1272,7 +1261,8 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         else if (h + NB == 8) {
             // the epilogue input streams in, into the buffer hop h used, while the last hops compute
             if (needx) async_fetch_x<PREC, RECON, NF>(smem_async + (h % NB) * H::BUF, tid,
-                                                     reinterpret_cast<const SC *>(a.x), a.x_norm, cb, a.Vh);
+                                                     reinterpret_cast<const SC *>(a.x) + boff,
+                                                     a.x_norm ? a.x_norm + noff : nullptr, cb, a.Vh);
             cp_commit();
         }
     }
@@ -1299,10 +1289,11 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         if (epi == EPI_TW_XPAY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
         else if (epi == EPI_TWX_AXPY_TW) apply_twist<T, NF>(a.tw_acc, acc);
     }
-    SC *O = reinterpret_cast<SC *>(a.out);
+    SC *O = reinterpret_cast<SC *>(a.out) + boff;
+    float *out_norm = a.out_norm ? a.out_norm + noff : nullptr;
 #pragma unroll
     for (int f = 0; f < NF; f++)
-        store_spinor<PREC>(O + f * fstride, a.out_norm ? a.out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+        store_spinor<PREC>(O + f * fstride, out_norm ? out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
 }
 
 template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false>
@@ -1389,6 +1380,54 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
     k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR><<<(a.ncb + 127) / 128, 128, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Multi-RHS with the staged hop pipeline (multi-RHS launch forms 12 / 14): a 128-thread block is
+// 128 / RPB consecutive sites x RPB right-hand sides, a warp being 32 sites of one right-hand side
+// (its spinor chunks are one contiguous 512-byte request).  Every thread runs the two-buffer
+// staged pipeline of launch form 8 / 9 (paired hop where that form pairs) for its (site, source);
+// the link chunks are copied with L1 allocation, so the RPB warps that read the same links are
+// served by one trip to L2, and consecutive blocks take the next RPB sources of the same sites,
+// so links leave DRAM about once per site for all sources.
+template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
+__global__ void __launch_bounds__(128, 3)
+    k_dslash_multi_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act,
+                         int nact, int nrhs)
+{
+    extern __shared__ __align__(16) char smem_async[];
+    constexpr int WPR = 4 / RPB;  // warps per right-hand side
+    const int tid = threadIdx.x, w = tid >> 5;
+    const int ngrp = (nact + RPB - 1) / RPB;
+    const int grp = (int)(blockIdx.x % ngrp);
+    const long sblk = blockIdx.x / ngrp;
+    const int slot = grp * RPB + w / WPR;
+    const long cb = sblk * (32 * WPR) + (w % WPR) * 32 + (tid & 31);
+    if (slot >= nact || cb >= a.Vh) return;
+    const int rhs = act ? __ldg(act + slot) : slot;
+    if (rhs < 0 || rhs >= nrhs) return;  // an index outside the fields is skipped, never dereferenced
+    async_site<PREC, NF, RECON, false, 2, PRO, false, PAIR, true>(a, (int)cb, tid, smem_async, nullptr, nullptr, 0, rhs);
+}
+
+template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
+cudaError_t launch_multi_async(const DslashArgs<typename Traits<PREC>::real> &a, const int *act, int nact, int nrhs,
+                               cudaStream_t s)
+{
+    constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    constexpr int SPB = 128 / RPB;  // sites per block
+    const unsigned grid = (unsigned)(((long)a.Vh + SPB - 1) / SPB * ((nact + RPB - 1) / RPB));
+    k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR><<<grid, 128, bytes, s>>>(a, act, nact, nrhs);
     return cudaGetLastError();
 }
 
@@ -1569,6 +1608,57 @@ cudaError_t launch_dslash_impl(const DslashArgs<typename Traits<PREC>::real> &a,
     }
 #undef TM_RECON
 #undef TM_LAUNCH
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
+                                     const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
+{
+    if (rpb == 12 || rpb == 14) {
+        // staged multi-RHS forms, 2 or 4 right-hand sides per block; the hop pairs as form 8 / 9 does
+        // (binary32 and binary16, except one flavour with 18-real links)
+        constexpr bool CP = PREC == P32 || PREC == P16;
+#define TM_MA1(NF, R, P)                                                                                 \
+    {                                                                                                    \
+        constexpr bool PR = CP && (NF == 2 || R != 18);                                                  \
+        return rpb == 12 ? launch_multi_async<PREC, NF, R, P, 2, PR>(a, act, nact, nrhs, s)              \
+                         : launch_multi_async<PREC, NF, R, P, 4, PR>(a, act, nact, nrhs, s);             \
+    }
+#define TM_MAR(NF, P)                          \
+    switch (recon) {                           \
+    case 18: TM_MA1(NF, 18, P)                 \
+    case 12: TM_MA1(NF, 12, P)                 \
+    case 8: TM_MA1(NF, 8, P)                   \
+    default: return cudaErrorInvalidValue;     \
+    }
+        if (nf == 1) {
+            if (pro) { TM_MAR(1, true) } else { TM_MAR(1, false) }
+        } else {
+            if (pro) { TM_MAR(2, true) } else { TM_MAR(2, false) }
+        }
+#undef TM_MAR
+#undef TM_MA1
+    }
+    if (rpb != 2 && rpb != 4 && rpb != 8) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(((long)a.Vh + 31) / 32 * ((nact + rpb - 1) / rpb));
+#define TM_M1(NF, R, P, B) k_dslash_multi<PREC, NF, R, P, B><<<grid, 32 * B, 0, s>>>(a, act, nact, nrhs)
+#define TM_M(NF, R, P)                     \
+    if (rpb == 2) TM_M1(NF, R, P, 2);      \
+    else if (rpb == 4) TM_M1(NF, R, P, 4); \
+    else TM_M1(NF, R, P, 8);
+#define TM_MR(NF, P)                                          \
+    if (recon == 18) { TM_M(NF, 18, P) }                      \
+    else if (recon == 12) { TM_M(NF, 12, P) }                 \
+    else { TM_M(NF, 8, P) }
+    if (nf == 1) {
+        if (pro) { TM_MR(1, true) } else { TM_MR(1, false) }
+    } else {
+        if (pro) { TM_MR(2, true) } else { TM_MR(2, false) }
+    }
+#undef TM_MR
+#undef TM_M
+#undef TM_M1
     return cudaGetLastError();
 }
 

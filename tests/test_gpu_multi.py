@@ -32,7 +32,7 @@ def make(case, nrhs, recon=12):
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", [8, 4, 2])
-@pytest.mark.parametrize("rpb", [2, 4, 8], ids=["rpb2", "rpb4", "rpb8"])
+@pytest.mark.parametrize("rpb", [2, 4, 8, 12, 14], ids=["rpb2", "rpb4", "rpb8", "staged2", "staged4"])
 def test_multi_rhs_operators_match_oracle(case, prec, rpb):
     nr = 5  # not a multiple of any block shape: the last group of every shape is ragged
     tmq, p, po, U, g, src = make(case, nr)
