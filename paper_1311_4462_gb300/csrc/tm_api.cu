@@ -735,7 +735,9 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
         const bool nd = p->flavor == TM_NDEG_DOUBLET;
         if ((i == 1 || i == 2) && (nd || p->recon != 18))
             for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(nd && i == 1) ? 8 : 9, 128};
-        g->multi_rpb[i] = 4;
+        // multi-RHS shape, measured at 32^3x64 on 16 sources: the staged form with 4 sources per block
+        // for the binary32 / binary16 doublet, with 2 for one flavour; FP64 the register form, 4
+        g->multi_rpb[i] = (i == 1 || i == 2) ? (nd ? 14 : 12) : 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
     }

@@ -8,8 +8,9 @@
 // (bc = -1 on links across the antiperiodic time boundary), times a caller coefficient.
 // The twist R does not depend on U.  project = 1 returns the component in the tangent space
 // of SU(3) at U: P(G) = TA(G U^dag) U with TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6.
-// One thread per site computes its four links; the colour outer products are summed over spin
-// and flavour in registers and the 3x3 results are written in the canonical gauge layout.
+// One thread per site computes its four links; the colour outer products of spin-projected
+// half-spinors are summed over the two projected spin rows and the flavours in registers and the
+// 3x3 results are written in the canonical gauge layout.
 #include "tm_blas.cuh"
 #include "tm_core.cuh"
 #include "tm_internal.h"
@@ -27,33 +28,30 @@ struct ForceArgs {
     double coef;  // -kappa * caller coefficient
 };
 
-// (gamma_mu v)_s for the DeGrand-Rossi basis, returned as complex spin components
-template <typename T, int MU>
-__device__ __forceinline__ void gamma_apply(const C<T> v[4][3], C<T> o[4][3])
+// Both projectors are twice rank-2 hermitian projectors whose lower spin rows are a unitary image
+// of the upper ones, so a spin sum of an outer product with (1 -+ g_mu) collapses to the two
+// upper rows:  sum_s ((1 - g) a)_s b_s^dag = sum_{s=0,1} ((1 - g) a)_s ((1 - g) b)_s^dag  (and the
+// same with 1 + g).  The upper rows of (1 + sp g_mu) v are those of the hopping kernel's projection:
+//   mu = x: (v0 + sp i v3, v1 + sp i v2)    mu = y: (v0 - sp v3, v1 + sp v2)
+//   mu = z: (v0 + sp i v2, v1 - sp i v3)    mu = t: (v0 + sp v2, v1 + sp v3)
+template <int MU, typename T>
+__device__ __forceinline__ void project_upper(const C<T> v[4][3], T sp, C<T> h[2][3])
 {
-    const C<T> I1 = {T(0), T(1)};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
+        const C<T> p0 = v[0][c], p1 = v[1][c], p2 = v[2][c], p3 = v[3][c];
         if (MU == 0) {
-            o[0][c] = cmul(I1, v[3][c]);
-            o[1][c] = cmul(I1, v[2][c]);
-            o[2][c] = cscale(T(-1), cmul(I1, v[1][c]));
-            o[3][c] = cscale(T(-1), cmul(I1, v[0][c]));
+            h[0][c] = {p0.r - sp * p3.i, p0.i + sp * p3.r};
+            h[1][c] = {p1.r - sp * p2.i, p1.i + sp * p2.r};
         } else if (MU == 1) {
-            o[0][c] = cscale(T(-1), v[3][c]);
-            o[1][c] = v[2][c];
-            o[2][c] = v[1][c];
-            o[3][c] = cscale(T(-1), v[0][c]);
+            h[0][c] = {p0.r - sp * p3.r, p0.i - sp * p3.i};
+            h[1][c] = {p1.r + sp * p2.r, p1.i + sp * p2.i};
         } else if (MU == 2) {
-            o[0][c] = cmul(I1, v[2][c]);
-            o[1][c] = cscale(T(-1), cmul(I1, v[3][c]));
-            o[2][c] = cscale(T(-1), cmul(I1, v[0][c]));
-            o[3][c] = cmul(I1, v[1][c]);
+            h[0][c] = {p0.r - sp * p2.i, p0.i + sp * p2.r};
+            h[1][c] = {p1.r + sp * p3.i, p1.i - sp * p3.r};
         } else {
-            o[0][c] = v[2][c];
-            o[1][c] = v[3][c];
-            o[2][c] = v[0][c];
-            o[3][c] = v[1][c];
+            h[0][c] = {p0.r + sp * p2.r, p0.i + sp * p2.i};
+            h[1][c] = {p1.r + sp * p3.r, p1.i + sp * p3.i};
         }
     }
 }
@@ -72,21 +70,29 @@ __device__ __forceinline__ void load_sp(const void *base, const float *norm, int
         for (int c = 0; c < 3; c++) v[s][c] = {(T)r[2 * (3 * s + c)], (T)r[2 * (3 * s + c) + 1]};
 }
 
-// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
-// of the canonical output): psi(x) and g(x) are loaded once and reused by the four links
-// U_mu(x); each link's 3x3 gradient goes through shared memory so that the block writes its
-// contiguous run of the canonical layout with 16-byte stores.
-template <int PREC, int NF, typename T>
-__device__ __forceinline__ void load_site(const ForceArgs &a, const void *const *fld, const float *const *nrm, int par,
-                                          int cb, C<T> v[NF][4][3])
+// m += sum_{s=0,1} a_s b_s^dag (colour outer products of two projected half-spinors)
+template <typename T>
+__device__ __forceinline__ void outer_add(const C<T> a[2][3], const C<T> b[2][3], C<T> m[3][3])
 {
 #pragma unroll
-    for (int f = 0; f < NF; f++) load_sp<PREC>(fld[par], nrm[par], f, cb, a.Vh, v[f]);
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {  // a_i conj(b_j)
+                m[i][j].r = fma(a[s][i].r, b[s][j].r, fma(a[s][i].i, b[s][j].i, m[i][j].r));
+                m[i][j].i = fma(a[s][i].i, b[s][j].r, fma(-a[s][i].r, b[s][j].i, m[i][j].i));
+            }
 }
 
+// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
+// of the canonical output).  For each direction the thread reads psi(x), g(x) (L1 after the first
+// direction) and psi(x+mu), g(x+mu), projects them to half-spinors and sums the two outer
+// products; each link's 3x3 gradient goes through shared memory so that the block writes its
+// contiguous run of the canonical layout with 16-byte stores.
 template <int PREC, int RECON, int NF, int MU, typename T>
 __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int cb, int x, int y, int z, int t,
-                                              const C<T> (&px)[NF][4][3], const C<T> (&gx)[NF][4][3], C<T> m[3][3])
+                                              C<T> m[3][3])
 {
     int nb;
     T bc = T(1);
@@ -105,33 +111,19 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
         for (int j = 0; j < 3; j++) m[i][j] = {T(0), T(0)};
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-        C<T> w[4][3], q[4][3], tt[4][3];
-        // (1 - gamma) g(x), outer product with psi(x+mu)
-        gamma_apply<T, MU>(gx[f], tt);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) w[s][c] = csub(gx[f][s][c], tt[s][c]);
-        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, q);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(w[s][i], cconj(q[s][j])));
-        // psi(x), outer product with (1 + gamma) g(x+mu)
-        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, q);
-        gamma_apply<T, MU>(q, tt);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) w[s][c] = cadd(q[s][c], tt[s][c]);
-#pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) m[i][j] = cadd(m[i][j], cmul(px[f][s][i], cconj(w[s][j])));
+        C<T> v[4][3], ha[2][3], hb[2][3];
+        // sum_s ((1 - g) g(x))_s psi(x+mu)_s^dag
+        load_sp<PREC>(a.gv[par], a.gv_norm[par], f, cb, a.Vh, v);
+        project_upper<MU>(v, T(-1), ha);
+        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, v);
+        project_upper<MU>(v, T(-1), hb);
+        outer_add(ha, hb, m);
+        // sum_s psi(x)_s ((1 + g) g(x+mu))_s^dag
+        load_sp<PREC>(a.psi[par], a.psi_norm[par], f, cb, a.Vh, v);
+        project_upper<MU>(v, T(1), ha);
+        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, v);
+        project_upper<MU>(v, T(1), hb);
+        outer_add(ha, hb, m);
     }
     const T sc = (T)a.coef * bc;
 #pragma unroll
@@ -204,7 +196,7 @@ __device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long 
 }
 
 template <int PREC, int RECON, int NF, typename CT>
-__global__ void __launch_bounds__(128) k_force(const ForceArgs a)
+__global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __grid_constant__ ForceArgs a)
 {
     using T = typename Traits<PREC>::real;
     __shared__ __align__(16) CT tile[128 * 9];
@@ -213,7 +205,6 @@ __global__ void __launch_bounds__(128) k_force(const ForceArgs a)
     const long lex = lex0 + threadIdx.x;
     const bool valid = lex < V;  // every thread takes part in the block's barriers
     int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0;
-    C<T> px[NF][4][3], gx[NF][4][3];
     if (valid) {
         long r = lex;
         x = (int)(r % a.Lx);
@@ -224,17 +215,15 @@ __global__ void __launch_bounds__(128) k_force(const ForceArgs a)
         t = (int)(r / a.Lz);
         par = (x + y + z + t) & 1;
         cb = (int)(lex >> 1);
-        load_site<PREC, NF>(a, a.psi, a.psi_norm, par, cb, px);
-        load_site<PREC, NF>(a, a.gv, a.gv_norm, par, cb, gx);
     }
     C<T> m[3][3];
-    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, px, gx, m);
+    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
     store_links<0>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, px, gx, m);
+    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
     store_links<1>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, px, gx, m);
+    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
     store_links<2>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, px, gx, m);
+    if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m);
     store_links<3>(a, lex0, V, valid, m, tile);
 }
 
