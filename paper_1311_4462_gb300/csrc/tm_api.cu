@@ -7,6 +7,7 @@
 
 #include <vector>
 
+#include "tm_blas.cuh"
 #include "tm_dslash.cuh"
 #include "tm_internal.h"
 
@@ -77,6 +78,12 @@ cudaError_t launch_dd_p32(const DslashArgs<float> &a, const DDArgs<float> *dd, v
 cudaError_t launch_dd_p16(const DslashArgs<float> &a, const DDArgs<float> *dd, void *face_prev, void *face_next,
                           int nf, int recon, bool pro, cudaStream_t s);
 size_t dd_face_bytes(int prec, int nf, int st);
+cudaError_t launch_dslash_red_p64(const DslashArgs<double> &a, int nf, int recon, int variant, const RedArgs &red,
+                                  cudaStream_t s);
+cudaError_t launch_dslash_red_p32(const DslashArgs<float> &a, int nf, int recon, int variant, const RedArgs &red,
+                                  cudaStream_t s);
+cudaError_t launch_dslash_red_p16(const DslashArgs<float> &a, int nf, int recon, int variant, const RedArgs &red,
+                                  cudaStream_t s);
 
 static thread_local char g_err[512];
 constexpr int TM_MAX_RHS_API = 64;
@@ -607,14 +614,56 @@ static Twist<double> rrdag_inverse(const tm_gauge *g)
     return Q;
 }
 
+// Whether normal_core can fuse |A in|^2 into the epilogue of its second launch: single-RHS FP64 /
+// FP32 / FP16 fields, no clover term, A = M_pc (no dagger), the handle's no-prologue launch form a
+// staged one (variants 6 - 9), and room for one partial sum per block in the reduction scratch.
+bool normal_red_supported(const tm_gauge *g, int prec, int dagger)
+{
+    const int pidx = prec_index(prec);
+    if (pidx < 0 || pidx > 2 || dagger || g->csw != 0.0 || g->dd) return false;
+    const int v = g->tune[pidx][0].variant;
+    const size_t blocks = (size_t)(g->Vh + 127) / 128;
+    return v >= 6 && v <= 9 && blocks * sizeof(double) <= g->scratch_bytes - SCRATCH_PARTIALS_OFF;
+}
+
 // out = A^dag A in with A = M_pc, or A = M_pc^dag when dagger (tm_normal_op).  For the symmetric
 // operator (no dagger, no clover term) M_sym = R_ee^-1 M_asym gives
 //   M_sym^dag M_sym = M_asym^dag (R_ee R_ee^dag)^-1 M_asym,
 // four launches without the input-twist prologue: M_asym with Q = (R R^dag)^-1 applied in the
 // epilogue of its second launch, then M_asym^dag.  te_e is overwritten with that intermediate.
 tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
-                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact)
+                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact,
+                      const RedArgs *red)
 {
+    if (red) {
+        // |A in|^2 = <in, A^dag A in> from the epilogue of the second launch of A (the CG's <p, Ap>):
+        // for the symmetric operator Re<u, Q u> with u = M_asym in, since M_sym = R^-1 M_asym
+        if (!normal_red_supported(g, in_e->prec, dagger) || act || nact > 1 || in_e->nrhs != 1) {
+            set_error("internal: fused reduction not available for this operator");
+            return TM_ERR_ARG;
+        }
+        const int pidx = prec_index(in_e->prec);
+        const double k2 = g->p.kappa * g->p.kappa;
+        const Twist<double> R = make_twist(g, TW_R, 0), Ri = make_twist(g, TW_RINV, 0), Q = rrdag_inverse(g);
+        const bool sym = pc == TM_PC_SYM;
+        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s, nullptr, 1));
+        cudaError_t e;
+        const int variant = g->tune[pidx][0].variant;
+        if (pidx == 0) {
+            DslashArgs<double> a = pass_args<double>(g, te_e, tmp_o, in_e, 0, 0, sym ? EPI_TWX_AXPY_TW : EPI_TWX_AXPY,
+                                                     -k2, R, 0);
+            a.tw_acc = Q;
+            e = launch_dslash_red_p64(a, g->nf, g->p.recon, variant, *red, s);
+        } else {
+            DslashArgs<float> a = pass_args<float>(g, te_e, tmp_o, in_e, 0, 0, sym ? EPI_TWX_AXPY_TW : EPI_TWX_AXPY,
+                                                   -k2, to_float(R), pidx);
+            a.tw_acc = to_float(Q);
+            e = pidx == 1 ? launch_dslash_red_p32(a, g->nf, g->p.recon, variant, *red, s)
+                          : launch_dslash_red_p16(a, g->nf, g->p.recon, variant, *red, s);
+        }
+        TM_TRY(cuda_check(e, "fused-reduction launch"));
+        return precond_core(g, out_e, te_e, tmp_o, TM_PC_ASYM, 1, s, nullptr, 1);
+    }
     if (pc == TM_PC_SYM && !dagger && g->csw == 0.0) {
         const double k2 = g->p.kappa * g->p.kappa;
         const Twist<double> R = make_twist(g, TW_R, 0), Ri = make_twist(g, TW_RINV, 0), Q = rrdag_inverse(g);
@@ -922,7 +971,7 @@ tm_status tm_normal_op(const tm_gauge *g, const tm_field *out_e, const tm_field 
     for (int i = 0; i < 4; i++)
         for (int j = i + 1; j < 4; j++)
             if (d[i] == d[j]) { set_error("tm_normal_op: out_e, in_e, tmp_e and tmp_o must be distinct"); return TM_ERR_ARG; }
-    return normal_core(g, out_e, in_e, tmp_e, tmp_o, pc, dagger, (cudaStream_t)stream, nullptr, out_e->nrhs);
+    return normal_core(g, out_e, in_e, tmp_e, tmp_o, pc, dagger, (cudaStream_t)stream, nullptr, out_e->nrhs, nullptr);
 }
 
 tm_status tm_mat(const tm_gauge *g, const tm_field *out_e, const tm_field *out_o, const tm_field *in_e,

@@ -88,6 +88,65 @@ __device__ __forceinline__ void store_block(const FieldRef &f, long blk, int cb,
     }
 }
 
+// ---------------------------------------------------------------------------- reductions
+// (shared by the site-wise kernels and the hopping kernel's fused epilogue reduction)
+// Block-level sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Write this block's partial for column `col` (one column per rhs = blockIdx.y); the last block
+// of the whole grid sums every column in block order and applies `fin` per column.
+__device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
+{
+    const int col = blockIdx.y;
+    if (threadIdx.x == 0) r.partials[(size_t)col * gridDim.x + blockIdx.x] = part;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y;
+        last = (atomicAdd(r.counter, 1u) == total - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = threadIdx.x; c < (int)gridDim.y; c += blockDim.x) {
+        double s = 0.0;
+        const volatile double *pp = r.partials + (size_t)c * gridDim.x;
+        for (unsigned b = 0; b < gridDim.x; b++) s += pp[b];
+        double *S = r.scalars;
+        const int R = TM_MAX_RHS;
+        const bool active = !r.active || r.active[c];
+        switch (r.fin) {
+        case FIN_STORE: S[r.slot * R + c] = s; break;
+        case FIN_ALPHA:  // pAp -> alpha = rr / pAp
+            S[SL_PAP * R + c] = s;
+            S[SL_ALPHA * R + c] = (active && s != 0.0) ? S[SL_RR * R + c] / s : 0.0;
+            break;
+        case FIN_BETA:  // |r|^2 new -> beta = rr_new / rr, rr = rr_new
+            S[SL_RRNEW * R + c] = s;
+            S[SL_BETA * R + c] = (active && S[SL_RR * R + c] != 0.0) ? s / S[SL_RR * R + c] : 0.0;
+            if (active) S[SL_RR * R + c] = s;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) *r.counter = 0u;  // ready for the next launch on this stream
+}
+
 cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s);
 
 inline FieldRef fref(const tm_field *f) { return FieldRef{f->data, f->norm, f->prec}; }

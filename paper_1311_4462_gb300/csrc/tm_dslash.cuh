@@ -25,6 +25,7 @@
 #include <atomic>
 #include <type_traits>
 
+#include "tm_blas.cuh"
 #include "tm_clover.cuh"
 #include "tm_core.cuh"
 #include "tm_internal.h"
@@ -1173,13 +1174,28 @@ __device__ __forceinline__ bool wait_flag(const int *f, int *sync, unsigned long
     return false;
 }
 
+template <int PREC, int NF, typename T>
+__device__ __forceinline__ void store_out(const DslashArgs<T> &a, T (&acc)[NF][24], int cb, size_t boff, size_t noff)
+{
+    using SC = typename Traits<PREC>::schunk;
+    const size_t fstride = (size_t)Traits<PREC>::SCHUNKS * a.Vh;
+    SC *O = reinterpret_cast<SC *>(a.out) + boff;
+    float *out_norm = a.out_norm ? a.out_norm + noff : nullptr;
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+        store_spinor<PREC>(O + f * fstride, out_norm ? out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+}
+
 // One site of the staged hop pipeline (launch forms 6 / 7 and the fused operator).  WAIT: the
 // input field is produced by other tiles of the same launch; before its first load the thread
 // waits for the completion flags of the 128-site tiles that hold its 8 neighbours.
-template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false, bool L1LINK = false>
-__device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
-                                           char *smem_async, const int *flags, int *sync,
-                                           unsigned long long limit_ns = 0, int rhs = 0)
+// RED: the site's share of the fused reduction of the output, returned in FP64: |out|^2, or for
+// EPI_TWX_AXPY_TW Re<u, Q u> with u = T x + c acc (out = Q u); 0 otherwise.
+template <int PREC, int NF, int RECON, bool CLOV, int NB, bool PRO, bool WAIT, bool PAIR = false, bool L1LINK = false,
+          bool RED = false>
+__device__ __forceinline__ double async_site(const DslashArgs<typename Traits<PREC>::real> &a, int cb, int tid,
+                                             char *smem_async, const int *flags, int *sync,
+                                             unsigned long long limit_ns = 0, int rhs = 0)
 {
     using T = typename Traits<PREC>::real;
     using LL = LinkLayout<PREC, RECON>;
@@ -1224,7 +1240,7 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         bool ok = true;
 #pragma unroll
         for (int h = 0; h < 8; h++) ok = ok && wait_flag(flags + (nbr[h] >> 7), sync, limit_ns);
-        if (!ok) return;
+        if (!ok) return 0.0;
     }
     auto fetch = [&](int h) {
         char *b = smem_async + (h % NB) * H::BUF;
@@ -1286,24 +1302,64 @@ __device__ __forceinline__ void async_site(const DslashArgs<typename Traits<PREC
         for (int f = 0; f < NF; f++)
 #pragma unroll
             for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
-        if (epi == EPI_TW_XPAY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
-        else if (epi == EPI_TWX_AXPY_TW) apply_twist<T, NF>(a.tw_acc, acc);
-    }
-    SC *O = reinterpret_cast<SC *>(a.out) + boff;
-    float *out_norm = a.out_norm ? a.out_norm + noff : nullptr;
+        if (epi == EPI_TW_XPAY) {
+            local_op<PREC, NF, CLOV, true>(a, cb, acc);
+        } else if (epi == EPI_TWX_AXPY_TW) {
+            if constexpr (RED) {  // Re<u, Q u> (Q hermitian): u is acc before the twist
 #pragma unroll
-    for (int f = 0; f < NF; f++)
-        store_spinor<PREC>(O + f * fstride, out_norm ? out_norm + (size_t)f * a.Vh : nullptr, cb, a.Vh, acc[f]);
+                for (int f = 0; f < NF; f++)
+#pragma unroll
+                    for (int k = 0; k < 24; k++) xv[f][k] = acc[f][k];
+            }
+            apply_twist<T, NF>(a.tw_acc, acc);
+            if constexpr (RED) {
+                double part = 0.0;
+#pragma unroll
+                for (int f = 0; f < NF; f++) {
+                    T sf = T(0);
+#pragma unroll
+                    for (int k = 0; k < 24; k++) sf = fma(xv[f][k], acc[f][k], sf);
+                    part += (double)sf;
+                }
+                store_out<PREC, NF>(a, acc, cb, boff, noff);
+                return part;
+            }
+        }
+    }
+    store_out<PREC, NF>(a, acc, cb, boff, noff);
+    double part = 0.0;
+    if constexpr (RED) {
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            T sf = T(0);
+#pragma unroll
+            for (int k = 0; k < 24; k++) sf = fma(acc[f][k], acc[f][k], sf);
+            part += (double)sf;
+        }
+    }
+    return part;
 }
 
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false>
-__global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a)
+// RED: the launch also reduces its output (async_site) into red (the last block finishes the sum
+// in block order and applies red.fin, as the site-wise reductions do).
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false,
+          bool RED = false>
+__global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a,
+                                                            const __grid_constant__ RedArgs red)
 {
     extern __shared__ __align__(16) char smem_async[];
     const int tid = threadIdx.x;
     const int cb = a.cb0 + blockIdx.x * AsyncHop<PREC, RECON, NF>::BS + tid;
-    if (cb >= a.cb0 + a.ncb) return;
-    async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR>(a, cb, tid, smem_async, nullptr, nullptr);
+    if constexpr (!RED) {
+        if (cb >= a.cb0 + a.ncb) return;
+        async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR>(a, cb, tid, smem_async, nullptr, nullptr);
+    } else {
+        double part = 0.0;  // every thread reaches the block reduction
+        if (cb < a.cb0 + a.ncb)
+            part = async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR, false, true>(a, cb, tid, smem_async, nullptr,
+                                                                                          nullptr);
+        grid_finish(block_sum(part), red);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1364,8 +1420,9 @@ __global__ void __launch_bounds__(128, MINB)
 // The shared-memory opt-in is set once per kernel and device: the attribute call is not a
 // stream operation and can wait for work already queued on the device, so it must stay out of
 // the per-launch path (it would serialise copy streams with the compute stream).
-template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false>
-cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s)
+template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false,
+          bool RED = false>
+cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaStream_t s, const RedArgs *red = nullptr)
 {
     constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
     static std::atomic<unsigned long long> opted{0};  // bit d: done on device d (d < 64)
@@ -1374,12 +1431,15 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR>,
+        e = cudaFuncSetAttribute(k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR, RED>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR><<<(a.ncb + 127) / 128, 128, bytes, s>>>(a);
+    RedArgs r;
+    memset(&r, 0, sizeof(r));
+    if (red) r = *red;
+    k_dslash_async<PREC, NF, RECON, MINB, CLOV, NB, PRO, PAIR, RED><<<(a.ncb + 127) / 128, 128, bytes, s>>>(a, r);
     return cudaGetLastError();
 }
 
@@ -1527,6 +1587,31 @@ cudaError_t launch_staged(const DslashArgs<typename Traits<PREC>::real> &a, bool
                    : launch_async<PREC, NF, RECON, 3, false, 2, true, PAIR>(a, s);
     return nb3 ? launch_async<PREC, NF, RECON, 2, false, 3, false, PAIR>(a, s)
                : launch_async<PREC, NF, RECON, 3, false, 2, false, PAIR>(a, s);
+}
+
+// The staged forms (variants 6 - 9, no prologue) with the fused reduction of the output.
+template <int PREC>
+cudaError_t launch_dslash_red_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, int variant,
+                                   const RedArgs &red, cudaStream_t s)
+{
+    if (variant < 6 || variant > 9) return cudaErrorInvalidValue;
+    const bool nb3 = variant == 7 || variant == 9, pair = variant >= 8;
+    constexpr bool CP = PREC == P32 || PREC == P16;
+#define TM_RD2(NF, R, P)                                                                          \
+    return nb3 ? launch_async<PREC, NF, R, 2, false, 3, false, P, true>(a, s, &red)               \
+               : launch_async<PREC, NF, R, 3, false, 2, false, P, true>(a, s, &red);
+#define TM_RD1(NF, R) if (pair) { TM_RD2(NF, R, CP) } else { TM_RD2(NF, R, false) }
+#define TM_RDR(NF)                             \
+    switch (recon) {                           \
+    case 18: { TM_RD1(NF, 18) }                \
+    case 12: { TM_RD1(NF, 12) }                \
+    case 8: { TM_RD1(NF, 8) }                  \
+    default: return cudaErrorInvalidValue;     \
+    }
+    if (nf == 1) { TM_RDR(1) } else { TM_RDR(2) }
+#undef TM_RDR
+#undef TM_RD1
+#undef TM_RD2
 }
 
 // variant 0: one thread per site (both flavours); variant 2: the two-stage load pipeline (no

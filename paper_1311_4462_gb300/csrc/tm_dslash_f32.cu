@@ -8,4 +8,9 @@ cudaError_t launch_dslash_p32(const DslashArgs<float> &a, int nf, int recon, boo
 {
     return launch_dslash_impl<P32>(a, nf, recon, pro, variant, block, s);
 }
+cudaError_t launch_dslash_red_p32(const DslashArgs<float> &a, int nf, int recon, int variant, const RedArgs &red,
+                                  cudaStream_t s)
+{
+    return launch_dslash_red_impl<P32>(a, nf, recon, variant, red, s);
+}
 }  // namespace tmk

@@ -8,4 +8,9 @@ cudaError_t launch_dslash_p64(const DslashArgs<double> &a, int nf, int recon, bo
 {
     return launch_dslash_impl<P64>(a, nf, recon, pro, variant, block, s);
 }
+cudaError_t launch_dslash_red_p64(const DslashArgs<double> &a, int nf, int recon, int variant, const RedArgs &red,
+                                  cudaStream_t s)
+{
+    return launch_dslash_red_impl<P64>(a, nf, recon, variant, red, s);
+}
 }  // namespace tmk

@@ -8,7 +8,7 @@
 // (bc = -1 on links across the antiperiodic time boundary), times a caller coefficient.
 // The twist R does not depend on U.  project = 1 returns the component in the tangent space
 // of SU(3) at U: P(G) = TA(G U^dag) U with TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6.
-// One thread per site computes its four links; the colour outer products of spin-projected
+// One thread per link computes its gradient; the colour outer products of spin-projected
 // half-spinors are summed over the two projected spin rows and the flavours in registers and the
 // 3x3 results are written in the canonical gauge layout.
 #include "tm_blas.cuh"
@@ -85,11 +85,8 @@ __device__ __forceinline__ void outer_add(const C<T> a[2][3], const C<T> b[2][3]
             }
 }
 
-// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
-// of the canonical output).  For each direction the thread reads psi(x), g(x) (L1 after the first
-// direction) and psi(x+mu), g(x+mu), projects them to half-spinors and sums the two outer
-// products; each link's 3x3 gradient goes through shared memory so that the block writes its
-// contiguous run of the canonical layout with 16-byte stores.
+// The gradient of U_mu(x): psi(x), g(x), psi(x+mu) and g(x+mu) projected to half-spinors and the
+// two outer products summed, scaled, and (project) taken to the tangent space at U.
 template <int PREC, int RECON, int NF, int MU, typename T>
 __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int cb, int x, int y, int z, int t,
                                               C<T> m[3][3])
@@ -167,12 +164,37 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
     }
 }
 
-// the block's run of sites for direction MU: stage in shared memory, then 16-byte stores
-template <int MU, typename CT, typename T>
-__device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long V, bool valid, const C<T> m[3][3],
-                                           CT *tile)
+// One warp per (32 consecutive sites in lexicographic order, direction mu): warp mu of a block
+// computes U_mu(x) for the block's 32 sites, so the four directions of a site run in parallel and
+// share psi(x), g(x) through L1.  The warp stages its 32 x 9 results in shared memory and writes its
+// contiguous run of the canonical layout with 16-byte stores.
+template <int PREC, int RECON, int NF, typename CT>
+__global__ void __launch_bounds__(128, (PREC == P64 ? 3 : 5)) k_force(const __grid_constant__ ForceArgs a)
 {
-    if (valid) {
+    using T = typename Traits<PREC>::real;
+    __shared__ __align__(16) CT tile[4][32 * 9];
+    const long V = 2L * a.Vh;
+    const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+    const long lex0 = (long)blockIdx.x * 32;
+    const long lex = lex0 + lane;
+    CT *tw = tile[mu];
+    if (lex < V) {
+        long r = lex;
+        const int x = (int)(r % a.Lx);
+        r /= a.Lx;
+        const int y = (int)(r % a.Ly);
+        r /= a.Ly;
+        const int z = (int)(r % a.Lz);
+        const int t = (int)(r / a.Lz);
+        const int par = (x + y + z + t) & 1;
+        const int cb = (int)(lex >> 1);
+        C<T> m[3][3];
+        switch (mu) {  // warp-uniform
+        case 0: link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m); break;
+        case 1: link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m); break;
+        case 2: link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m); break;
+        default: link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m); break;
+        }
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -180,51 +202,18 @@ __device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long 
                 CT v;
                 v.x = m[i][j].r;
                 v.y = m[i][j].i;
-                tile[threadIdx.x * 9 + 3 * i + j] = v;
+                tw[lane * 9 + 3 * i + j] = v;
             }
     }
-    __syncthreads();
-    const long nsite = (V - lex0) < (long)blockDim.x ? (V - lex0) : (long)blockDim.x;
+    __syncwarp();
+    const long nsite = (V - lex0) < 32 ? (V - lex0) : 32;
     const long nvec = nsite * 9 * (long)sizeof(CT) / 16;  // 9 complex per site, a multiple of 16 bytes per 2 sites
-    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)MU * V + lex0) * 9);
-    const uint4 *src = reinterpret_cast<const uint4 *>(tile);
-    for (long k = threadIdx.x; k < nvec; k += blockDim.x) dst[k] = src[k];
+    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex0) * 9);
+    const uint4 *src = reinterpret_cast<const uint4 *>(tw);
+    for (long k = lane; k < nvec; k += 32) dst[k] = src[k];
     // an odd number of complex64 sites leaves 8 bytes: written element-wise
-    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && threadIdx.x == 0)
-        reinterpret_cast<CT *>(a.out)[((long)MU * V + lex0) * 9 + nsite * 9 - 1] = tile[nsite * 9 - 1];
-    __syncthreads();
-}
-
-template <int PREC, int RECON, int NF, typename CT>
-__global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __grid_constant__ ForceArgs a)
-{
-    using T = typename Traits<PREC>::real;
-    __shared__ __align__(16) CT tile[128 * 9];
-    const long V = 2L * a.Vh;
-    const long lex0 = (long)blockIdx.x * blockDim.x;
-    const long lex = lex0 + threadIdx.x;
-    const bool valid = lex < V;  // every thread takes part in the block's barriers
-    int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0;
-    if (valid) {
-        long r = lex;
-        x = (int)(r % a.Lx);
-        r /= a.Lx;
-        y = (int)(r % a.Ly);
-        r /= a.Ly;
-        z = (int)(r % a.Lz);
-        t = (int)(r / a.Lz);
-        par = (x + y + z + t) & 1;
-        cb = (int)(lex >> 1);
-    }
-    C<T> m[3][3];
-    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
-    store_links<0>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
-    store_links<1>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
-    store_links<2>(a, lex0, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m);
-    store_links<3>(a, lex0, V, valid, m, tile);
+    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && lane == 0)
+        reinterpret_cast<CT *>(a.out)[((long)mu * V + lex0) * 9 + nsite * 9 - 1] = tw[nsite * 9 - 1];
 }
 
 }  // namespace tmk
@@ -274,9 +263,9 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     a.gauge = g->links[pidx];
     a.out = F_canon;
     if (((uintptr_t)F_canon & 15) != 0) { set_error("tm_force: the output must be 16-byte aligned"); return TM_ERR_ARG; }
-    const long n = 2L * g->Vh;  // one thread per site
+    const long n = 2L * g->Vh;  // one warp per 32 sites and direction, four directions per block
     const int block = 128;
-    const long grid = (n + block - 1) / block;
+    const long grid = (n + 31) / 32;
     cudaStream_t s = (cudaStream_t)stream;
     const int recon = g->p.recon;
 #define TM_F1(P, R, CT) \

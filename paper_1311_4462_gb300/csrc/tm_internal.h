@@ -37,8 +37,11 @@ size_t clover_bytes(int pidx, long Vh);
 // operator composition shared by the API and the solvers (tm_api.cu)
 tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
                        int dagger, cudaStream_t s, const int *act, int nact);
+struct RedArgs;
 tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
-                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact);
+                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact,
+                      const RedArgs *red = nullptr);
+bool normal_red_supported(const tm_gauge *g, int prec, int dagger);
 }  // namespace tmk
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
@@ -84,13 +87,4 @@ int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
 size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);
 tm_status cuda_check(cudaError_t e, const char *what);
-// clover field of a handle (tm_clover.cu)
-tm_status clover_build(tm_gauge *g, double csw, cudaStream_t s);
-void clover_free(tm_gauge *g);
-size_t clover_bytes(int pidx, long Vh);
-// operator composition shared by the API and the solvers (tm_api.cu)
-tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
-                       int dagger, cudaStream_t s, const int *act, int nact);
-tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *te_e,
-                      const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact);
 }  // namespace tmk

@@ -133,6 +133,25 @@ class Solver {
     {
         return normal_core(g, out, in, te, to, sp->pc, sp->dagger, s, nullptr, 1);
     }
+    // out = A^dag A p and alpha = |r|^2 / <p, A^dag A p> in the scalar table.  Where the operator's
+    // launch form allows it, <p, A^dag A p> = |A p|^2 is summed in the epilogue of the launch that
+    // writes A p (sec. 2.1's local operations merged into the dslash kernels), which saves the
+    // separate pass over p and A^dag A p.
+    tm_status normal_op_alpha(const tm_field *out, const tm_field *p, const tm_field *te, const tm_field *to)
+    {
+        if (!normal_red_supported(g, p->prec, sp->dagger)) {
+            tm_status st = normal_op(out, p, te, to);
+            if (st != TM_OK) return st;
+            return site(OP_DOT, fref(p), fref(out), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0);
+        }
+        RedArgs r;
+        memset(&r, 0, sizeof(r));
+        r.partials = reinterpret_cast<double *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_PARTIALS_OFF);
+        r.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_COUNTER_OFF);
+        r.scalars = S;
+        r.fin = FIN_ALPHA;
+        return normal_core(g, out, p, te, to, sp->pc, sp->dagger, s, nullptr, 1, &r);
+    }
 };
 
 static tm_status check_solver_params(const tm_gauge *g, const tm_solver_params *sp)
@@ -244,8 +263,7 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
             TRY(V.copy(&p, &r));
             rr = r2;
             while (rr > tol2 * bb && it < sp->maxiter) {
-                TRY(V.normal_op(&Ap, &p, &te, &to));
-                TRY(V.site(OP_DOT, fref(&p), fref(&Ap), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0));
+                TRY(V.normal_op_alpha(&Ap, &p, &te, &to));
                 TRY(V.site(OP_CG_UPDATE, fref(&p), fref(&r), fref(x), fref(&Ap), sslot(SL_ALPHA, 1.0), sv(0), 1,
                            FIN_BETA, 0));
                 TRY(V.read(SL_RRNEW, &rr));
@@ -272,8 +290,7 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
         double maxr = sqrt(r2);
         bool converged = r2 <= tol2 * bb;
         while (!converged && it < sp->maxiter) {
-            TRY(V.normal_op(&Aps, &ps, &tes, &tos));
-            TRY(V.site(OP_DOT, fref(&ps), fref(&Aps), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0));
+            TRY(V.normal_op_alpha(&Aps, &ps, &tes, &tos));
             TRY(V.site(OP_CG_UPDATE, fref(&ps), fref(&rs), fref(&xs), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
                        FIN_STORE, SL_RRNEW));
             TRY(V.read(SL_RRNEW, &rr));

@@ -188,3 +188,23 @@ def test_df64_cg_to_1e12():
     psi, st = full_solve(tmq, g, b, 0, False, solver="cg", tol=1e-12, maxiter=5000, true_prec=tmq.TM_PREC_DF64)
     assert st["status"] == 0 and st["true_residual"] <= 1e-12
     assert rel(orc.apply_M(po, U, psi), b) < 1e-8
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
+@pytest.mark.parametrize("sloppy", [4, 2], ids=["f32", "f16"])
+def test_fused_pap_matches_the_separate_reduction(case, pc, sloppy):
+    """<p, A^dag A p> summed in the hopping epilogue (staged launch forms) or by a separate pass
+    (register-capped form): both mixed solves converge to the same solution."""
+    tmq, p, po, U, g, b = setup(case)
+    name = {4: "f32", 2: "f16"}[sloppy]
+    saved = tmq.tune_export(g)
+    sols = []
+    for table in (f"{name}:0:{8 if p.nf == 2 else 9}:128", f"{name}:0:3:128"):
+        tmq.tune_import(g, table)
+        psi, st = full_solve(tmq, g, b, pc, False, solver="mixed", sloppy_prec=sloppy, tol=1e-10, maxiter=5000)
+        assert st["true_residual"] <= 1e-10
+        assert rel(orc.apply_M(po, U, psi), b) < 1e-7
+        sols.append(psi)
+    tmq.tune_import(g, saved)
+    assert rel(sols[0], sols[1]) < 1e-7
