@@ -124,6 +124,12 @@ tm_status tm_last_error(char *buf, size_t n);
  */
 tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out);
 
+/* tm_gauge_create packing only the link storage forms in prec_mask: bit 0 FP64, 1 FP32, 2 FP16,
+ * 3 DF64 (0 = all, as tm_gauge_create).  An operator, solver or force call on fields of a storage
+ * form the handle did not pack returns TM_ERR_ARG; a clover term needs the FP64 links.  32^3x64,
+ * recon 12: FP64 805 MB, FP32 403 MB, FP16 201 MB, DF64 805 MB. */
+tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_mask, void *stream, tm_gauge **out);
+
 /* Release a handle (NULL is accepted).  Waits for the device to finish using it. */
 tm_status tm_gauge_destroy(tm_gauge *g);
 

@@ -71,7 +71,8 @@ class Params:
 class Gauge:
     """tm_gauge handle: packed links in FP64/FP32/FP16 (the handle's recon) on the current device."""
 
-    def __init__(self, params: Params, U, stream=None):
+    def __init__(self, params: Params, U, stream=None, precs=None):
+        """precs: the storage precisions whose links to pack (None: all; tm_gauge_create_ex)."""
         torch = _torch()
         self.params = params
         self.csw = 0.0
@@ -82,8 +83,10 @@ class Gauge:
         assert tuple(U.shape) == params.gauge_shape, (U.shape, params.gauge_shape)
         h = ctypes.c_void_p()
         self._pc = params.c()
-        L.check(L.load().tm_gauge_create(ctypes.byref(self._pc), ctypes.c_void_p(U.data_ptr()), _stream(stream),
-                                         ctypes.byref(h)))
+        bit = {TM_PREC_F64: 1, TM_PREC_F32: 2, TM_PREC_F16: 4, TM_PREC_DF64: 8}
+        mask = 0 if precs is None else sum(bit[int(q)] for q in set(precs))
+        L.check(L.load().tm_gauge_create_ex(ctypes.byref(self._pc), ctypes.c_void_p(U.data_ptr()), int(mask),
+                                            _stream(stream), ctypes.byref(h)))
         self.h = h
 
     def close(self):

@@ -56,6 +56,7 @@ FP = ctypes.POINTER(tm_field)
 _SIGS = {
     "tm_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     "tm_gauge_create": [ctypes.POINTER(tm_params), vp, vp, ctypes.POINTER(vp)],
+    "tm_gauge_create_ex": [ctypes.POINTER(tm_params), vp, ctypes.c_int, vp, ctypes.POINTER(vp)],
     "tm_gauge_destroy": [vp],
     "tm_field_bytes": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
                        ctypes.POINTER(ctypes.c_size_t)],

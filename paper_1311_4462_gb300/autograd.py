@@ -14,7 +14,7 @@ on field values is a library call; this module only packs, unpacks and sequences
 
 Gauge handles are reused while U is unchanged: a handle is kept per parameter set together with a
 weak reference to its U and U's version counter, so repeated calls with the same (unmodified) U pack
-the links once.  A handle dropped from the cache stays alive while an autograd graph still holds it.
+the links once, and only in the storage precisions the call computes in (tm_gauge_create_ex).  A handle dropped from the cache stays alive while an autograd graph still holds it.
 """
 from __future__ import annotations
 
@@ -29,18 +29,19 @@ _CACHE: dict = {}   # params key -> (weakref to U, U._version, Gauge)
 _CACHE_MAX = 2
 
 
-def _key(params: Params, U):
+def _key(params: Params, U, precs):
     return (params.L, params.kappa, params.mu, params.eps, params.flavor, params.t_antiperiodic, params.recon,
-            U.device.index)
+            U.device.index, tuple(sorted(precs)))
 
 
-def gauge_for(U, params: Params) -> Gauge:
-    """The cached handle of (U, params), created when U is new or was modified in place."""
-    k = _key(params, U)
+def gauge_for(U, params: Params, precs=(TM_PREC_F64, TM_PREC_F32)) -> Gauge:
+    """The cached handle of (U, params) holding the links of `precs` only, created when U is new or
+    was modified in place."""
+    k = _key(params, U, precs)
     hit = _CACHE.get(k)
     if hit is not None and hit[0]() is U and hit[1] == U._version:
         return hit[2]
-    g = Gauge(params, U.detach())
+    g = Gauge(params, U.detach(), precs=precs)
     _CACHE.pop(k, None)
     while len(_CACHE) >= _CACHE_MAX:
         _CACHE.pop(next(iter(_CACHE)))
@@ -71,7 +72,7 @@ class TMApply(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, U, psi, params: Params):
-        g = gauge_for(U, params)
+        g = gauge_for(U, params, (_prec(psi),))
         y = _apply_full(g, psi.detach(), False, _prec(psi))
         ctx.save_for_backward(psi)
         ctx.g, ctx.U_dtype = g, U.dtype
@@ -123,7 +124,7 @@ class PseudofermionAction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, U, phi, params: Params, tol=1e-12, solver="cg"):
-        g = gauge_for(U, params)
+        g = gauge_for(U, params, (TM_PREC_F64, TM_PREC_F32) if solver == "mixed" else (TM_PREC_F64,))
         phi64 = phi.detach().to(torch.complex128)
         pe, po = pack(g, phi64, 0, TM_PREC_F64), pack(g, phi64, 1, TM_PREC_F64)
         ye, yo, _ = solve_fields(g, pe, po, dagger=True, tol=tol, solver=solver)  # Y = M^-dag phi

@@ -266,6 +266,17 @@ static tm_status check_params(const tm_params *p)
     return TM_OK;
 }
 
+// A handle made with tm_gauge_create_ex packs only the link precisions of its mask.
+tm_status need_links(const tm_gauge *g, int prec)
+{
+    const int pidx = prec_index(prec);
+    if (pidx < 0 || !g->links[pidx]) {
+        set_error("the handle holds no links for storage precision %d (tm_gauge_create_ex mask)", prec);
+        return TM_ERR_ARG;
+    }
+    return TM_OK;
+}
+
 // ------------------------------------------------------------------------------- dslash core
 template <typename T>
 static void fill_common(DslashArgs<T> &a, const tm_gauge *g, const tm_field *out, const tm_field *in,
@@ -300,6 +311,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
                         const Twist<double> *tw_acc = nullptr)
 {
     const int pidx = prec_index(in->prec);
+    if (need_links(g, in->prec) != TM_OK) return TM_ERR_ARG;
     const bool pro = tw_pro != nullptr;
     Twist<double> z;
     memset(&z, 0, sizeof(z));
@@ -544,7 +556,7 @@ tm_status precond_core(const tm_gauge *g, const tm_field *out_e, const tm_field 
     {
         const int pidx = prec_index(out_e->prec);
         if ((pidx == 0 || pidx == 1) && g->fused[pidx] && g->csw == 0.0 && act == nullptr && nact <= 1 &&
-            out_e->nrhs == 1 && !(pc == TM_PC_SYM && dagger) && g->fused_sync)
+            out_e->nrhs == 1 && !(pc == TM_PC_SYM && dagger) && g->fused_sync && g->links[pidx])
             return fused_launch(g, out_e, in_e, tmp_o, pc, dagger, s);
     }
     const double k2 = g->p.kappa * g->p.kappa;
@@ -620,7 +632,7 @@ static Twist<double> rrdag_inverse(const tm_gauge *g)
 bool normal_red_supported(const tm_gauge *g, int prec, int dagger)
 {
     const int pidx = prec_index(prec);
-    if (pidx < 0 || pidx > 2 || dagger || g->csw != 0.0 || g->dd) return false;
+    if (pidx < 0 || pidx > 2 || dagger || g->csw != 0.0 || g->dd || !g->links[pidx]) return false;
     const int v = g->tune[pidx][0].variant;
     const size_t blocks = (size_t)(g->Vh + 127) / 128;
     return v >= 6 && v <= 9 && blocks * sizeof(double) <= g->scratch_bytes - SCRATCH_PARTIALS_OFF;
@@ -721,6 +733,7 @@ static tm_status dd_call(const tm_gauge *g, const tm_field *out, const tm_field 
                          const void *ghost_prev, const void *ghost_next, void *face_prev, void *face_next, cudaStream_t s)
 {
     const int pidx = prec_index(in->prec);
+    TM_TRY(need_links(g, in->prec));
     DslashArgs<T> a;
     memset(&a, 0, sizeof(a));
     fill_common(a, g, out ? out : in, in, x, out_parity, pidx);
@@ -764,7 +777,14 @@ tm_status tm_last_error(char *buf, size_t n)
 
 tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out)
 {
+    return tm_gauge_create_ex(p, U_canon, 0, stream, out);
+}
+
+tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_mask, void *stream, tm_gauge **out)
+{
     TM_NVTX("tm_gauge_create");
+    if (prec_mask < 0 || prec_mask > 15) { set_error("tm_gauge_create_ex: prec_mask must be in [0, 15]"); return TM_ERR_ARG; }
+    if (prec_mask == 0) prec_mask = 15;
     TM_TRY(check_params(p));
     if (!U_canon || !out) { set_error("tm_gauge_create: null pointer"); return TM_ERR_ARG; }
     *out = nullptr;
@@ -803,6 +823,7 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
                                      "cudaDeviceGetAttribute");
     const int precs[4] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64};
     for (int i = 0; i < 4 && st == TM_OK; i++) {
+        if (!(prec_mask & (1 << i))) continue;  // this storage form is not packed: its operators are refused
         const int recon_i = (precs[i] == TM_PREC_DF64 && p->recon == 8) ? 12 : p->recon;
         const size_t per_link = (size_t)recon_i * real_bytes(precs[i]);
         const size_t chunks = per_link / link_chunk_bytes(precs[i], recon_i);
@@ -1098,6 +1119,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
     if (st == TM_OK) st = cuda_check(cudaEventCreate(&e0), "event");
     if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
     for (int pi = 0; pi < 3 && st == TM_OK; pi++) {
+        if (!g->links[pi]) continue;  // not packed on this handle
         // one FP64-sized buffer per field holds any precision; FP16 norms sit in the tail
         tm_field_bytes(g, precs[pi], 1, &d, &n);
         tm_field f[3];
@@ -1165,6 +1187,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
     }
     // fused operator or two launches, timed on the asymmetric operator (FP64, FP32)
     for (int pi = 0; pi < 2 && st == TM_OK; pi++) {
+        if (!g->links[pi]) continue;
         tm_field_bytes(g, precs[pi], 1, &d, &n);
         tm_field f[3];
         for (int k = 0; k < 3; k++) {
@@ -1197,6 +1220,7 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
     // multi-RHS block shape (right-hand sides per block), timed on 8 right-hand sides of the
     // single-RHS buffers' size each: the fields are carved from one allocation of 3 x 8 fields
     for (int pi = 0; pi < 3 && st == TM_OK; pi++) {
+        if (!g->links[pi]) continue;
         const int nr = 8;
         tm_field_bytes(g, precs[pi], nr, &d, &n);
         const size_t fbm = ((d + 255) & ~(size_t)255) + ((n + 255) & ~(size_t)255);

@@ -124,10 +124,15 @@ __device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int c = threadIdx.x; c < (int)gridDim.y; c += blockDim.x) {
+    // the last block sums each column: thread t the partials t, t + blockDim, ... in order, then the
+    // block tree -- a fixed order for a given grid, so the result is reproducible
+    for (int c = 0; c < (int)gridDim.y; c++) {
         double s = 0.0;
         const volatile double *pp = r.partials + (size_t)c * gridDim.x;
-        for (unsigned b = 0; b < gridDim.x; b++) s += pp[b];
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += pp[b];
+        s = block_sum(s);
+        __syncthreads();  // block_sum's shared slots are reused by the next column
+        if (threadIdx.x != 0) continue;
         double *S = r.scalars;
         const int R = TM_MAX_RHS;
         const bool active = !r.active || r.active[c];

@@ -366,6 +366,10 @@ tm_status clover_build(tm_gauge *g, double csw, cudaStream_t s)
     }
     const double ta = 2.0 * g->p.kappa * g->p.mu, tb = 2.0 * g->p.kappa * g->p.epsilon;
     a.x2 = (g->nf == 2) ? (tb * tb - ta * ta) : -ta * ta;
+    if (!g->links[0]) {
+        set_error("clover: the clover field is built from the FP64 links, which this handle did not pack");
+        return TM_ERR_ARG;
+    }
     a.links = g->links[0];
     a.Vh = g->Vh;
     a.X1h = g->X1h;

@@ -11,8 +11,11 @@
 // One thread per link computes its gradient; the colour outer products of spin-projected
 // half-spinors are summed over the two projected spin rows and the flavours in registers and the
 // 3x3 results are written in the canonical gauge layout.
+#include <atomic>
+
 #include "tm_blas.cuh"
 #include "tm_core.cuh"
+#include "tm_dslash.cuh"
 #include "tm_internal.h"
 
 namespace tmk {
@@ -85,23 +88,25 @@ __device__ __forceinline__ void outer_add(const C<T> a[2][3], const C<T> b[2][3]
             }
 }
 
-// The gradient of U_mu(x): psi(x), g(x), psi(x+mu) and g(x+mu) projected to half-spinors and the
-// two outer products summed, scaled, and (project) taken to the tangent space at U.
-template <int PREC, int RECON, int NF, int MU, typename T>
-__device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int cb, int x, int y, int z, int t,
-                                              C<T> m[3][3])
+// neighbour x + mu of site (x, y, z, t) with checkerboard index cb, and the boundary sign
+template <int MU, typename T>
+__device__ __forceinline__ int force_neighbour(const ForceArgs &a, int cb, int x, int y, int z, int t, T &bc)
 {
-    int nb;
-    T bc = T(1);
-    const int xh = x >> 1;
-    if (MU == 0) nb = (cb - xh) + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
-    else if (MU == 1) nb = (y == a.Ly - 1) ? cb - (a.Ly - 1) * a.X1h : cb + a.X1h;
-    else if (MU == 2) nb = (z == a.Lz - 1) ? cb - (a.Lz - 1) * a.X1h * a.Ly : cb + a.X1h * a.Ly;
-    else {
-        const int s = a.X1h * a.Ly * a.Lz;
-        nb = (t == a.Lt - 1) ? cb - (a.Lt - 1) * s : cb + s;
-        if (t == a.Lt - 1 && a.tbc) bc = T(-1);
-    }
+    bc = T(1);
+    if (MU == 0) return (cb - (x >> 1)) + (((x == a.Lx - 1) ? 0 : x + 1) >> 1);
+    if (MU == 1) return (y == a.Ly - 1) ? cb - (a.Ly - 1) * a.X1h : cb + a.X1h;
+    if (MU == 2) return (z == a.Lz - 1) ? cb - (a.Lz - 1) * a.X1h * a.Ly : cb + a.X1h * a.Ly;
+    const int s = a.X1h * a.Ly * a.Lz;
+    if (t == a.Lt - 1 && a.tbc) bc = T(-1);
+    return (t == a.Lt - 1) ? cb - (a.Lt - 1) * s : cb + s;
+}
+
+// The gradient of U_mu(x): g(x), psi(x+mu), psi(x), g(x+mu) (loadv(k, f, v), k = 0..3) projected
+// to half-spinors and the two outer products summed, scaled by coef * bc, and (project) taken to
+// the tangent space at U (loadu(U)).
+template <int MU, int NF, typename T, typename LV, typename LU>
+__device__ __forceinline__ void gradient_core(const ForceArgs &a, T bc, LV loadv, LU loadu, C<T> m[3][3])
+{
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -110,15 +115,15 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
     for (int f = 0; f < NF; f++) {
         C<T> v[4][3], ha[2][3], hb[2][3];
         // sum_s ((1 - g) g(x))_s psi(x+mu)_s^dag
-        load_sp<PREC>(a.gv[par], a.gv_norm[par], f, cb, a.Vh, v);
+        loadv(0, f, v);
         project_upper<MU>(v, T(-1), ha);
-        load_sp<PREC>(a.psi[1 - par], a.psi_norm[1 - par], f, nb, a.Vh, v);
+        loadv(1, f, v);
         project_upper<MU>(v, T(-1), hb);
         outer_add(ha, hb, m);
         // sum_s psi(x)_s ((1 + g) g(x+mu))_s^dag
-        load_sp<PREC>(a.psi[par], a.psi_norm[par], f, cb, a.Vh, v);
+        loadv(2, f, v);
         project_upper<MU>(v, T(1), ha);
-        load_sp<PREC>(a.gv[1 - par], a.gv_norm[1 - par], f, nb, a.Vh, v);
+        loadv(3, f, v);
         project_upper<MU>(v, T(1), hb);
         outer_add(ha, hb, m);
     }
@@ -128,10 +133,8 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
 #pragma unroll
         for (int j = 0; j < 3; j++) m[i][j] = cscale(sc, m[i][j]);
     if (a.project) {
-        using LL = LinkLayout<PREC, RECON>;
-        const typename LL::chunk *G = reinterpret_cast<const typename LL::chunk *>(a.gauge);
         Link<T> U;
-        LinkLoader<PREC, RECON>::load(G + (size_t)(MU * 2 + par) * LL::N * a.Vh, cb, a.Vh, U);
+        loadu(U);
         C<T> zz[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -162,6 +165,26 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
                 m[i][j] = s;
             }
     }
+}
+
+// The gradient of U_mu(x) with its operands read from global memory.
+template <int PREC, int RECON, int NF, int MU, typename T>
+__device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int cb, int x, int y, int z, int t,
+                                              C<T> m[3][3])
+{
+    T bc;
+    const int nb = force_neighbour<MU>(a, cb, x, y, z, t, bc);
+    auto loadv = [&](int k, int f, C<T> v[4][3]) {
+        const int fp = (k == 0 || k == 2) ? par : 1 - par, site = (k == 0 || k == 2) ? cb : nb;
+        if (k == 0 || k == 3) load_sp<PREC>(a.gv[fp], a.gv_norm[fp], f, site, a.Vh, v);
+        else load_sp<PREC>(a.psi[fp], a.psi_norm[fp], f, site, a.Vh, v);
+    };
+    auto loadu = [&](Link<T> &U) {
+        using LL = LinkLayout<PREC, RECON>;
+        const typename LL::chunk *G = reinterpret_cast<const typename LL::chunk *>(a.gauge);
+        LinkLoader<PREC, RECON>::load(G + (size_t)(MU * 2 + par) * LL::N * a.Vh, cb, a.Vh, U);
+    };
+    gradient_core<MU, NF, T>(a, bc, loadv, loadu, m);
 }
 
 // One warp per (32 consecutive sites in lexicographic order, direction mu): warp mu of a block
@@ -216,6 +239,156 @@ __global__ void __launch_bounds__(128, (PREC == P64 ? 3 : 5)) k_force(const __gr
         reinterpret_cast<CT *>(a.out)[((long)mu * V + lex0) * 9 + nsite * 9 - 1] = tw[nsite * 9 - 1];
 }
 
+// The same work with every operand of a warp's links copied into shared memory by cp.async before
+// the arithmetic (binary32 fields): all 16-byte chunks of psi(x), g(x) (copied once per block,
+// a quarter by each warp), psi(x+mu), g(x+mu) and U_mu(x) are in flight together instead of being
+// waited for one spinor at a time.  Layout [chunk][lane], conflict-free; a warp's neighbour area
+// is reused to stage its 32 x 9 results for the coalesced stores.
+template <int PREC, int RECON, int NF>
+struct ForceStage {
+    using SC = typename Traits<PREC>::schunk;
+    using LC = typename LinkLayout<PREC, RECON>::chunk;
+    static constexpr int SCH = NF * Traits<PREC>::SCHUNKS;             // chunks of one field per site
+    static constexpr int OWN = 2 * SCH * 32 * 16;                       // psi(x), g(x) of the block's sites
+    static constexpr int NBR = 2 * SCH * 32 * 16;                       // psi(x+mu), g(x+mu) of one warp
+    static constexpr int LNK = LinkLayout<PREC, RECON>::N * 32 * (int)sizeof(LC);  // U_mu(x) of one warp
+    static constexpr int WARP = NBR + LNK;
+    static constexpr int BYTES = OWN + 4 * WARP;
+};
+
+template <int PREC, int RECON, int NF, typename CT>
+__global__ void __launch_bounds__(128, 5) k_force_staged(const __grid_constant__ ForceArgs a)
+{
+    using T = typename Traits<PREC>::real;
+    using S = ForceStage<PREC, RECON, NF>;
+    using SC = typename S::SC;
+    using LC = typename S::LC;
+    using LL = LinkLayout<PREC, RECON>;
+    extern __shared__ __align__(16) char smem_force[];
+    SC *own = reinterpret_cast<SC *>(smem_force);                           // [field][chunk][lane]
+    char *wbase = smem_force + S::OWN + (threadIdx.x >> 5) * S::WARP;
+    SC *nbr = reinterpret_cast<SC *>(wbase);                                // [field][chunk][lane]
+    LC *lnk = reinterpret_cast<LC *>(wbase + S::NBR);                       // [chunk][lane]
+    const long V = 2L * a.Vh;
+    const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+    const long lex0 = (long)blockIdx.x * 32;
+    const long lex = lex0 + lane;
+    const bool valid = lex < V;
+    int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0, nb = 0;
+    T bc = T(1);
+    if (valid) {
+        long r = lex;
+        x = (int)(r % a.Lx);
+        r /= a.Lx;
+        y = (int)(r % a.Ly);
+        r /= a.Ly;
+        z = (int)(r % a.Lz);
+        t = (int)(r / a.Lz);
+        par = (x + y + z + t) & 1;
+        cb = (int)(lex >> 1);
+        switch (mu) {
+        case 0: nb = force_neighbour<0>(a, cb, x, y, z, t, bc); break;
+        case 1: nb = force_neighbour<1>(a, cb, x, y, z, t, bc); break;
+        case 2: nb = force_neighbour<2>(a, cb, x, y, z, t, bc); break;
+        default: nb = force_neighbour<3>(a, cb, x, y, z, t, bc); break;
+        }
+        const long fst = (long)Traits<PREC>::SCHUNKS * a.Vh;  // chunks per flavour block
+        // own site: chunk k of field fld, k = mu, mu + 4, ... (the four warps share the copies)
+        for (int q = mu; q < 2 * S::SCH; q += 4) {
+            const int fld = q / S::SCH, k = q % S::SCH, f = k / Traits<PREC>::SCHUNKS, kk = k % Traits<PREC>::SCHUNKS;
+            const SC *src = reinterpret_cast<const SC *>(fld ? a.gv[par] : a.psi[par]) + f * fst + (long)kk * a.Vh + cb;
+            cp_async<16>(own + ((size_t)fld * S::SCH + k) * 32 + lane, src);
+        }
+#pragma unroll
+        for (int fld = 0; fld < 2; fld++)
+#pragma unroll
+            for (int k = 0; k < S::SCH; k++) {
+                const int f = k / Traits<PREC>::SCHUNKS, kk = k % Traits<PREC>::SCHUNKS;
+                const SC *src = reinterpret_cast<const SC *>(fld ? a.gv[1 - par] : a.psi[1 - par]) + f * fst +
+                                (long)kk * a.Vh + nb;
+                cp_async<16>(nbr + ((size_t)fld * S::SCH + k) * 32 + lane, src);
+            }
+        if (a.project) {
+            const LC *G = reinterpret_cast<const LC *>(a.gauge) + (size_t)(mu * 2 + par) * LL::N * a.Vh;
+#pragma unroll
+            for (int k = 0; k < LL::N; k++) cp_async<(int)sizeof(LC)>(lnk + k * 32 + lane, G + (size_t)k * a.Vh + cb);
+        }
+    }
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();  // the own-site chunks were copied by all four warps
+    C<T> m[3][3];
+    if (valid) {
+        auto loadv = [&](int k, int f, C<T> v[4][3]) {
+            const SC *base = (k == 0 || k == 2) ? own : nbr;
+            const int fld = (k == 0 || k == 3) ? 1 : 0;
+            SC c[Traits<PREC>::SCHUNKS];
+#pragma unroll
+            for (int q = 0; q < Traits<PREC>::SCHUNKS; q++)
+                c[q] = base[((size_t)fld * S::SCH + f * Traits<PREC>::SCHUNKS + q) * 32 + lane];
+            T r[24];
+            spinor_from_chunks<PREC>(c, r);
+#pragma unroll
+            for (int s2 = 0; s2 < 4; s2++)
+#pragma unroll
+                for (int c2 = 0; c2 < 3; c2++) v[s2][c2] = {r[2 * (3 * s2 + c2)], r[2 * (3 * s2 + c2) + 1]};
+        };
+        auto loadu = [&](Link<T> &U) {
+            LC c[LL::N];
+#pragma unroll
+            for (int k = 0; k < LL::N; k++) c[k] = lnk[k * 32 + lane];
+            LinkRegLoader<PREC, RECON>::load(c, U);
+        };
+        switch (mu) {
+        case 0: gradient_core<0, NF, T>(a, bc, loadv, loadu, m); break;
+        case 1: gradient_core<1, NF, T>(a, bc, loadv, loadu, m); break;
+        case 2: gradient_core<2, NF, T>(a, bc, loadv, loadu, m); break;
+        default: gradient_core<3, NF, T>(a, bc, loadv, loadu, m); break;
+        }
+    }
+    __syncwarp();  // the warp's neighbour area is free again: stage the results there
+    CT *tw = reinterpret_cast<CT *>(wbase);
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                CT v;
+                v.x = m[i][j].r;
+                v.y = m[i][j].i;
+                tw[lane * 9 + 3 * i + j] = v;
+            }
+    }
+    __syncwarp();
+    const long nsite = (V - lex0) < 32 ? (V - lex0) : 32;
+    const long nvec = nsite * 9 * (long)sizeof(CT) / 16;
+    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex0) * 9);
+    const uint4 *src = reinterpret_cast<const uint4 *>(tw);
+    for (long k = lane; k < nvec; k += 32) dst[k] = src[k];
+    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && lane == 0)
+        reinterpret_cast<CT *>(a.out)[((long)mu * V + lex0) * 9 + nsite * 9 - 1] = tw[nsite * 9 - 1];
+}
+
+template <int RECON, int NF, typename CT>
+cudaError_t launch_force_staged(const ForceArgs &a, long grid, cudaStream_t s)
+{
+    using S = ForceStage<P32, RECON, NF>;
+    static_assert(S::NBR >= 32 * 9 * (int)sizeof(CT), "the neighbour area holds the staged results");
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_force_staged<P32, RECON, NF, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 S::BYTES);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    k_force_staged<P32, RECON, NF, CT><<<grid, 128, S::BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace tmk
 
 using namespace tmk;
@@ -260,6 +433,7 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     a.project = project ? 1 : 0;
     a.coef = -g->p.kappa * coef;
     const int pidx = prec_index(psi_e->prec);
+    if (need_links(g, psi_e->prec) != TM_OK) return TM_ERR_ARG;
     a.gauge = g->links[pidx];
     a.out = F_canon;
     if (((uintptr_t)F_canon & 15) != 0) { set_error("tm_force: the output must be 16-byte aligned"); return TM_ERR_ARG; }
@@ -274,11 +448,20 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     if (recon == 18) { TM_F1(P, 18, CT) }         \
     else if (recon == 12) { TM_F1(P, 12, CT) }    \
     else { TM_F1(P, 8, CT) }
+    // binary32: the staged form; binary64 (bound by the FP64 pipe) the register form
+#define TM_S1(R, CT) return cuda_check(g->nf == 1 ? launch_force_staged<R, 1, CT>(a, grid, s) \
+                                                   : launch_force_staged<R, 2, CT>(a, grid, s), "tm_force launch");
+#define TM_SR(CT)                                 \
+    if (recon == 18) { TM_S1(18, CT) }            \
+    else if (recon == 12) { TM_S1(12, CT) }       \
+    else { TM_S1(8, CT) }
     if (pidx == 0) {
         if (canon_type == TM_C128) { TM_FR(P64, double2) } else { TM_FR(P64, float2) }
     } else {
-        if (canon_type == TM_C128) { TM_FR(P32, double2) } else { TM_FR(P32, float2) }
+        if (canon_type == TM_C128) { TM_SR(double2) } else { TM_SR(float2) }
     }
+#undef TM_SR
+#undef TM_S1
 #undef TM_FR
 #undef TM_F1
     return cuda_check(cudaGetLastError(), "tm_force launch");

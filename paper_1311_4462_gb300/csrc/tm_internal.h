@@ -87,4 +87,5 @@ int spinor_chunks(int prec);       // 16-byte chunks per site and flavour
 size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);
 tm_status cuda_check(cudaError_t e, const char *what);
+tm_status need_links(const tm_gauge *g, int prec);  // TM_ERR_ARG when the handle did not pack prec
 }  // namespace tmk

@@ -136,13 +136,13 @@ def test_autograd_reuses_the_handle_while_U_is_unchanged():
     tU = torch.from_numpy(U).to("cuda").requires_grad_(True)
     tpsi = torch.from_numpy(psi).to("cuda")
     y1 = TMApply.apply(tU, tpsi, p)
-    g1 = tag.gauge_for(tU, p)
+    g1 = tag.gauge_for(tU, p, (tmq.TM_PREC_F64,))
     y2 = TMApply.apply(tU, tpsi, p)
-    assert tag.gauge_for(tU, p) is g1
+    assert tag.gauge_for(tU, p, (tmq.TM_PREC_F64,)) is g1
     assert torch.equal(y1, y2)
     tphi = torch.from_numpy(phi).to("cuda").requires_grad_(True)
     S = PseudofermionAction.apply(tU, tphi, p, 1e-11)
-    assert tag.gauge_for(tU, p) is g1
+    assert tag.gauge_for(tU, p, (tmq.TM_PREC_F64,)) is g1  # FP64 CG: the same FP64-only handle
     (0.5 * S).backward()
     gU_half, gphi_half = tU.grad.clone(), tphi.grad.clone()
     tU.grad, tphi.grad = None, None
@@ -152,5 +152,28 @@ def test_autograd_reuses_the_handle_while_U_is_unchanged():
     assert torch.allclose(2 * gphi_half, tphi.grad, rtol=1e-12, atol=0)
     with torch.no_grad():
         tU.mul_(1.0)  # an in-place change bumps U's version: the cached links are stale
-    assert tag.gauge_for(tU, p) is not g1
+    assert tag.gauge_for(tU, p, (tmq.TM_PREC_F64,)) is not g1
     tag.clear_cache()
+
+
+def test_handle_with_a_subset_of_link_precisions():
+    """tm_gauge_create_ex packs only the masked storage forms; calls on the others are refused."""
+    import paper_1311_4462_gb300 as tmq
+    name, L, flavor, kappa, mu, eps = CASES[1]
+    p = tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=12)
+    po = orc.Params(L, kappa, mu, eps, flavor=flavor)
+    U = inputs.gauge_field(L, 1305)
+    psi = inputs.spinor_field(L, p.nf, 2410)
+    g = tmq.Gauge(p, torch.from_numpy(U), precs=(tmq.TM_PREC_F32,))
+    xe = tmq.pack(g, torch.from_numpy(psi), 0, 4)
+    out, tmp = tmq.Field(g, 4), tmq.Field(g, 4)
+    tmq.precond_op(g, out, xe, tmp, 0, False)
+    assert rel(tmq.unpack(g, out, 0).cpu().numpy(), orc.apply_M_pc(po, U, orc.project_parity(po, psi, 0))) < 1e-6
+    x64 = tmq.pack(g, torch.from_numpy(psi), 0, 8)
+    with pytest.raises(tmq.TMError) as e:
+        tmq.precond_op(g, tmq.Field(g, 8), x64, tmq.Field(g, 8), 0, False)
+    assert "no links" in str(e.value)
+    with pytest.raises(tmq.TMError):
+        tmq.set_clover(g, 1.0)  # the clover field is built from the FP64 links
+    tmq.autotune(g)  # tunes the packed precision only
+    g.close()
