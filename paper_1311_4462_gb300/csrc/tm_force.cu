@@ -8,14 +8,11 @@
 // (bc = -1 on links across the antiperiodic time boundary), times a caller coefficient.
 // The twist R does not depend on U.  project = 1 returns the component in the tangent space
 // of SU(3) at U: P(G) = TA(G U^dag) U with TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6.
-// One thread per link computes its gradient; the colour outer products of spin-projected
+// One thread per site computes its four links; the colour outer products of spin-projected
 // half-spinors are summed over the two projected spin rows and the flavours in registers and the
 // 3x3 results are written in the canonical gauge layout.
-#include <atomic>
-
 #include "tm_blas.cuh"
 #include "tm_core.cuh"
-#include "tm_dslash.cuh"
 #include "tm_internal.h"
 
 namespace tmk {
@@ -187,37 +184,18 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
     gradient_core<MU, NF, T>(a, bc, loadv, loadu, m);
 }
 
-// One warp per (32 consecutive sites in lexicographic order, direction mu): warp mu of a block
-// computes U_mu(x) for the block's 32 sites, so the four directions of a site run in parallel and
-// share psi(x), g(x) through L1.  The warp stages its 32 x 9 results in shared memory and writes its
-// contiguous run of the canonical layout with 16-byte stores.
-template <int PREC, int RECON, int NF, typename CT>
-__global__ void __launch_bounds__(128, (PREC == P64 ? 3 : 5)) k_force(const __grid_constant__ ForceArgs a)
+// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
+// of the canonical output) computes its four links in turn, re-reading psi(x), g(x) from L1;
+// each link's 3x3 gradient goes through shared memory so that the block writes its contiguous
+// run of the canonical layout with 16-byte stores.  (Measured alternatives, slower at 24^3x48 in
+// FP32: one warp per direction and 32 sites, 143 us; every operand of a warp's links copied into
+// shared memory by cp.async first, 181-254 us; this form 133 us.)
+// the block's run of sites for direction MU: stage in shared memory, then 16-byte stores
+template <int MU, typename CT, typename T>
+__device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long V, bool valid, const C<T> m[3][3],
+                                           CT *tile)
 {
-    using T = typename Traits<PREC>::real;
-    __shared__ __align__(16) CT tile[4][32 * 9];
-    const long V = 2L * a.Vh;
-    const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
-    const long lex0 = (long)blockIdx.x * 32;
-    const long lex = lex0 + lane;
-    CT *tw = tile[mu];
-    if (lex < V) {
-        long r = lex;
-        const int x = (int)(r % a.Lx);
-        r /= a.Lx;
-        const int y = (int)(r % a.Ly);
-        r /= a.Ly;
-        const int z = (int)(r % a.Lz);
-        const int t = (int)(r / a.Lz);
-        const int par = (x + y + z + t) & 1;
-        const int cb = (int)(lex >> 1);
-        C<T> m[3][3];
-        switch (mu) {  // warp-uniform
-        case 0: link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m); break;
-        case 1: link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m); break;
-        case 2: link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m); break;
-        default: link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m); break;
-        }
+    if (valid) {
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -225,57 +203,31 @@ __global__ void __launch_bounds__(128, (PREC == P64 ? 3 : 5)) k_force(const __gr
                 CT v;
                 v.x = m[i][j].r;
                 v.y = m[i][j].i;
-                tw[lane * 9 + 3 * i + j] = v;
+                tile[threadIdx.x * 9 + 3 * i + j] = v;
             }
     }
-    __syncwarp();
-    const long nsite = (V - lex0) < 32 ? (V - lex0) : 32;
+    __syncthreads();
+    const long nsite = (V - lex0) < (long)blockDim.x ? (V - lex0) : (long)blockDim.x;
     const long nvec = nsite * 9 * (long)sizeof(CT) / 16;  // 9 complex per site, a multiple of 16 bytes per 2 sites
-    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex0) * 9);
-    const uint4 *src = reinterpret_cast<const uint4 *>(tw);
-    for (long k = lane; k < nvec; k += 32) dst[k] = src[k];
+    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)MU * V + lex0) * 9);
+    const uint4 *src = reinterpret_cast<const uint4 *>(tile);
+    for (long k = threadIdx.x; k < nvec; k += blockDim.x) dst[k] = src[k];
     // an odd number of complex64 sites leaves 8 bytes: written element-wise
-    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && lane == 0)
-        reinterpret_cast<CT *>(a.out)[((long)mu * V + lex0) * 9 + nsite * 9 - 1] = tw[nsite * 9 - 1];
+    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && threadIdx.x == 0)
+        reinterpret_cast<CT *>(a.out)[((long)MU * V + lex0) * 9 + nsite * 9 - 1] = tile[nsite * 9 - 1];
+    __syncthreads();
 }
 
-// The same work with every operand of a warp's links copied into shared memory by cp.async before
-// the arithmetic (binary32 fields): all 16-byte chunks of psi(x), g(x) (copied once per block,
-// a quarter by each warp), psi(x+mu), g(x+mu) and U_mu(x) are in flight together instead of being
-// waited for one spinor at a time.  Layout [chunk][lane], conflict-free; a warp's neighbour area
-// is reused to stage its 32 x 9 results for the coalesced stores.
-template <int PREC, int RECON, int NF>
-struct ForceStage {
-    using SC = typename Traits<PREC>::schunk;
-    using LC = typename LinkLayout<PREC, RECON>::chunk;
-    static constexpr int SCH = NF * Traits<PREC>::SCHUNKS;             // chunks of one field per site
-    static constexpr int OWN = 2 * SCH * 32 * 16;                       // psi(x), g(x) of the block's sites
-    static constexpr int NBR = 2 * SCH * 32 * 16;                       // psi(x+mu), g(x+mu) of one warp
-    static constexpr int LNK = LinkLayout<PREC, RECON>::N * 32 * (int)sizeof(LC);  // U_mu(x) of one warp
-    static constexpr int WARP = NBR + LNK;
-    static constexpr int BYTES = OWN + 4 * WARP;
-};
-
 template <int PREC, int RECON, int NF, typename CT>
-__global__ void __launch_bounds__(128, 5) k_force_staged(const __grid_constant__ ForceArgs a)
+__global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __grid_constant__ ForceArgs a)
 {
     using T = typename Traits<PREC>::real;
-    using S = ForceStage<PREC, RECON, NF>;
-    using SC = typename S::SC;
-    using LC = typename S::LC;
-    using LL = LinkLayout<PREC, RECON>;
-    extern __shared__ __align__(16) char smem_force[];
-    SC *own = reinterpret_cast<SC *>(smem_force);                           // [field][chunk][lane]
-    char *wbase = smem_force + S::OWN + (threadIdx.x >> 5) * S::WARP;
-    SC *nbr = reinterpret_cast<SC *>(wbase);                                // [field][chunk][lane]
-    LC *lnk = reinterpret_cast<LC *>(wbase + S::NBR);                       // [chunk][lane]
+    __shared__ __align__(16) CT tile[128 * 9];
     const long V = 2L * a.Vh;
-    const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
-    const long lex0 = (long)blockIdx.x * 32;
-    const long lex = lex0 + lane;
-    const bool valid = lex < V;
-    int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0, nb = 0;
-    T bc = T(1);
+    const long lex0 = (long)blockIdx.x * blockDim.x;
+    const long lex = lex0 + threadIdx.x;
+    const bool valid = lex < V;  // every thread takes part in the block's barriers
+    int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0;
     if (valid) {
         long r = lex;
         x = (int)(r % a.Lx);
@@ -286,107 +238,16 @@ __global__ void __launch_bounds__(128, 5) k_force_staged(const __grid_constant__
         t = (int)(r / a.Lz);
         par = (x + y + z + t) & 1;
         cb = (int)(lex >> 1);
-        switch (mu) {
-        case 0: nb = force_neighbour<0>(a, cb, x, y, z, t, bc); break;
-        case 1: nb = force_neighbour<1>(a, cb, x, y, z, t, bc); break;
-        case 2: nb = force_neighbour<2>(a, cb, x, y, z, t, bc); break;
-        default: nb = force_neighbour<3>(a, cb, x, y, z, t, bc); break;
-        }
-        const long fst = (long)Traits<PREC>::SCHUNKS * a.Vh;  // chunks per flavour block
-        // own site: chunk k of field fld, k = mu, mu + 4, ... (the four warps share the copies)
-        for (int q = mu; q < 2 * S::SCH; q += 4) {
-            const int fld = q / S::SCH, k = q % S::SCH, f = k / Traits<PREC>::SCHUNKS, kk = k % Traits<PREC>::SCHUNKS;
-            const SC *src = reinterpret_cast<const SC *>(fld ? a.gv[par] : a.psi[par]) + f * fst + (long)kk * a.Vh + cb;
-            cp_async<16>(own + ((size_t)fld * S::SCH + k) * 32 + lane, src);
-        }
-#pragma unroll
-        for (int fld = 0; fld < 2; fld++)
-#pragma unroll
-            for (int k = 0; k < S::SCH; k++) {
-                const int f = k / Traits<PREC>::SCHUNKS, kk = k % Traits<PREC>::SCHUNKS;
-                const SC *src = reinterpret_cast<const SC *>(fld ? a.gv[1 - par] : a.psi[1 - par]) + f * fst +
-                                (long)kk * a.Vh + nb;
-                cp_async<16>(nbr + ((size_t)fld * S::SCH + k) * 32 + lane, src);
-            }
-        if (a.project) {
-            const LC *G = reinterpret_cast<const LC *>(a.gauge) + (size_t)(mu * 2 + par) * LL::N * a.Vh;
-#pragma unroll
-            for (int k = 0; k < LL::N; k++) cp_async<(int)sizeof(LC)>(lnk + k * 32 + lane, G + (size_t)k * a.Vh + cb);
-        }
     }
-    cp_commit();
-    cp_wait<0>();
-    __syncthreads();  // the own-site chunks were copied by all four warps
     C<T> m[3][3];
-    if (valid) {
-        auto loadv = [&](int k, int f, C<T> v[4][3]) {
-            const SC *base = (k == 0 || k == 2) ? own : nbr;
-            const int fld = (k == 0 || k == 3) ? 1 : 0;
-            SC c[Traits<PREC>::SCHUNKS];
-#pragma unroll
-            for (int q = 0; q < Traits<PREC>::SCHUNKS; q++)
-                c[q] = base[((size_t)fld * S::SCH + f * Traits<PREC>::SCHUNKS + q) * 32 + lane];
-            T r[24];
-            spinor_from_chunks<PREC>(c, r);
-#pragma unroll
-            for (int s2 = 0; s2 < 4; s2++)
-#pragma unroll
-                for (int c2 = 0; c2 < 3; c2++) v[s2][c2] = {r[2 * (3 * s2 + c2)], r[2 * (3 * s2 + c2) + 1]};
-        };
-        auto loadu = [&](Link<T> &U) {
-            LC c[LL::N];
-#pragma unroll
-            for (int k = 0; k < LL::N; k++) c[k] = lnk[k * 32 + lane];
-            LinkRegLoader<PREC, RECON>::load(c, U);
-        };
-        switch (mu) {
-        case 0: gradient_core<0, NF, T>(a, bc, loadv, loadu, m); break;
-        case 1: gradient_core<1, NF, T>(a, bc, loadv, loadu, m); break;
-        case 2: gradient_core<2, NF, T>(a, bc, loadv, loadu, m); break;
-        default: gradient_core<3, NF, T>(a, bc, loadv, loadu, m); break;
-        }
-    }
-    __syncwarp();  // the warp's neighbour area is free again: stage the results there
-    CT *tw = reinterpret_cast<CT *>(wbase);
-    if (valid) {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                CT v;
-                v.x = m[i][j].r;
-                v.y = m[i][j].i;
-                tw[lane * 9 + 3 * i + j] = v;
-            }
-    }
-    __syncwarp();
-    const long nsite = (V - lex0) < 32 ? (V - lex0) : 32;
-    const long nvec = nsite * 9 * (long)sizeof(CT) / 16;
-    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)mu * V + lex0) * 9);
-    const uint4 *src = reinterpret_cast<const uint4 *>(tw);
-    for (long k = lane; k < nvec; k += 32) dst[k] = src[k];
-    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && lane == 0)
-        reinterpret_cast<CT *>(a.out)[((long)mu * V + lex0) * 9 + nsite * 9 - 1] = tw[nsite * 9 - 1];
-}
-
-template <int RECON, int NF, typename CT>
-cudaError_t launch_force_staged(const ForceArgs &a, long grid, cudaStream_t s)
-{
-    using S = ForceStage<P32, RECON, NF>;
-    static_assert(S::NBR >= 32 * 9 * (int)sizeof(CT), "the neighbour area holds the staged results");
-    static std::atomic<unsigned long long> opted{0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
-    if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_force_staged<P32, RECON, NF, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 S::BYTES);
-        if (e != cudaSuccess) return e;
-        opted.fetch_or(bit, std::memory_order_acq_rel);
-    }
-    k_force_staged<P32, RECON, NF, CT><<<grid, 128, S::BYTES, s>>>(a);
-    return cudaGetLastError();
+    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
+    store_links<0>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
+    store_links<1>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
+    store_links<2>(a, lex0, V, valid, m, tile);
+    if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m);
+    store_links<3>(a, lex0, V, valid, m, tile);
 }
 
 }  // namespace tmk
@@ -437,9 +298,9 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     a.gauge = g->links[pidx];
     a.out = F_canon;
     if (((uintptr_t)F_canon & 15) != 0) { set_error("tm_force: the output must be 16-byte aligned"); return TM_ERR_ARG; }
-    const long n = 2L * g->Vh;  // one warp per 32 sites and direction, four directions per block
+    const long n = 2L * g->Vh;  // one thread per site
     const int block = 128;
-    const long grid = (n + 31) / 32;
+    const long grid = (n + block - 1) / block;
     cudaStream_t s = (cudaStream_t)stream;
     const int recon = g->p.recon;
 #define TM_F1(P, R, CT) \
@@ -448,20 +309,11 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     if (recon == 18) { TM_F1(P, 18, CT) }         \
     else if (recon == 12) { TM_F1(P, 12, CT) }    \
     else { TM_F1(P, 8, CT) }
-    // binary32: the staged form; binary64 (bound by the FP64 pipe) the register form
-#define TM_S1(R, CT) return cuda_check(g->nf == 1 ? launch_force_staged<R, 1, CT>(a, grid, s) \
-                                                   : launch_force_staged<R, 2, CT>(a, grid, s), "tm_force launch");
-#define TM_SR(CT)                                 \
-    if (recon == 18) { TM_S1(18, CT) }            \
-    else if (recon == 12) { TM_S1(12, CT) }       \
-    else { TM_S1(8, CT) }
     if (pidx == 0) {
         if (canon_type == TM_C128) { TM_FR(P64, double2) } else { TM_FR(P64, float2) }
     } else {
-        if (canon_type == TM_C128) { TM_SR(double2) } else { TM_SR(float2) }
+        if (canon_type == TM_C128) { TM_FR(P32, double2) } else { TM_FR(P32, float2) }
     }
-#undef TM_SR
-#undef TM_S1
 #undef TM_FR
 #undef TM_F1
     return cuda_check(cudaGetLastError(), "tm_force launch");
