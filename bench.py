@@ -290,6 +290,7 @@ def run_ours(args, rank, world):
         result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
         result["cg"] = cg_section(tmq, g, U, psi, dev, args)
         result["multi_rhs"] = multi_rhs_section(tmq, U, dev, args)
+        result["domain_decomposition"] = dd_section(tmq, U, psi, dev, args)
         result["batching"] = batching_section(tmq, U, dev, args)
         result["clover"] = clover_section(tmq, U, psi, dev, args)
         result["differentiation"] = force_section(tmq, dev, args)
@@ -760,6 +761,60 @@ def multi_rhs_section(tmq, U, dev, args):
             "launch_tables": tables}
 
 
+def dd_section(tmq, U, psi, dev, args):
+    """The domain-decomposed operator (sec. 2.1) emulated on one GPU: every time slab in this process,
+    faces moved by device copies that overlap the interior launches.  M_asym of the 32^3x64 doublet
+    (FP32, recon 12) cut into R = 1, 2, 4, 8 slabs, per application, against the undecomposed handle
+    (one GPU runs all R slabs' launches one after another, so this is the decomposition's overhead,
+    not a scaling measurement); and the analogue of Table 2 on the 16^3x32 one-flavour system: the
+    decomposed FP64 CG with asymmetric and symmetric PC, iterations and time, R = 1 and 4."""
+    import torch
+    from paper_1311_4462_gb300 import dd, inputs
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    p = tmq.Params(L_FULL, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=12)
+    prec = tmq.TM_PREC_F32
+    rows = []
+    for R in (1, 2, 4, 8):
+        if L_FULL[3] % R or (L_FULL[3] // R) % 2:
+            continue
+        slabs = dd.make_slabs(p, U, R)
+        tr = dd.LocalTransport()
+        ins = dd.pack_slabs(slabs, dd.split_field(slabs, psi), 0, prec)
+        outs, tmps = [s.field(prec) for s in slabs], [s.field(prec) for s in slabs]
+        ms = time_op(lambda: dd.precond_op(slabs, outs, ins, tmps, tr, 0, False), 10, flush)
+        face = slabs[0].faces(prec).nbytes
+        rows.append({"slabs": R, "us": round(ms * 1e3, 1), "face_bytes": face,
+                     "faces_per_application": 4 * R, "gflops": round(FLOPS_PER_SITE[2] * p.Vh / (ms * 1e-3) / 1e9, 1)})
+        for s_ in slabs:
+            s_.close()
+        del ins, outs, tmps
+    # Table 2 analogue: decomposed FP64 CG, asym vs sym, 16^3x32 one flavour
+    L2 = (16, 16, 16, 32)
+    p2 = tmq.Params(L2, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=12)
+    U2 = torch.from_numpy(inputs.gauge_field(L2, 1001)).to(dev)
+    b2 = torch.from_numpy(inputs.spinor_field(L2, 1, 2001)).to(dev)
+    cg = []
+    for R in (1, 4):
+        slabs = dd.make_slabs(p2, U2, R)
+        tr = dd.LocalTransport()
+        parts = dd.split_field(slabs, b2)
+        bes, bos = dd.pack_slabs(slabs, parts, 0), dd.pack_slabs(slabs, parts, 1)
+        for pc in (0, 1):
+            bps, xes = [s_.field() for s_ in slabs], [s_.field() for s_ in slabs]
+            dd.prepare_rhs(slabs, bps, bes, bos, tr, pc)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            st = dd.cg(slabs, xes, bps, tr, pc=pc, tol=1e-10)
+            torch.cuda.synchronize()
+            cg.append({"slabs": R, "pc": "sym" if pc else "asym", "iterations": st["iterations"],
+                       "true_residual": st["true_residual"], "s": round(time.time() - t0, 3)})
+        for s_ in slabs:
+            s_.close()
+    return {"operator": {"lattice": list(L_FULL), "workload": "M_asym, doublet, FP32, recon 12", "rows": rows},
+            "cg_16x16x16x32_fp64_tol_1e-10": cg,
+            "note": "all slabs on one GPU: the time is the decomposition's overhead, not scaling"}
+
+
 def batching_section(tmq, U, dev, args):
     """Loop estimator Tr[gamma5 M^-1] on the 32^3x64 one-flavour lattice (kappa 0.1612, mu 0.004):
     256 Z2 sources, 16 per batched mixed-precision CG to 1e-8 with source dropping and CUDA-graph
@@ -827,6 +882,66 @@ def cpu_baseline(U_np, psi_np, args):
                                         f"{dt:.2f} s each"}
 
 
+def solve_only(args):
+    """One solve of the headline system (32^3x64 doublet, asymmetric PC, tol 1e-10), run twice (the
+    first warms up): the command the solver's launch list is captured on."""
+    import torch
+
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import inputs
+    p = tmq.Params(L_FULL, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=args.recon)
+    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L_FULL, 1002)).cuda())
+    b = torch.from_numpy(inputs.spinor_field(L_FULL, 2, 2002)).cuda()
+    be, bo = tmq.pack(g, b, 0, tmq.TM_PREC_F64), tmq.pack(g, b, 1, tmq.TM_PREC_F64)
+    bp = tmq.Field(g, tmq.TM_PREC_F64)
+    tmq.prepare_rhs(g, bp, be, bo, 0, False)
+    kw = {"cg": {"solver": "cg"}, "mixed_f32": {"solver": "mixed", "sloppy_prec": tmq.TM_PREC_F32},
+          "mixed_f16": {"solver": "mixed", "sloppy_prec": tmq.TM_PREC_F16}}[args.solve]
+    out = []
+    for _ in range(2):
+        xe = tmq.Field(g, tmq.TM_PREC_F64)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st = tmq.solve(g, xe, bp, tol=1e-10, maxiter=20000, **kw)
+        torch.cuda.synchronize()
+        out.append({"s": round(time.time() - t0, 4), "iterations": st["iterations"],
+                    "reliable_updates": st["reliable_updates"], "true_residual": st["true_residual"]})
+    g.close()
+    return {"solve": args.solve, "lattice": list(L_FULL), "runs": out}
+
+
+def force_only(args):
+    """tm_force (projected) at 24^3x48 one flavour in FP32 or FP64: the command the force kernel's
+    profile is captured on; prints its time and algorithmic bandwidth."""
+    import torch
+
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import inputs
+    L = (24, 24, 24, 48)
+    prec = {"f32": tmq.TM_PREC_F32, "f64": tmq.TM_PREC_F64}[args.force]
+    p = tmq.Params(L, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=12)
+    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L, 1003)).cuda(), precs=(prec,))
+    psi = torch.from_numpy(inputs.spinor_field(L, 1, 2003)).cuda()
+    gv = torch.from_numpy(inputs.spinor_field(L, 1, 2103)).cuda()
+    pe, po = tmq.pack(g, psi, 0, prec), tmq.pack(g, psi, 1, prec)
+    ge, go = tmq.pack(g, gv, 0, prec), tmq.pack(g, gv, 1, prec)
+    out = torch.empty(p.gauge_shape, dtype=torch.complex128 if prec == 8 else torch.complex64, device="cuda")
+    for _ in range(args.warmup):
+        tmq.force(g, pe, po, ge, go, coef=1.0, project=True, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        tmq.force(g, pe, po, ge, go, coef=1.0, project=True, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    V, w = 2 * p.Vh, REAL_BYTES[prec]
+    by = 2 * V * 24 * w + 4 * V * 12 * w + 4 * V * 18 * w
+    g.close()
+    return {"force": args.force, "lattice": list(L), "us": round(ms * 1e3, 1), "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+
+
 # -------------------------------------------------------------------------------------- reference
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP) timed as the reference arm on a bounded sub-lattice sample."""
@@ -886,6 +1001,10 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline storage (profiling runs)")
     ap.add_argument("--nf", type=int, default=2, choices=[1, 2], help="flavours of the headline step (profiling runs)")
     ap.add_argument("--recon", type=int, default=12, choices=[18, 12, 8], help="link storage (profiling runs)")
+    ap.add_argument("--solve", default=None, choices=["cg", "mixed_f32", "mixed_f16"],
+                    help="profiling run: only this solve (asymmetric PC, 1e-10) of the headline system, twice")
+    ap.add_argument("--force", default=None, choices=["f32", "f64"],
+                    help="profiling run: only tm_force at 24^3x48 (one flavour), --warmup + --steps launches")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -895,6 +1014,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.solve or args.force:
+        if rank == 0:
+            print(json.dumps(solve_only(args) if args.solve else force_only(args)), flush=True)
         return
     if world > 1:
         import torch

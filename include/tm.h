@@ -390,7 +390,9 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
  * flavours of an FP32 or FP16 doublet, the two projected spin rows of one flavour (as 6 / 7 in
  * FP64), with results bit-identical to 6 / 7; 2 has no prologue form); multi-RHS entries "f32:m:4" = precision:m:right-hand sides per block (2, 4
  * or 8) of the register form, or 12 / 14 for the staged form (the pipeline of 8 / 9 with links
- * copied through L1) with 2 / 4 right-hand sides per block; clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
+ * copied through L1) with 2 / 4 right-hand sides per block, or 16 (one flavour): with every
+ * right-hand side of an even count, two sources at a time through the doublet's staged kernels
+ * (a one-flavour field with 2k sources has a doublet field's layout with k), else as 14; clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline;
  * fused-operator entries "f32:p:1" = precision:p:1 when tm_precond_op runs as one fused launch
  * (FP64 and FP32; see tm_device_status).  Import accepts any subset of the entries; an

@@ -349,6 +349,45 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         return cuda_check(e, "clover dslash launch");
     }
     if (ncb > 0 && (multi || pidx == 3)) { set_error("internal: site ranges are single-RHS FP64 / FP32 / FP16"); return TM_ERR_ARG; }
+    // Paired sources (multi-RHS tune entry 16, one flavour): every right-hand side of an even count,
+    // two sources at a time through the doublet's kernels -- a one-flavour field with 2k sources has
+    // the layout of a doublet field with k -- with the one-flavour local operator on both
+    // "flavours"; the doublet's staged form pairs the two sources in its packed FMAs.
+    if (multi && act == nullptr && g->nf == 1 && pidx <= 2 && g->multi_rpb[pidx] == 16 && (nact & 1) == 0 &&
+        nact == out->nrhs) {
+        auto diag = [](const Twist<double> &t) {
+            Twist<double> d = t;
+            for (int gi = 0; gi < 2; gi++) {
+                d.m[gi][1][1] = t.m[gi][0][0];
+                d.m[gi][0][1] = d.m[gi][1][0] = {0.0, 0.0};
+            }
+            return d;
+        };
+        const Twist<double> de = diag(te), dp = diag(tp), da = diag(ta);
+        if (pidx == 0) {
+            DslashArgs<double> a;
+            fill_common(a, g, out, in, x, out_parity, pidx);
+            a.epilogue = epi;
+            a.sigma = dagger ? -1.0 : 1.0;
+            a.coef = coef;
+            a.tw_epi = de;
+            a.tw_pro = dp;
+            a.tw_acc = da;
+            e = launch_dslash_multi_p64(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s);
+        } else {
+            DslashArgs<float> a;
+            fill_common(a, g, out, in, x, out_parity, pidx);
+            a.epilogue = epi;
+            a.sigma = dagger ? -1.0f : 1.0f;
+            a.coef = (float)coef;
+            a.tw_epi = to_float(de);
+            a.tw_pro = to_float(dp);
+            a.tw_acc = to_float(da);
+            e = pidx == 1 ? launch_dslash_multi_p32(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s)
+                          : launch_dslash_multi_p16(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s);
+        }
+        return cuda_check(e, "dslash launch (paired sources)");
+    }
     if (pidx == 0) {
         DslashArgs<double> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -1238,10 +1277,10 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             f[k].nrhs = nr;
         }
         const Twist<double> Ri = make_twist(g, TW_RINV, 0);
-        const int rpbs[5] = {2, 4, 8, 12, 14};
+        const int rpbs[6] = {2, 4, 8, 12, 14, 16};
         float best = 1e30f;
         int bestr = g->multi_rpb[pi];
-        for (int ri = 0; ri < 5 && st == TM_OK; ri++) {
+        for (int ri = 0; ri < (g->nf == 1 ? 6 : 5) && st == TM_OK; ri++) {
             g->multi_rpb[pi] = rpbs[ri];
             float ms = 0;
             for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -1319,7 +1358,7 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
         if (sscanf(p, "%3[a-z0-9]:m:%d%n", name, &block, &used) == 2 && used > 0) {
             // multi-RHS entry "<prec>:m:<right-hand sides per block>"
             const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-            if (pi < 0 || (block != 2 && block != 4 && block != 8 && block != 12 && block != 14)) {
+            if (pi < 0 || (block != 2 && block != 4 && block != 8 && block != 12 && block != 14 && block != 16)) {
                 set_error("tm_tune_import: invalid entry '%.32s'", p);
                 return TM_ERR_ARG;
             }

@@ -1700,6 +1700,7 @@ template <int PREC>
 cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                      const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
 {
+    if (rpb == 16) rpb = 14;  // paired sources are arranged by the caller; otherwise the staged form
     if (rpb == 12 || rpb == 14) {
         // staged multi-RHS forms, 2 or 4 right-hand sides per block; the hop pairs as form 8 / 9 does
         // (binary32 and binary16, except one flavour with 18-real links)

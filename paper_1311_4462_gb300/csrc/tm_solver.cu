@@ -559,7 +559,8 @@ class MultiSolver {
     }
     tm_status normal_op(const tm_field *out, const tm_field *in, const tm_field *te, const tm_field *to, int nact)
     {
-        return normal_core(g, out, in, te, to, sp->pc, sp->dagger, s, d_list, nact);
+        // every source active: no list (the operator may then pair sources, tune entry m:16)
+        return normal_core(g, out, in, te, to, sp->pc, sp->dagger, s, nact == nrhs ? nullptr : d_list, nact);
     }
 };
 
