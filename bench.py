@@ -284,17 +284,21 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.quick and (args.prec, nf, recon, L, args.csw) != ("f32", 2, 12, (32, 32, 32, 64), 0.0):
         args.quick = True  # the extra sections describe the default workload only
     if rank == 0 and not args.quick:
-        result["e2e"] = e2e_ours(args, tmq, g, psi_np, dev, flops_step)
-        result["per_precision"] = per_precision(tmq, U, psi, dev, args)
-        result["l2_resident_16x16x16x32"] = l2_resident_section(tmq, dev, args)
-        result["table1_analog"] = table1_section(tmq, U, psi, dev, args)
-        result["cg"] = cg_section(tmq, g, U, psi, dev, args)
-        result["multi_rhs"] = multi_rhs_section(tmq, U, dev, args)
-        result["domain_decomposition"] = dd_section(tmq, U, psi, dev, args)
-        result["batching"] = batching_section(tmq, U, dev, args)
-        result["clover"] = clover_section(tmq, U, psi, dev, args)
-        result["differentiation"] = force_section(tmq, dev, args)
-        result["cpu_baseline"] = cpu_baseline(U_np, psi_np, args)
+        sections = [("e2e", lambda: e2e_ours(args, tmq, g, psi_np, dev, flops_step)),
+                    ("per_precision", lambda: per_precision(tmq, U, psi, dev, args)),
+                    ("l2_resident_16x16x16x32", lambda: l2_resident_section(tmq, dev, args)),
+                    ("table1_analog", lambda: table1_section(tmq, U, psi, dev, args)),
+                    ("cg", lambda: cg_section(tmq, g, U, psi, dev, args)),
+                    ("multi_rhs", lambda: multi_rhs_section(tmq, U, dev, args)),
+                    ("domain_decomposition", lambda: dd_section(tmq, U, psi, dev, args)),
+                    ("batching", lambda: batching_section(tmq, U, dev, args)),
+                    ("clover", lambda: clover_section(tmq, U, psi, dev, args)),
+                    ("differentiation", lambda: force_section(tmq, dev, args)),
+                    ("cpu_baseline", lambda: cpu_baseline(U_np, psi_np, args))]
+        only = set(args.only.split(",")) if args.only else None
+        for name, fn in sections:
+            if only is None or name in only:
+                result[name] = fn()
     result["input_generation_s"] = round(gen_s, 2)
     g.close()
     return result
@@ -1001,6 +1005,7 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline storage (profiling runs)")
     ap.add_argument("--nf", type=int, default=2, choices=[1, 2], help="flavours of the headline step (profiling runs)")
     ap.add_argument("--recon", type=int, default=12, choices=[18, 12, 8], help="link storage (profiling runs)")
+    ap.add_argument("--only", default=None, help="comma-separated extra sections to run (default: all)")
     ap.add_argument("--solve", default=None, choices=["cg", "mixed_f32", "mixed_f16"],
                     help="profiling run: only this solve (asymmetric PC, 1e-10) of the headline system, twice")
     ap.add_argument("--force", default=None, choices=["f32", "f64"],
