@@ -914,6 +914,37 @@ def solve_only(args):
     return {"solve": args.solve, "lattice": list(L_FULL), "runs": out}
 
 
+def multi_only(args):
+    """M_asym on 16 Z2 sources in one multi-RHS launch per factor (the handle's default multi-RHS
+    form), at the headline lattice: the command the multi-RHS kernel's profile is captured on."""
+    import torch
+
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import inputs
+    nf = args.nf
+    p = tmq.Params(L_FULL, KAPPA, MU_ND if nf == 2 else MU_DEG, EPS_ND if nf == 2 else 0.0,
+                   flavor=tmq.TM_NDEG_DOUBLET if nf == 2 else tmq.TM_TWIST_PLUS, recon=args.recon)
+    prec = {"f32": tmq.TM_PREC_F32, "f16": tmq.TM_PREC_F16}[args.multi]
+    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L_FULL, 1002)).cuda(), precs=(prec,))
+    N = 16
+    xe = tmq.noise_z2(g, tmq.Field(g, prec, N), 0, 5000)
+    out, tmp = tmq.Field(g, prec, N), tmq.Field(g, prec, N)
+    for _ in range(args.warmup):
+        tmq.precond_op(g, out, xe, tmp, 0, False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        tmq.precond_op(g, out, xe, tmp, 0, False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    table = tmq.tune_export(g)
+    g.close()
+    return {"multi": args.multi, "flavours": nf, "lattice": list(L_FULL), "nrhs": N, "us_per_source": round(ms / N * 1e3, 1),
+            "launch_table": table}
+
+
 def force_only(args):
     """tm_force (projected) at 24^3x48 one flavour in FP32 or FP64: the command the force kernel's
     profile is captured on; prints its time and algorithmic bandwidth."""
@@ -1008,6 +1039,8 @@ def main():
     ap.add_argument("--only", default=None, help="comma-separated extra sections to run (default: all)")
     ap.add_argument("--solve", default=None, choices=["cg", "mixed_f32", "mixed_f16"],
                     help="profiling run: only this solve (asymmetric PC, 1e-10) of the headline system, twice")
+    ap.add_argument("--multi", default=None, choices=["f32", "f16"],
+                    help="profiling run: only the 16-source multi-RHS M_asym (--nf flavours), --warmup + --steps times")
     ap.add_argument("--force", default=None, choices=["f32", "f64"],
                     help="profiling run: only tm_force at 24^3x48 (one flavour), --warmup + --steps launches")
     args = ap.parse_args()
@@ -1020,9 +1053,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.solve or args.force:
+    if args.solve or args.force or args.multi:
         if rank == 0:
-            print(json.dumps(solve_only(args) if args.solve else force_only(args)), flush=True)
+            fn = solve_only if args.solve else (force_only if args.force else multi_only)
+            print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:
         import torch

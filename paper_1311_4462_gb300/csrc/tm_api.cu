@@ -673,8 +673,8 @@ bool normal_red_supported(const tm_gauge *g, int prec, int dagger)
     const int pidx = prec_index(prec);
     if (pidx < 0 || pidx > 2 || dagger || g->csw != 0.0 || g->dd || !g->links[pidx]) return false;
     const int v = g->tune[pidx][0].variant;
-    const size_t blocks = (size_t)(g->Vh + 127) / 128;
-    return v >= 6 && v <= 9 && blocks * sizeof(double) <= g->scratch_bytes - SCRATCH_PARTIALS_OFF;
+    const size_t blocks = (size_t)(g->Vh + 127) / 128;  // four partial sums (warps) per block
+    return v >= 6 && v <= 9 && 4 * blocks * sizeof(double) <= g->scratch_bytes - SCRATCH_PARTIALS_OFF;
 }
 
 // out = A^dag A in with A = M_pc, or A = M_pc^dag when dagger (tm_normal_op).  For the symmetric
@@ -713,6 +713,7 @@ tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *
                           : launch_dslash_red_p16(a, g->nf, g->p.recon, variant, *red, s);
         }
         TM_TRY(cuda_check(e, "fused-reduction launch"));
+        TM_TRY(cuda_check(launch_finish_partials(red->partials, 4L * ((g->Vh + 127) / 128), *red, s), "reduction finish"));
         return precond_core(g, out_e, te_e, tmp_o, TM_PC_ASYM, 1, s, nullptr, 1);
     }
     if (pc == TM_PC_SYM && !dagger && g->csw == 0.0) {
@@ -844,8 +845,8 @@ tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_m
         if ((i == 1 || i == 2) && (nd || p->recon != 18))
             for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(nd && i == 1) ? 8 : 9, 128};
         // multi-RHS shape, measured at 32^3x64 on 16 sources: the staged form with 4 sources per block
-        // for the binary32 / binary16 doublet, with 2 for one flavour; FP64 the register form, 4
-        g->multi_rpb[i] = (i == 1 || i == 2) ? (nd ? 14 : 12) : 4;
+        // for the binary32 / binary16 doublet, paired sources for one flavour; FP64 the register form, 4
+        g->multi_rpb[i] = (i == 1 || i == 2) ? (nd ? 14 : 16) : 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
     }

@@ -217,6 +217,23 @@ static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
     X(PDF, PDF, P32, PDF)     \
     X(PDF, PDF, P16, PDF)
 
+// The end of a reduction whose partial sums another kernel wrote (the hopping kernel's fused
+// reduction, one partial per warp): one block, thread t adds partials t, t + 256, ... in order,
+// then the block tree, then the scalar update -- a fixed order, so the result is reproducible.
+__global__ void __launch_bounds__(256) k_finish_partials(const double *__restrict__ partials, long n, RedArgs r)
+{
+    double s = 0.0;
+    for (long b = threadIdx.x; b < n; b += blockDim.x) s += partials[b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) apply_fin(s, r, 0);
+}
+
+cudaError_t launch_finish_partials(const double *partials, long n, const RedArgs &r, cudaStream_t s)
+{
+    k_finish_partials<<<1, 256, 0, s>>>(partials, n, r);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s)
 {
     a.Vh = g->Vh;

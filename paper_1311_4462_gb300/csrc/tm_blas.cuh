@@ -110,6 +110,26 @@ __device__ __forceinline__ double block_sum(double v)
 
 // Write this block's partial for column `col` (one column per rhs = blockIdx.y); the last block
 // of the whole grid sums every column in block order and applies `fin` per column.
+// The scalar update that ends a reduction of column c (one right-hand side) with the sum s.
+__device__ __forceinline__ void apply_fin(double s, const RedArgs &r, int c)
+{
+    double *S = r.scalars;
+    const int R = TM_MAX_RHS;
+    const bool active = !r.active || r.active[c];
+    switch (r.fin) {
+    case FIN_STORE: S[r.slot * R + c] = s; break;
+    case FIN_ALPHA:  // pAp -> alpha = rr / pAp
+        S[SL_PAP * R + c] = s;
+        S[SL_ALPHA * R + c] = (active && s != 0.0) ? S[SL_RR * R + c] / s : 0.0;
+        break;
+    case FIN_BETA:  // |r|^2 new -> beta = rr_new / rr, rr = rr_new
+        S[SL_RRNEW * R + c] = s;
+        S[SL_BETA * R + c] = (active && S[SL_RR * R + c] != 0.0) ? s / S[SL_RR * R + c] : 0.0;
+        if (active) S[SL_RR * R + c] = s;
+        break;
+    }
+}
+
 __device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
 {
     const int col = blockIdx.y;
@@ -132,27 +152,14 @@ __device__ __forceinline__ void grid_finish(double part, const RedArgs &r)
         for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += pp[b];
         s = block_sum(s);
         __syncthreads();  // block_sum's shared slots are reused by the next column
-        if (threadIdx.x != 0) continue;
-        double *S = r.scalars;
-        const int R = TM_MAX_RHS;
-        const bool active = !r.active || r.active[c];
-        switch (r.fin) {
-        case FIN_STORE: S[r.slot * R + c] = s; break;
-        case FIN_ALPHA:  // pAp -> alpha = rr / pAp
-            S[SL_PAP * R + c] = s;
-            S[SL_ALPHA * R + c] = (active && s != 0.0) ? S[SL_RR * R + c] / s : 0.0;
-            break;
-        case FIN_BETA:  // |r|^2 new -> beta = rr_new / rr, rr = rr_new
-            S[SL_RRNEW * R + c] = s;
-            S[SL_BETA * R + c] = (active && S[SL_RR * R + c] != 0.0) ? s / S[SL_RR * R + c] : 0.0;
-            if (active) S[SL_RR * R + c] = s;
-            break;
-        }
+        if (threadIdx.x == 0) apply_fin(s, r, c);
     }
     if (threadIdx.x == 0) *r.counter = 0u;  // ready for the next launch on this stream
 }
 
 cudaError_t launch_site_op(const tm_gauge *g, SiteOpArgs a, int nrhs, cudaStream_t s);
+// one block sums n partials (column 0) in a fixed order and applies r.fin (tm_blas.cu)
+cudaError_t launch_finish_partials(const double *partials, long n, const RedArgs &r, cudaStream_t s);
 
 inline FieldRef fref(const tm_field *f) { return FieldRef{f->data, f->norm, f->prec}; }
 inline FieldRef fnone() { return FieldRef{nullptr, nullptr, 0}; }

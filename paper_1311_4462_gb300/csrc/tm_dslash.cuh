@@ -1340,8 +1340,9 @@ __device__ __forceinline__ double async_site(const DslashArgs<typename Traits<PR
     return part;
 }
 
-// RED: the launch also reduces its output (async_site) into red (the last block finishes the sum
-// in block order and applies red.fin, as the site-wise reductions do).
+// RED: the launch also reduces its output (async_site): each warp writes the sum of its 32 sites'
+// shares to red.partials[4 * block + warp] (warp shuffles, no block barrier); k_finish_partials
+// then adds them in a fixed order and applies red.fin.
 template <int PREC, int NF, int RECON, int MINB, bool CLOV = false, int NB = 2, bool PRO = false, bool PAIR = false,
           bool RED = false>
 __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a,
@@ -1354,11 +1355,13 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_async(const __grid_constan
         if (cb >= a.cb0 + a.ncb) return;
         async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR>(a, cb, tid, smem_async, nullptr, nullptr);
     } else {
-        double part = 0.0;  // every thread reaches the block reduction
+        double part = 0.0;  // every lane takes part in the warp reduction
         if (cb < a.cb0 + a.ncb)
             part = async_site<PREC, NF, RECON, CLOV, NB, PRO, false, PAIR, false, true>(a, cb, tid, smem_async, nullptr,
                                                                                           nullptr);
-        grid_finish(block_sum(part), red);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if ((tid & 31) == 0) red.partials[(size_t)blockIdx.x * 4 + (tid >> 5)] = part;
     }
 }
 
