@@ -342,9 +342,12 @@ tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double
 /*
  * out = a x + b y on one parity field (y = NULL: out = a x), every right-hand side, the solvers'
  * site-wise linear combination (sec. 2.2, the BLAS of CG) offered for callers that combine
- * solutions, e.g. the gradient 2 X of the pseudofermion action.  out, x, y share a precision
- * and nrhs; out may alias x or y.  Arithmetic in FP64 for FP64 fields, double-float for DF64,
- * FP32 otherwise.  Asynchronous on `stream`.  Errors: TM_ERR_ARG, TM_ERR_CUDA.
+ * solutions, e.g. the gradient 2 X of the pseudofermion action.  out, x, y share nrhs; out may
+ * alias x or y.  Precisions: all equal, or the mixed combinations the solvers use (an FP64 or
+ * DF64 out / y with an FP32 or FP16 x and the reverse conversions, e.g. out FP32 = x FP64, or
+ * out FP64 = x FP32 + y FP64); others return TM_ERR_ARG.  Arithmetic in FP64 when a field is
+ * FP64, double-float for DF64, FP32 otherwise.  Asynchronous on `stream`.
+ * Errors: TM_ERR_ARG, TM_ERR_CUDA.
  */
 tm_status tm_axpby(const tm_gauge *g, const tm_field *out, double a, const tm_field *x, double b, const tm_field *y,
                    void *stream);
@@ -392,7 +395,9 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
  * or 8) of the register form, or 12 / 14 for the staged form (the pipeline of 8 / 9 with links
  * copied through L1) with 2 / 4 right-hand sides per block, or 16 (one flavour): with every
  * right-hand side of an even count, two sources at a time through the doublet's staged kernels
- * (a one-flavour field with 2k sources has a doublet field's layout with k), else as 14; clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
+ * (a one-flavour field with 2k sources has a doublet field's layout with k), else as 14; 32 / 34
+ * / 36 = 12 / 14 / 16 with the blocks ordered group by group (one sweep over the sites per group
+ * of sources) instead of interleaving the groups of a site block; clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline;
  * fused-operator entries "f32:p:1" = precision:p:1 when tm_precond_op runs as one fused launch
  * (FP64 and FP32; see tm_device_status).  Import accepts any subset of the entries; an

@@ -353,8 +353,9 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
     // two sources at a time through the doublet's kernels -- a one-flavour field with 2k sources has
     // the layout of a doublet field with k -- with the one-flavour local operator on both
     // "flavours"; the doublet's staged form pairs the two sources in its packed FMAs.
-    if (multi && act == nullptr && g->nf == 1 && pidx <= 2 && g->multi_rpb[pidx] == 16 && (nact & 1) == 0 &&
-        nact == out->nrhs) {
+    if (multi && act == nullptr && g->nf == 1 && pidx <= 2 && (g->multi_rpb[pidx] == 16 || g->multi_rpb[pidx] == 36) &&
+        (nact & 1) == 0 && nact == out->nrhs) {
+        const int form = g->multi_rpb[pidx] == 36 ? 34 : 14;
         auto diag = [](const Twist<double> &t) {
             Twist<double> d = t;
             for (int gi = 0; gi < 2; gi++) {
@@ -373,7 +374,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.tw_epi = de;
             a.tw_pro = dp;
             a.tw_acc = da;
-            e = launch_dslash_multi_p64(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s);
+            e = launch_dslash_multi_p64(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s);
         } else {
             DslashArgs<float> a;
             fill_common(a, g, out, in, x, out_parity, pidx);
@@ -383,8 +384,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.tw_epi = to_float(de);
             a.tw_pro = to_float(dp);
             a.tw_acc = to_float(da);
-            e = pidx == 1 ? launch_dslash_multi_p32(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s)
-                          : launch_dslash_multi_p16(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, 14, s);
+            e = pidx == 1 ? launch_dslash_multi_p32(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s)
+                          : launch_dslash_multi_p16(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s);
         }
         return cuda_check(e, "dslash launch (paired sources)");
     }
@@ -1278,10 +1279,10 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             f[k].nrhs = nr;
         }
         const Twist<double> Ri = make_twist(g, TW_RINV, 0);
-        const int rpbs[6] = {2, 4, 8, 12, 14, 16};
+        const int rpbs[9] = {2, 4, 8, 12, 14, 32, 34, 16, 36};  // the paired forms last: one flavour only
         float best = 1e30f;
         int bestr = g->multi_rpb[pi];
-        for (int ri = 0; ri < (g->nf == 1 ? 6 : 5) && st == TM_OK; ri++) {
+        for (int ri = 0; ri < (g->nf == 1 ? 9 : 7) && st == TM_OK; ri++) {
             g->multi_rpb[pi] = rpbs[ri];
             float ms = 0;
             for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -1359,7 +1360,9 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
         if (sscanf(p, "%3[a-z0-9]:m:%d%n", name, &block, &used) == 2 && used > 0) {
             // multi-RHS entry "<prec>:m:<right-hand sides per block>"
             const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
-            if (pi < 0 || (block != 2 && block != 4 && block != 8 && block != 12 && block != 14 && block != 16)) {
+            const bool okm = block == 2 || block == 4 || block == 8 || block == 12 || block == 14 || block == 16 ||
+                             block == 32 || block == 34 || block == 36;
+            if (pi < 0 || !okm) {
                 set_error("tm_tune_import: invalid entry '%.32s'", p);
                 return TM_ERR_ARG;
             }

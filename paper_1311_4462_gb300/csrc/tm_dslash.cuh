@@ -1456,14 +1456,18 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
 template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
 __global__ void __launch_bounds__(128, 3)
     k_dslash_multi_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act,
-                         int nact, int nrhs)
+                         int nact, int nrhs, int gmajor)
 {
     extern __shared__ __align__(16) char smem_async[];
     constexpr int WPR = 4 / RPB;  // warps per right-hand side
     const int tid = threadIdx.x, w = tid >> 5;
     const int ngrp = (nact + RPB - 1) / RPB;
-    const int grp = (int)(blockIdx.x % ngrp);
-    const long sblk = blockIdx.x / ngrp;
+    // block order: interleaved (the groups of RPB sources of a site block one after another, so the
+    // links are shared through L2 by all sources) or group-major (one sweep over the sites per group:
+    // the links are read once per group, but a sweep's neighbour spinors stay within L2's reach)
+    const long nsblk = ((long)a.Vh + 32 * WPR - 1) / (32 * WPR);
+    const int grp = gmajor ? (int)(blockIdx.x / nsblk) : (int)(blockIdx.x % ngrp);
+    const long sblk = gmajor ? (long)(blockIdx.x % nsblk) : (long)(blockIdx.x / ngrp);
     const int slot = grp * RPB + w / WPR;
     const long cb = sblk * (32 * WPR) + (w % WPR) * 32 + (tid & 31);
     if (slot >= nact || cb >= a.Vh) return;
@@ -1474,7 +1478,7 @@ __global__ void __launch_bounds__(128, 3)
 
 template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
 cudaError_t launch_multi_async(const DslashArgs<typename Traits<PREC>::real> &a, const int *act, int nact, int nrhs,
-                               cudaStream_t s)
+                               bool gmajor, cudaStream_t s)
 {
     constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
     static std::atomic<unsigned long long> opted{0};
@@ -1490,7 +1494,7 @@ cudaError_t launch_multi_async(const DslashArgs<typename Traits<PREC>::real> &a,
     }
     constexpr int SPB = 128 / RPB;  // sites per block
     const unsigned grid = (unsigned)(((long)a.Vh + SPB - 1) / SPB * ((nact + RPB - 1) / RPB));
-    k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR><<<grid, 128, bytes, s>>>(a, act, nact, nrhs);
+    k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR><<<grid, 128, bytes, s>>>(a, act, nact, nrhs, gmajor ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1703,7 +1707,11 @@ template <int PREC>
 cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::real> &a, int nf, int recon, bool pro,
                                      const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
 {
-    if (rpb == 16) rpb = 14;  // paired sources are arranged by the caller; otherwise the staged form
+    // staged forms: 12 / 14 (2 / 4 per block, interleaved order), + 20 for the group-major order;
+    // 16 / 36 (paired sources) are arranged by the caller, otherwise they run as 14 / 34
+    const bool gmajor = rpb >= 32;
+    if (gmajor) rpb -= 20;
+    if (rpb == 16) rpb = 14;
     if (rpb == 12 || rpb == 14) {
         // staged multi-RHS forms, 2 or 4 right-hand sides per block; the hop pairs as form 8 / 9 does
         // (binary32 and binary16, except one flavour with 18-real links)
@@ -1711,8 +1719,8 @@ cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::rea
 #define TM_MA1(NF, R, P)                                                                                 \
     {                                                                                                    \
         constexpr bool PR = CP && (NF == 2 || R != 18);                                                  \
-        return rpb == 12 ? launch_multi_async<PREC, NF, R, P, 2, PR>(a, act, nact, nrhs, s)              \
-                         : launch_multi_async<PREC, NF, R, P, 4, PR>(a, act, nact, nrhs, s);             \
+        return rpb == 12 ? launch_multi_async<PREC, NF, R, P, 2, PR>(a, act, nact, nrhs, gmajor, s)      \
+                         : launch_multi_async<PREC, NF, R, P, 4, PR>(a, act, nact, nrhs, gmajor, s);     \
     }
 #define TM_MAR(NF, P)                          \
     switch (recon) {                           \

@@ -410,12 +410,12 @@ tm_status tm_axpby(const tm_gauge *g, const tm_field *out, double a, const tm_fi
     if (!g || !out || !x || !out->data || !x->data) { set_error("tm_axpby: null argument"); return TM_ERR_ARG; }
     const bool hasy = y != nullptr;
     if (hasy && !y->data) { set_error("tm_axpby: null y data"); return TM_ERR_ARG; }
-    if (out->prec != x->prec || (hasy && y->prec != x->prec)) {
-        set_error("tm_axpby: out, x and y must share a precision");
+    if (prec_index(x->prec) < 0 || prec_index(out->prec) < 0 || (hasy && prec_index(y->prec) < 0)) {
+        set_error("tm_axpby: unknown precision");
         return TM_ERR_ARG;
     }
-    if (prec_index(x->prec) < 0) { set_error("tm_axpby: unknown precision %d", x->prec); return TM_ERR_ARG; }
-    if ((x->prec == TM_PREC_F16) && (!out->norm || !x->norm || (hasy && !y->norm))) {
+    if ((out->prec == TM_PREC_F16 && !out->norm) || (x->prec == TM_PREC_F16 && !x->norm) ||
+        (hasy && y->prec == TM_PREC_F16 && !y->norm)) {
         set_error("tm_axpby: FP16 fields need their norm arrays");
         return TM_ERR_ARG;
     }
@@ -432,7 +432,13 @@ tm_status tm_axpby(const tm_gauge *g, const tm_field *out, double a, const tm_fi
     sa.C = fref(out);
     sa.ca = sv(a);
     sa.cb = sv(b);
-    return cuda_check(launch_site_op(g, sa, x->nrhs, (cudaStream_t)stream), "tm_axpby");
+    const cudaError_t e = launch_site_op(g, sa, x->nrhs, (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) {
+        set_error("tm_axpby: precision combination out %d, x %d, y %d is not offered", out->prec, x->prec,
+                  hasy ? y->prec : x->prec);
+        return TM_ERR_ARG;
+    }
+    return cuda_check(e, "tm_axpby");
 }
 
 tm_status tm_dot(const tm_gauge *g, const tm_field *a, const tm_field *b, double *re_out, void *stream)

@@ -271,38 +271,98 @@ def _fields(slabs, prec=TM_PREC_F64):
     return [s.field(prec) for s in slabs]
 
 
-def cg(slabs, xs, bs, transport, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000):
+def cg(slabs, xs, bs, transport, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter=20000, sloppy_prec=None,
+       delta=1e-5):
     """CG on the normal equations A^dag A x = A^dag b of the decomposed even-odd operator A = M_pc
-    (A = M_pc^dag when dagger), FP64 fields, x starting from zero: the solve_type NORMOP of sec. 2.2
-    with every reduction summed over the ranks.  Stops when the recursive residual reaches tol, then
-    recomputes the true residual |A^dag b - A^dag A x| / |A^dag b| and restarts from it (at most four
-    times) while it is above tol.  Returns a dict with iterations, restarts and true_residual."""
-    ar = transport.allreduce
-    bh, r, p, Ap, te, to = (_fields(slabs) for _ in range(6))
+    (A = M_pc^dag when dagger), FP64 fields x, b, x starting from zero: the solve_type NORMOP of
+    sec. 2.2 with every reduction summed over the ranks.
 
-    def normal(out, inp):
-        precond_op(slabs, te, inp, to, transport, pc, dagger)
-        precond_op(slabs, out, te, to, transport, pc, not dagger)
+    sloppy_prec None: FP64 CG; it stops when the recursive residual reaches tol, recomputes the true
+    residual |A^dag b - A^dag A x| / |A^dag b| and restarts from it (at most four times) while it is
+    above tol.  sloppy_prec TM_PREC_F32: the reliable-update mixed CG of sec. 3 (ref. [Clark:2009wm])
+    as tm_solve runs it -- FP32 search direction, residual and solution increment, and when the
+    sloppy residual has fallen by delta since the last update (or meets tol) the increment is added
+    to the FP64 x and the true residual recomputed in FP64.  Returns a dict with iterations,
+    reliable updates / restarts, true_residual and converged."""
+    ar = transport.allreduce
+    tol2 = tol * tol
+    bh, r, Ap, te, to = (_fields(slabs) for _ in range(5))
+
+    def normal(out, inp, tes, tos):
+        precond_op(slabs, tes, inp, tos, transport, pc, dagger)
+        precond_op(slabs, out, tes, tos, transport, pc, not dagger)
 
     def n2(fs):
         return ar([norm2(s.g, f) for s, f in zip(slabs, fs)])
 
     precond_op(slabs, bh, bs, to, transport, pc, not dagger)  # bhat = A^dag b
     bb = n2(bh)
-    for s, x in zip(slabs, xs):
+    for x in xs:
         x.zero_()
     if bb == 0.0:
-        return {"iterations": 0, "restarts": 0, "true_residual": 0.0}
-    for s, rr_, b_ in zip(slabs, r, bh):
-        axpby(s.g, rr_, 1.0, b_)
+        return {"iterations": 0, "restarts": 0, "true_residual": 0.0, "converged": True}
+    for s, r_, b_ in zip(slabs, r, bh):
+        axpby(s.g, r_, 1.0, b_)
     r2 = n2(r)
-    it = restarts = 0
-    while r2 > tol * tol * bb and it < maxiter and restarts < 5:
+    it = nrel = 0
+    if sloppy_prec is not None:
+        if int(sloppy_prec) != 4:
+            raise ValueError("dd.cg: the sloppy fields are FP32 (TM_PREC_F32)")
+        rs, ps, Aps, tes, tos, xsl = (_fields(slabs, 4) for _ in range(6))
+        for s, a, b_ in zip(slabs, rs, r):
+            axpby(s.g, a, 1.0, b_)  # FP32 copy of the FP64 residual
+        for s, a, b_ in zip(slabs, ps, rs):
+            axpby(s.g, a, 1.0, b_)
+        for x in xsl:
+            x.zero_()
+        rr = n2(rs)
+        maxr = math.sqrt(r2)
+        converged = r2 <= tol2 * bb
+        while not converged and it < maxiter:
+            normal(Aps, ps, tes, tos)
+            pAp = ar([dot(s.g, p_, a_) for s, p_, a_ in zip(slabs, ps, Aps)])
+            alpha = rr / pAp
+            for s, x, p_, r_, a_ in zip(slabs, xsl, ps, rs, Aps):
+                axpby(s.g, x, 1.0, x, alpha, p_)
+                axpby(s.g, r_, 1.0, r_, -alpha, a_)
+            rnew = n2(rs)
+            it += 1
+            if not math.isfinite(rnew):
+                raise L.TMError(L.TM_ERR_NAN, f"dd.cg: non-finite residual at iteration {it}")
+            rn = math.sqrt(rnew)
+            maxr = max(maxr, rn)
+            if rn < delta * maxr or rnew <= tol2 * bb or it == maxiter:
+                # reliable update: x += x_sloppy in FP64, true residual recomputed in FP64
+                for s, x, d in zip(slabs, xs, xsl):
+                    axpby(s.g, x, 1.0, d, 1.0, x)
+                for x in xsl:
+                    x.zero_()
+                normal(Ap, xs, te, to)
+                for s, r_, b_, a_ in zip(slabs, r, bh, Ap):
+                    axpby(s.g, r_, 1.0, b_, -1.0, a_)
+                r2 = n2(r)
+                nrel += 1
+                if r2 <= tol2 * bb:
+                    converged = True
+                    break
+                for s, a, b_ in zip(slabs, rs, r):
+                    axpby(s.g, a, 1.0, b_)
+                rnew = n2(rs)
+                maxr = math.sqrt(r2)
+            beta = rnew / rr
+            rr = rnew
+            for s, p_, r_ in zip(slabs, ps, rs):
+                axpby(s.g, p_, 1.0, r_, beta, p_)
+        return {"iterations": it, "reliable_updates": nrel, "true_residual": math.sqrt(r2 / bb),
+                "converged": r2 <= tol2 * bb}
+    p = _fields(slabs)
+    restarts = 0
+    while r2 > tol2 * bb and it < maxiter and restarts < 5:
         for s, p_, r_ in zip(slabs, p, r):
             axpby(s.g, p_, 1.0, r_)
         rr = r2
-        while rr > tol * tol * bb and it < maxiter:
-            normal(Ap, p)
+        while rr > tol2 * bb and it < maxiter:
+            normal(Ap, p, te, to)
             pAp = ar([dot(s.g, p_, a_) for s, p_, a_ in zip(slabs, p, Ap)])
             alpha = rr / pAp
             for s, x, p_, r_, a_ in zip(slabs, xs, p, r, Ap):
@@ -312,17 +372,17 @@ def cg(slabs, xs, bs, transport, pc=TM_PC_ASYM, dagger=False, tol=1e-10, maxiter
             it += 1
             if not math.isfinite(rnew):
                 raise L.TMError(L.TM_ERR_NAN, f"dd.cg: non-finite residual at iteration {it}")
-            if rnew <= tol * tol * bb:
+            if rnew <= tol2 * bb:
                 rr = rnew
                 break
             beta = rnew / rr
             rr = rnew
             for s, p_, r_ in zip(slabs, p, r):
                 axpby(s.g, p_, 1.0, r_, beta, p_)
-        normal(Ap, xs)  # true residual r = bhat - A^dag A x
+        normal(Ap, xs, te, to)  # true residual r = bhat - A^dag A x
         for s, r_, b_, a_ in zip(slabs, r, bh, Ap):
             axpby(s.g, r_, 1.0, b_, -1.0, a_)
         r2 = n2(r)
         restarts += 1
     return {"iterations": it, "restarts": restarts - 1, "true_residual": math.sqrt(r2 / bb),
-            "converged": r2 <= tol * tol * bb}
+            "converged": r2 <= tol2 * bb}

@@ -156,6 +156,16 @@ def test_dd_cg_full_solve(case):
     assert torch.equal(tmq.unpack(g, bp, 0), dd.unpack_slabs(slabs, bps, 0))
     tmq.solve(g, xe, bp, solver="cg", tol=1e-10)
     assert rel(dd.unpack_slabs(slabs, xes, 0).cpu().numpy(), tmq.unpack(g, xe, 0).cpu().numpy()) < 1e-7
+    # the decomposed reliable-update mixed CG (FP32 sloppy fields, FP64 updates), both PC forms
+    for pc in (0, 1):
+        bps2, xes2, xos2 = ([s.field() for s in slabs] for _ in range(3))
+        dd.prepare_rhs(slabs, bps2, bes, bos, tr, pc)
+        st = dd.cg(slabs, xes2, bps2, tr, pc=pc, tol=1e-10, sloppy_prec=4)
+        assert st["converged"] and st["true_residual"] <= 1e-10 and st["reliable_updates"] >= 1
+        dd.reconstruct_odd(slabs, xos2, bos, xes2, tr)  # both forms solve for the same psi_e (eq. 2.4)
+        x2 = dd.unpack_slabs(slabs, xes2, 0)
+        dd.unpack_slabs(slabs, xos2, 1, out=x2)
+        assert rel(orc.apply_M(po, U, x2.cpu().numpy()), chi) < 1e-7
 
 
 def test_dd_argument_errors():

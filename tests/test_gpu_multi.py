@@ -32,11 +32,12 @@ def make(case, nrhs, recon=12):
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", [8, 4, 2])
-@pytest.mark.parametrize("rpb", [2, 4, 8, 12, 14, 16], ids=["rpb2", "rpb4", "rpb8", "staged2", "staged4", "paired"])
+@pytest.mark.parametrize("rpb", [2, 4, 8, 12, 14, 16, 32, 34, 36],
+                         ids=["rpb2", "rpb4", "rpb8", "staged2", "staged4", "paired", "staged2g", "staged4g", "pairedg"])
 def test_multi_rhs_operators_match_oracle(case, prec, rpb):
     # not a multiple of any block shape: the last group of every shape is ragged; the paired-source
     # form (one flavour, two sources through the doublet's kernels) needs an even count
-    nr = 6 if rpb == 16 else 5
+    nr = 6 if rpb in (16, 36) else 5
     tmq, p, po, U, g, src = make(case, nr)
     tmq.tune_import(g, f"f64:m:{rpb} f32:m:{rpb} f16:m:{rpb}")
     t = torch.from_numpy(src)

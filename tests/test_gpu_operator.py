@@ -254,7 +254,7 @@ def test_autotune_roundtrip_and_parity():
     clov = [e for e in entries if e.split(":")[1] == "c"]
     fused = [e for e in entries if e.split(":")[1] == "p"]
     assert len(single) == 6 and all(len(e.split(":")) == 4 for e in single)
-    assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8", "12", "14", "16") for e in multi)
+    assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8", "12", "14", "16", "32", "34", "36") for e in multi)
     assert len(clov) == 3 and all(e.split(":")[2] in ("1", "3", "4", "6") for e in clov)
     assert len(fused) == 2 and all(e.split(":")[2] in ("0", "1") for e in fused)
     tmq.tune_import(g, table)
