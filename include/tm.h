@@ -382,7 +382,8 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * uses defaults (FP64 capped 128 x 4; FP32 and FP16 the shared-memory pipeline with the paired
  * hop: two buffers for the FP32 doublet (8), three otherwise (9), except one flavour with
  * 18-real links, capped; multi-RHS: for FP32 / FP16 the staged form with 4 right-hand sides
- * per block (doublet) or paired sources (one flavour), the register form with 4 for FP64; clover 1 block per SM for FP64, 3 for FP16 and the FP32 doublet,
+ * per block in group-major order (doublet, 34) or paired sources (one flavour: FP32 36, FP16
+ * 16), the register form with 4 for FP64; clover 1 block per SM for FP64, 3 for FP16 and the FP32 doublet,
  * 4 for FP32 one flavour).
  */
 tm_status tm_autotune(tm_gauge *g, void *stream);

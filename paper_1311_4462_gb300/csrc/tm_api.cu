@@ -846,8 +846,9 @@ tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_m
         if ((i == 1 || i == 2) && (nd || p->recon != 18))
             for (int j = 0; j < 2; j++) g->tune[i][j] = tm_tune_entry{(nd && i == 1) ? 8 : 9, 128};
         // multi-RHS shape, measured at 32^3x64 on 16 sources: the staged form with 4 sources per block
-        // for the binary32 / binary16 doublet, paired sources for one flavour; FP64 the register form, 4
-        g->multi_rpb[i] = (i == 1 || i == 2) ? (nd ? 14 : 16) : 4;
+        // in group-major order for the binary32 / binary16 doublet, paired sources for one flavour
+        // (group-major for FP32); FP64 the register form, 4
+        g->multi_rpb[i] = (i == 1 || i == 2) ? (nd ? 34 : (i == 1 ? 36 : 16)) : 4;
         // measured on GB300 at 32^3x64: FP32 one flavour 4, doublet 3; FP16 3; FP64 insensitive
         if (i < 3) g->clov_minb[i] = i == 0 ? 1 : ((i == 1 && p->flavor != TM_NDEG_DOUBLET) ? 4 : 3);
     }
