@@ -182,3 +182,28 @@ def test_device_noise_matches_counter_definition(prec):
         else:
             assert np.abs(got[r] - ref).max() < 1e-3
     g.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", [8, 4, 2])
+@pytest.mark.parametrize("rpb", [4, 14, 16, 34, 36], ids=["rpb4", "staged4", "paired", "staged4g", "pairedg"])
+def test_multi_rhs_gives_the_single_rhs_bits(case, prec, rpb):
+    """Every multi-RHS form (register, staged, paired sources, either block order) performs the same
+    operations per source as the single-RHS forms, so each source's output has the same bits."""
+    nr = 6
+    tmq, p, po, U, g, src = make(case, nr)
+    name = {8: "f64", 4: "f32", 2: "f16"}[prec]
+    tmq.tune_import(g, f"{name}:m:{rpb}")
+    t = torch.from_numpy(src)
+    xe = tmq.pack(g, t, 0, prec, nrhs=nr)
+    for pc in (0, 1):
+        for dag in (False, True):
+            out, tmp = tmq.Field(g, prec, nr), tmq.Field(g, prec, nr)
+            tmq.precond_op(g, out, xe, tmp, pc, dag)
+            got = tmq.unpack(g, out, 0)
+            for r in range(nr):
+                x1 = tmq.pack(g, t[r], 0, prec)
+                o1, t1 = tmq.Field(g, prec), tmq.Field(g, prec)
+                tmq.precond_op(g, o1, x1, t1, pc, dag)
+                assert torch.equal(got[r], tmq.unpack(g, o1, 0)), (pc, dag, r)
+    g.close()
