@@ -142,6 +142,30 @@ __global__ void __launch_bounds__(256) k_site_op(SiteOpArgs a)
             for (int k = 0; k < 24; k++) part = fma(vb[k], vb[k], part);
             break;
         }
+        case OP_R_UPDATE: {  // B = r, D = Ap: r -= alpha Ap, then |r|^2 (the residual half of CG_UPDATE)
+            const T al = (T)sval(a.ca, rhs, a.red.scalars);
+            load_block<PB>(a.B, blk, cb, a.Vh, vb);
+            load_block<PD>(a.D, blk, cb, a.Vh, vd);
+#pragma unroll
+            for (int k = 0; k < 24; k++) vb[k] = fma(-al, vd[k], vb[k]);
+            store_block<PB>(a.B, blk, cb, a.Vh, vb);
+#pragma unroll
+            for (int k = 0; k < 24; k++) part = fma(vb[k], vb[k], part);
+            break;
+        }
+        case OP_XP_UPDATE: {  // A = p, C = x, D = r: x += alpha p, then p = r + beta p (one pass)
+            const T al = (T)sval(a.ca, rhs, a.red.scalars), be = (T)sval(a.cb, rhs, a.red.scalars);
+            load_block<PA>(a.A, blk, cb, a.Vh, va);
+            load_block<PC>(a.C, blk, cb, a.Vh, vc);
+#pragma unroll
+            for (int k = 0; k < 24; k++) vc[k] = fma(al, va[k], vc[k]);
+            store_block<PC>(a.C, blk, cb, a.Vh, vc);
+            load_block<PD>(a.D, blk, cb, a.Vh, vd);
+#pragma unroll
+            for (int k = 0; k < 24; k++) va[k] = fma(T(1), vd[k], be * va[k]);
+            store_block<PA>(a.A, blk, cb, a.Vh, va);
+            break;
+        }
         case OP_DOT: {
             load_block<PA>(a.A, blk, cb, a.Vh, va);
             load_block<PB>(a.B, blk, cb, a.Vh, vb);
@@ -204,6 +228,7 @@ static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
     X(P32, P32, P32, P32)     \
     X(P16, P16, P16, P16)     \
     X(P16, P16, P32, P16)     \
+    X(P16, P32, P32, P16)     \
     X(P32, P64, P64, P32)     \
     X(P64, P64, P32, P64)     \
     X(P64, P64, P16, P64)     \

@@ -16,7 +16,8 @@ constexpr size_t SCRATCH_SCALARS_OFF = 0;                                       
 constexpr size_t SCRATCH_COUNTER_OFF = SL_COUNT * TM_MAX_RHS * sizeof(double);  // 8 KB: ticket counter
 constexpr size_t SCRATCH_PARTIALS_OFF = 16384;                                  // per-block partial sums
 
-enum SiteOpCode { OP_AXPBY = 0, OP_CG_UPDATE = 1, OP_DOT = 2, OP_NORM = 3, OP_COPY = 4, OP_G5DOT_RE = 5, OP_G5DOT_IM = 6 };
+enum SiteOpCode { OP_AXPBY = 0, OP_CG_UPDATE = 1, OP_DOT = 2, OP_NORM = 3, OP_COPY = 4, OP_G5DOT_RE = 5, OP_G5DOT_IM = 6,
+                  OP_R_UPDATE = 7, OP_XP_UPDATE = 8 };
 enum FinCode { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
 
 struct FieldRef {

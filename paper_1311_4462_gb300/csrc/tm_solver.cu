@@ -291,14 +291,26 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
         bool converged = r2 <= tol2 * bb;
         while (!converged && it < sp->maxiter) {
             TRY(V.normal_op_alpha(&Aps, &ps, &tes, &tos));
-            TRY(V.site(OP_CG_UPDATE, fref(&ps), fref(&rs), fref(&xs), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
+            // r_s -= alpha A p with |r_s|^2; the increment x_s += alpha p waits for beta and shares
+            // the pass of the search-direction update (one field pass fewer per iteration)
+            TRY(V.site(OP_R_UPDATE, fref(&rs), fref(&rs), fnone(), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
                        FIN_STORE, SL_RRNEW));
             TRY(V.read(SL_RRNEW, &rr));
             it++;
             if (!isfinite(rr)) { set_error("tm_solve: non-finite residual at iteration %d", it); st = TM_ERR_NAN; goto done; }
             const double rn = sqrt(rr);
             if (rn > maxr) maxr = rn;
-            if (rn < sp->delta * maxr || rr <= tol2 * bb || it == sp->maxiter) {
+            const bool update = rn < sp->delta * maxr || rr <= tol2 * bb || it == sp->maxiter;
+            if (!update) {
+                k_scalar_beta<<<1, 32, 0, s>>>(V.S, 1, nullptr);
+                TRY(cuda_check(cudaGetLastError(), "beta"));
+                // x_s += alpha p ; p = r_s + beta p
+                TRY(V.site(OP_XP_UPDATE, fref(&ps), fnone(), fref(&xs), fref(&rs), sslot(SL_ALPHA, 1.0),
+                           sslot(SL_BETA, 1.0), 0, 0, 0));
+                continue;
+            }
+            TRY(V.axpby(&xs, sslot(SL_ALPHA, 1.0), &ps, sv(1.0), &xs));  // x_s += alpha p
+            {
                 // reliable update: fold the sloppy solution into x, recompute the true residual in FP64
                 TRY(V.axpby(x, sv(1.0), &xs, sv(1.0), x));
                 TRY(V.zero(&xs));
