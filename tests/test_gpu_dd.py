@@ -187,3 +187,37 @@ def test_dd_argument_errors():
     assert lib.tm_dd_dslash(s.g.h, s.field(4).ref(), f.ref(), 0, 0, None, 0, 0, None, None, Lb.TM_DD_ALL,
                             None) == Lb.TM_ERR_ARG  # the boundary needs faces
     assert lib.tm_dd_dslash(s.g.h, s.field(4).ref(), f.ref(), 0, 0, None, 0, 0, None, None, 7, None) == Lb.TM_ERR_ARG
+
+
+@pytest.mark.parametrize("recon", [18, 8])
+@pytest.mark.parametrize("prec", [8, 4, 2])
+def test_dd_other_link_formats(recon, prec):
+    """18- and 8-real links: the face of the backward hop carries the sender's decoded link product."""
+    import paper_1311_4462_gb300 as tmq
+    from paper_1311_4462_gb300 import dd
+    if recon == 8 and prec == 8:
+        pytest.skip("the same FP64 path as recon 12 (tested above); recon 8 decode is covered in FP32 / FP16")
+    L = (4, 2, 4, 8)
+    p = tmq.Params(L, 0.1612, 0.135, 0.15, flavor=tmq.TM_NDEG_DOUBLET, recon=recon)
+    po = orc.Params(L, 0.1612, 0.135, 0.15, flavor=2)
+    U = inputs.gauge_field(L, 1790)
+    psi = inputs.spinor_field(L, 2, 2790)
+    g = tmq.Gauge(p, torch.from_numpy(U))
+    tpsi = torch.from_numpy(psi).to("cuda")
+    xe = tmq.pack(g, tpsi, 0, prec)
+    out, tmp = tmq.Field(g, prec), tmq.Field(g, prec)
+    tr = dd.LocalTransport()
+    for R in (2, 4):
+        slabs = dd.make_slabs(p, torch.from_numpy(U).to("cuda"), R)
+        ins = dd.pack_slabs(slabs, dd.split_field(slabs, tpsi), 0, prec)
+        for pc, dag in ((0, False), (1, True)):
+            tmq.precond_op(g, out, xe, tmp, pc, dag)
+            outs, tmps = [s.field(prec) for s in slabs], [s.field(prec) for s in slabs]
+            dd.precond_op(slabs, outs, ins, tmps, tr, pc, dag)
+            got = dd.unpack_slabs(slabs, outs, 0)
+            assert torch.equal(got, tmq.unpack(g, out, 0)), (R, pc, dag)
+            ref = orc.apply_M_pc(po, U, orc.project_parity(po, psi, 0), sym=bool(pc), dagger=dag)
+            assert rel(got.cpu().numpy(), ref) < TOL[prec]
+        for s in slabs:
+            s.close()
+    g.close()
