@@ -195,8 +195,6 @@ def test_dd_other_link_formats(recon, prec):
     """18- and 8-real links: the face of the backward hop carries the sender's decoded link product."""
     import paper_1311_4462_gb300 as tmq
     from paper_1311_4462_gb300 import dd
-    if recon == 8 and prec == 8:
-        pytest.skip("the same FP64 path as recon 12 (tested above); recon 8 decode is covered in FP32 / FP16")
     L = (4, 2, 4, 8)
     p = tmq.Params(L, 0.1612, 0.135, 0.15, flavor=tmq.TM_NDEG_DOUBLET, recon=recon)
     po = orc.Params(L, 0.1612, 0.135, 0.15, flavor=2)
