@@ -573,7 +573,10 @@ def cg_section(tmq, g, U, psi, dev, args):
                 "reliable_updates": best["reliable_updates"], "true_residual": best["true_residual"],
                 "status": best["status"]}
 
-    res = {"tolerance": 1e-10, "residual": "FP64 |bhat - A^dag A x|/|bhat|, A = M_pc, bhat = A^dag b'"}
+    res = {"tolerance": 1e-10, "residual": "FP64 |bhat - A^dag A x|/|bhat|, A = M_pc, bhat = A^dag b'",
+           "links": "recon 12 for FP32 / FP16 / DF64, 18 reals for FP64 (TM_GAUGE_F64_FULL_LINKS)"}
+    # the solver's handle: FP64 links uncompressed (the FP64 operator is bound by the FP64 pipe)
+    g = tmq.Gauge(g.params, U, f64_full_links=True)
     b = psi
     be, bo = tmq.pack(g, b, 0, tmq.TM_PREC_F64), tmq.pack(g, b, 1, tmq.TM_PREC_F64)
     nd = {}
@@ -592,6 +595,8 @@ def cg_section(tmq, g, U, psi, dev, args):
                    nd[pname]["mixed_f32_df64_true_residual"]["ms"])
         nd[pname]["speedup_mixed_vs_fp64"] = round(nd[pname]["fp64_cg"]["ms"] / best, 2)
     res["doublet_32x32x32x64"] = nd
+    del be, bo, bp
+    g.close()
     # one flavour 16^3x32, kappa 0.1612, mu 0.004: FP64 CG + reconstruction, full-system residual
     L2 = (16, 16, 16, 32)
     p2 = tmq.Params(L2, KAPPA, MU_DEG, 0.0, flavor=tmq.TM_TWIST_PLUS, recon=12)
@@ -892,7 +897,7 @@ def solve_only(args):
     import paper_1311_4462_gb300 as tmq
     from paper_1311_4462_gb300 import inputs
     p = tmq.Params(L_FULL, KAPPA, MU_ND, EPS_ND, flavor=tmq.TM_NDEG_DOUBLET, recon=args.recon)
-    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L_FULL, 1002)).cuda())
+    g = tmq.Gauge(p, torch.from_numpy(inputs.gauge_field(L_FULL, 1002)).cuda(), f64_full_links=True)
     b = torch.from_numpy(inputs.spinor_field(L_FULL, 2, 2002)).cuda()
     be, bo = tmq.pack(g, b, 0, tmq.TM_PREC_F64), tmq.pack(g, b, 1, tmq.TM_PREC_F64)
     bp = tmq.Field(g, tmq.TM_PREC_F64)

@@ -96,7 +96,8 @@ typedef struct {
     double epsilon;       /* epsilon-bar of the doublet; must be 0 for TM_TWIST_PLUS/MINUS */
     int flavor;           /* tm_flavor */
     int t_antiperiodic;   /* 1: antiperiodic in time, 0: periodic */
-    int recon;            /* tm_recon, used for every precision of the gauge handle */
+    int recon;            /* tm_recon, used for every precision of the gauge handle (but see
+                             TM_GAUGE_F64_FULL_LINKS and the DF64 note above) */
 } tm_params;
 
 typedef struct {
@@ -125,9 +126,16 @@ tm_status tm_last_error(char *buf, size_t n);
 tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream, tm_gauge **out);
 
 /* tm_gauge_create packing only the link storage forms in prec_mask: bit 0 FP64, 1 FP32, 2 FP16,
- * 3 DF64 (0 = all, as tm_gauge_create).  An operator, solver or force call on fields of a storage
- * form the handle did not pack returns TM_ERR_ARG; a clover term needs the FP64 links.  32^3x64,
- * recon 12: FP64 805 MB, FP32 403 MB, FP16 201 MB, DF64 805 MB. */
+ * 3 DF64 (bits 0-3 all clear = all four, as tm_gauge_create).  An operator, solver or force call on
+ * fields of a storage form the handle did not pack returns TM_ERR_ARG; a clover term needs the
+ * FP64 links.  32^3x64, recon 12: FP64 805 MB, FP32 403 MB, FP16 201 MB, DF64 805 MB.
+ * Bit 4 (TM_GAUGE_F64_FULL_LINKS): the FP64 links keep all 18 reals whatever p->recon (1208 MB at
+ * 32^3x64); the other storage forms follow p->recon.  The FP64 hopping kernels are bound by the
+ * FP64 pipe, not by HBM, so rebuilding the third row costs them more than reading it: the FP64
+ * doublet M_asym at 32^3x64 takes 7.3 ms with 18-real links against 8.2 ms with 12 (sec. 3's
+ * trade of flops for bytes runs the other way at this precision).  Results differ from the
+ * compressed form by rounding only. */
+#define TM_GAUGE_F64_FULL_LINKS 16
 tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_mask, void *stream, tm_gauge **out);
 
 /* Release a handle (NULL is accepted).  Waits for the device to finish using it. */

@@ -11,7 +11,7 @@ import ctypes
 from . import _lib as L
 from ._lib import (TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT, TM_SOLVER_CG, TM_SOLVER_MIXED, TM_C64, TM_C128, TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM, TM_EPI_XMAY_K2,
                    TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, TM_NDEG_DOUBLET, TM_PC_ASYM, TM_PC_SYM, TM_PREC_F16, TM_PREC_F32,
-                   TM_PREC_F64, TM_PREC_DF64, TM_TWIST_MINUS, TM_TWIST_PLUS, TMError)
+                   TM_PREC_F64, TM_PREC_DF64, TM_TWIST_MINUS, TM_TWIST_PLUS, TM_GAUGE_F64_FULL_LINKS, TMError)
 
 PRECS = {"f64": TM_PREC_F64, "f32": TM_PREC_F32, "f16": TM_PREC_F16, "df64": TM_PREC_DF64}
 
@@ -71,8 +71,10 @@ class Params:
 class Gauge:
     """tm_gauge handle: packed links in FP64/FP32/FP16 (the handle's recon) on the current device."""
 
-    def __init__(self, params: Params, U, stream=None, precs=None):
-        """precs: the storage precisions whose links to pack (None: all; tm_gauge_create_ex)."""
+    def __init__(self, params: Params, U, stream=None, precs=None, f64_full_links=False):
+        """precs: the storage precisions whose links to pack (None: all; tm_gauge_create_ex).
+        f64_full_links: FP64 links with all 18 reals whatever params.recon (TM_GAUGE_F64_FULL_LINKS;
+        faster FP64 operators, e.g. the true residuals of the mixed solver)."""
         torch = _torch()
         self.params = params
         self.csw = 0.0
@@ -85,6 +87,8 @@ class Gauge:
         self._pc = params.c()
         bit = {TM_PREC_F64: 1, TM_PREC_F32: 2, TM_PREC_F16: 4, TM_PREC_DF64: 8}
         mask = 0 if precs is None else sum(bit[int(q)] for q in set(precs))
+        if f64_full_links:
+            mask |= TM_GAUGE_F64_FULL_LINKS
         L.check(L.load().tm_gauge_create_ex(ctypes.byref(self._pc), ctypes.c_void_p(U.data_ptr()), int(mask),
                                             _stream(stream), ctypes.byref(h)))
         self.h = h

@@ -18,6 +18,7 @@ TM_EPI_NONE, TM_EPI_TWINV, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XPAY, T
 TM_SOLVER_CG, TM_SOLVER_MIXED = 0, 1
 TM_SOLUTION_MAT, TM_SOLUTION_MATDAG_MAT = 0, 1
 TM_DD_ALL, TM_DD_INTERIOR, TM_DD_BOUNDARY = 0, 1, 2
+TM_GAUGE_F64_FULL_LINKS = 16
 
 
 class tm_params(ctypes.Structure):

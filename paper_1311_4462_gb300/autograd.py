@@ -14,7 +14,9 @@ on field values is a library call; this module only packs, unpacks and sequences
 
 Gauge handles are reused while U is unchanged: a handle is kept per parameter set together with a
 weak reference to its U and U's version counter, so repeated calls with the same (unmodified) U pack
-the links once, and only in the storage precisions the call computes in (tm_gauge_create_ex).  A handle dropped from the cache stays alive while an autograd graph still holds it.
+the links once, and only in the storage precisions the call computes in (tm_gauge_create_ex).  The
+FP64 links keep all 18 reals (TM_GAUGE_F64_FULL_LINKS): the FP64 operator, solves and force run on
+the FP64 pipe, where rebuilding the third row costs more than reading it.  A handle dropped from the cache stays alive while an autograd graph still holds it.
 """
 from __future__ import annotations
 
@@ -29,19 +31,19 @@ _CACHE: dict = {}   # params key -> (weakref to U, U._version, Gauge)
 _CACHE_MAX = 2
 
 
-def _key(params: Params, U, precs):
+def _key(params: Params, U, precs, f64_full):
     return (params.L, params.kappa, params.mu, params.eps, params.flavor, params.t_antiperiodic, params.recon,
-            U.device.index, tuple(sorted(precs)))
+            U.device.index, tuple(sorted(precs)), bool(f64_full))
 
 
-def gauge_for(U, params: Params, precs=(TM_PREC_F64, TM_PREC_F32)) -> Gauge:
-    """The cached handle of (U, params) holding the links of `precs` only, created when U is new or
-    was modified in place."""
-    k = _key(params, U, precs)
+def gauge_for(U, params: Params, precs=(TM_PREC_F64, TM_PREC_F32), f64_full=True) -> Gauge:
+    """The cached handle of (U, params) holding the links of `precs` only (FP64 ones with all 18
+    reals when f64_full), created when U is new or was modified in place."""
+    k = _key(params, U, precs, f64_full)
     hit = _CACHE.get(k)
     if hit is not None and hit[0]() is U and hit[1] == U._version:
         return hit[2]
-    g = Gauge(params, U.detach(), precs=precs)
+    g = Gauge(params, U.detach(), precs=precs, f64_full_links=f64_full)
     _CACHE.pop(k, None)
     while len(_CACHE) >= _CACHE_MAX:
         _CACHE.pop(next(iter(_CACHE)))

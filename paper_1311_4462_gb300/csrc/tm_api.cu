@@ -334,7 +334,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.coef = coef;
             a.tw_epi = X;
             a.tw_pro = X;
-            e = launch_dslash_clov_p64(a, g->nf, g->p.recon, g->clov_minb[0], s);
+            e = launch_dslash_clov_p64(a, g->nf, link_recon(g, 0), g->clov_minb[0], s);
         } else {
             DslashArgs<float> a;
             fill_common(a, g, out, in, x, out_parity, pidx);
@@ -343,8 +343,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.coef = (float)coef;
             a.tw_epi = to_float(X);
             a.tw_pro = a.tw_epi;
-            e = pidx == 1 ? launch_dslash_clov_p32(a, g->nf, g->p.recon, g->clov_minb[1], s)
-                           : launch_dslash_clov_p16(a, g->nf, g->p.recon, g->clov_minb[2], s);
+            e = pidx == 1 ? launch_dslash_clov_p32(a, g->nf, link_recon(g, pidx), g->clov_minb[1], s)
+                           : launch_dslash_clov_p16(a, g->nf, link_recon(g, pidx), g->clov_minb[2], s);
         }
         return cuda_check(e, "clover dslash launch");
     }
@@ -374,7 +374,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.tw_epi = de;
             a.tw_pro = dp;
             a.tw_acc = da;
-            e = launch_dslash_multi_p64(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s);
+            e = launch_dslash_multi_p64(a, 2, link_recon(g, 0), pro, nullptr, nact / 2, nact / 2, form, s);
         } else {
             DslashArgs<float> a;
             fill_common(a, g, out, in, x, out_parity, pidx);
@@ -384,8 +384,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
             a.tw_epi = to_float(de);
             a.tw_pro = to_float(dp);
             a.tw_acc = to_float(da);
-            e = pidx == 1 ? launch_dslash_multi_p32(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s)
-                          : launch_dslash_multi_p16(a, 2, g->p.recon, pro, nullptr, nact / 2, nact / 2, form, s);
+            e = pidx == 1 ? launch_dslash_multi_p32(a, 2, link_recon(g, pidx), pro, nullptr, nact / 2, nact / 2, form, s)
+                          : launch_dslash_multi_p16(a, 2, link_recon(g, pidx), pro, nullptr, nact / 2, nact / 2, form, s);
         }
         return cuda_check(e, "dslash launch (paired sources)");
     }
@@ -399,8 +399,8 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.tw_epi = te;
         a.tw_pro = tp;
         a.tw_acc = ta;
-        e = multi ? launch_dslash_multi_p64(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[0], s)
-                  : launch_dslash_p64(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
+        e = multi ? launch_dslash_multi_p64(a, g->nf, link_recon(g, 0), pro, act, nact, out->nrhs, g->multi_rpb[0], s)
+                  : launch_dslash_p64(a, g->nf, link_recon(g, 0), pro, tu.variant, tu.block, s);
     } else if (pidx == 3) {
         DslashArgs<df64> a;
         fill_common(a, g, out, in, x, out_parity, pidx);
@@ -410,7 +410,7 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.tw_epi = to_df64(te);
         a.tw_pro = to_df64(tp);
         a.tw_acc = to_df64(ta);
-        const int r = g->p.recon == 18 ? 18 : 12;
+        const int r = link_recon(g, 3);
         if (pro) {
             set_error("DF64 has no input-twist prologue kernel (the operators apply that twist separately)");
             return TM_ERR_ARG;
@@ -428,11 +428,11 @@ tm_status dslash_launch(const tm_gauge *g, const tm_field *out, const tm_field *
         a.tw_pro = to_float(tp);
         a.tw_acc = to_float(ta);
         if (multi)
-            e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[1], s)
-                            : launch_dslash_multi_p16(a, g->nf, g->p.recon, pro, act, nact, out->nrhs, g->multi_rpb[2], s);
+            e = (pidx == 1) ? launch_dslash_multi_p32(a, g->nf, link_recon(g, pidx), pro, act, nact, out->nrhs, g->multi_rpb[1], s)
+                            : launch_dslash_multi_p16(a, g->nf, link_recon(g, pidx), pro, act, nact, out->nrhs, g->multi_rpb[2], s);
         else
-            e = (pidx == 1) ? launch_dslash_p32(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s)
-                            : launch_dslash_p16(a, g->nf, g->p.recon, pro, tu.variant, tu.block, s);
+            e = (pidx == 1) ? launch_dslash_p32(a, g->nf, link_recon(g, pidx), pro, tu.variant, tu.block, s)
+                            : launch_dslash_p16(a, g->nf, link_recon(g, pidx), pro, tu.variant, tu.block, s);
     }
     return cuda_check(e, "dslash launch");
 }
@@ -579,12 +579,12 @@ static tm_status fused_launch(const tm_gauge *g, const tm_field *out_e, const tm
     if (out_e->prec == TM_PREC_F64) {
         const DslashArgs<double> aA = pass_args<double>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, Ri, 0);
         const DslashArgs<double> aB = pass_args<double>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, twB, 0);
-        e = launch_fused_p64(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
+        e = launch_fused_p64(aA, aB, g->nf, link_recon(g, 0), g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
                              g->num_sms, s);
     } else {
         const DslashArgs<float> aA = pass_args<float>(g, tmp_o, in_e, nullptr, 1, dagger, EPI_TW, 1.0, to_float(Ri), 1);
         const DslashArgs<float> aB = pass_args<float>(g, out_e, tmp_o, in_e, 0, dagger, epiB, -k2, to_float(twB), 1);
-        e = launch_fused_p32(aA, aB, g->nf, g->p.recon, g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
+        e = launch_fused_p32(aA, aB, g->nf, link_recon(g, 1), g->fused_items, g->fused_nitems, g->fused_sync, g->wait_limit_ns,
                              g->num_sms, s);
     }
     return cuda_check(e, "fused operator launch");
@@ -678,6 +678,63 @@ bool normal_red_supported(const tm_gauge *g, int prec, int dagger)
     return v >= 6 && v <= 9 && 4 * blocks * sizeof(double) <= g->scratch_bytes - SCRATCH_PARTIALS_OFF;
 }
 
+// One staged launch with the fused reduction (red) and its fixed-order finish.
+static tm_status red_launch(const tm_gauge *g, const tm_field *out, const tm_field *in, const tm_field *x, int dagger,
+                            int epi, double coef, const Twist<double> &tw, const Twist<double> *q, const double *scal,
+                            const RedArgs *red, cudaStream_t s)
+{
+    const int pidx = prec_index(in->prec);
+    const int variant = g->tune[pidx][0].variant;
+    cudaError_t e;
+    if (pidx == 0) {
+        DslashArgs<double> a = pass_args<double>(g, out, in, x, 0, dagger, epi, coef, tw, 0);
+        if (q) a.tw_acc = *q;
+        a.scal_in = scal;
+        e = launch_dslash_red_p64(a, g->nf, link_recon(g, 0), variant, *red, s);
+    } else {
+        DslashArgs<float> a = pass_args<float>(g, out, in, x, 0, dagger, epi, coef, to_float(tw), pidx);
+        if (q) a.tw_acc = to_float(*q);
+        a.scal_in = scal;
+        e = pidx == 1 ? launch_dslash_red_p32(a, g->nf, link_recon(g, pidx), variant, *red, s)
+                      : launch_dslash_red_p16(a, g->nf, link_recon(g, pidx), variant, *red, s);
+    }
+    TM_TRY(cuda_check(e, "fused-reduction launch"));
+    return cuda_check(launch_finish_partials(red->partials, 4L * ((g->Vh + 127) / 128), *red, s), "reduction finish");
+}
+
+// The first half of the normal operator with |A in|^2 = <in, A^dag A in> (CG's <p, A^dag A p>) from
+// the epilogue of its second launch: te = M_asym in and |te|^2 for the asymmetric operator; for the
+// symmetric one te = Q u with u = M_asym in and Q = (R R^dag)^-1, and the reduction Re<u, Q u>,
+// since M_sym = R^-1 M_asym.
+static tm_status normal_first_half_red(const tm_gauge *g, const tm_field *te_e, const tm_field *in_e,
+                                       const tm_field *tmp_o, int pc, cudaStream_t s, const RedArgs *red)
+{
+    if (!normal_red_supported(g, in_e->prec, 0) || in_e->nrhs != 1) {
+        set_error("internal: fused reduction not available for this operator");
+        return TM_ERR_ARG;
+    }
+    const double k2 = g->p.kappa * g->p.kappa;
+    const Twist<double> R = make_twist(g, TW_R, 0), Ri = make_twist(g, TW_RINV, 0), Q = rrdag_inverse(g);
+    const bool sym = pc == TM_PC_SYM;
+    TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s, nullptr, 1));
+    return red_launch(g, te_e, tmp_o, in_e, 0, sym ? EPI_TWX_AXPY_TW : EPI_TWX_AXPY, -k2, R, &Q, nullptr, red, s);
+}
+
+// CG's residual update without storing A^dag A p: launches 1 - 2 as normal_core with the fused
+// |A p|^2 (red_a, whose finish leaves alpha = |r|^2 / |A p|^2 at *alpha_dev), launch 3 the first
+// factor of M_asym^dag, launch 4 its second factor with r <- r - alpha (R^dag te - kappa^2
+// H^dag_eo tmp) in place and |r|^2 summed in the same epilogue (red_r).
+tm_status normal_rupd_core(const tm_gauge *g, const tm_field *r_e, const tm_field *p_e, const tm_field *te_e,
+                           const tm_field *tmp_o, int pc, cudaStream_t s, const RedArgs *red_a, const RedArgs *red_r,
+                           const double *alpha_dev)
+{
+    TM_TRY(normal_first_half_red(g, te_e, p_e, tmp_o, pc, s, red_a));
+    const double k2 = g->p.kappa * g->p.kappa;
+    const Twist<double> Rd = make_twist(g, TW_R, 1), Rid = make_twist(g, TW_RINV, 1);
+    TM_TRY(dslash_launch(g, tmp_o, te_e, nullptr, 1, 1, EPI_TW, 1.0, &Rid, nullptr, s, nullptr, 1));
+    return red_launch(g, r_e, tmp_o, te_e, 1, EPI_TWX_AXPY_RUPD, -k2, Rd, nullptr, alpha_dev, red_r, s);
+}
+
 // out = A^dag A in with A = M_pc, or A = M_pc^dag when dagger (tm_normal_op).  For the symmetric
 // operator (no dagger, no clover term) M_sym = R_ee^-1 M_asym gives
 //   M_sym^dag M_sym = M_asym^dag (R_ee R_ee^dag)^-1 M_asym,
@@ -688,33 +745,11 @@ tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *
                       const RedArgs *red)
 {
     if (red) {
-        // |A in|^2 = <in, A^dag A in> from the epilogue of the second launch of A (the CG's <p, Ap>):
-        // for the symmetric operator Re<u, Q u> with u = M_asym in, since M_sym = R^-1 M_asym
-        if (!normal_red_supported(g, in_e->prec, dagger) || act || nact > 1 || in_e->nrhs != 1) {
+        if (dagger || act || nact > 1) {
             set_error("internal: fused reduction not available for this operator");
             return TM_ERR_ARG;
         }
-        const int pidx = prec_index(in_e->prec);
-        const double k2 = g->p.kappa * g->p.kappa;
-        const Twist<double> R = make_twist(g, TW_R, 0), Ri = make_twist(g, TW_RINV, 0), Q = rrdag_inverse(g);
-        const bool sym = pc == TM_PC_SYM;
-        TM_TRY(dslash_launch(g, tmp_o, in_e, nullptr, 1, 0, EPI_TW, 1.0, &Ri, nullptr, s, nullptr, 1));
-        cudaError_t e;
-        const int variant = g->tune[pidx][0].variant;
-        if (pidx == 0) {
-            DslashArgs<double> a = pass_args<double>(g, te_e, tmp_o, in_e, 0, 0, sym ? EPI_TWX_AXPY_TW : EPI_TWX_AXPY,
-                                                     -k2, R, 0);
-            a.tw_acc = Q;
-            e = launch_dslash_red_p64(a, g->nf, g->p.recon, variant, *red, s);
-        } else {
-            DslashArgs<float> a = pass_args<float>(g, te_e, tmp_o, in_e, 0, 0, sym ? EPI_TWX_AXPY_TW : EPI_TWX_AXPY,
-                                                   -k2, to_float(R), pidx);
-            a.tw_acc = to_float(Q);
-            e = pidx == 1 ? launch_dslash_red_p32(a, g->nf, g->p.recon, variant, *red, s)
-                          : launch_dslash_red_p16(a, g->nf, g->p.recon, variant, *red, s);
-        }
-        TM_TRY(cuda_check(e, "fused-reduction launch"));
-        TM_TRY(cuda_check(launch_finish_partials(red->partials, 4L * ((g->Vh + 127) / 128), *red, s), "reduction finish"));
+        TM_TRY(normal_first_half_red(g, te_e, in_e, tmp_o, pc, s, red));
         return precond_core(g, out_e, te_e, tmp_o, TM_PC_ASYM, 1, s, nullptr, 1);
     }
     if (pc == TM_PC_SYM && !dagger && g->csw == 0.0) {
@@ -763,9 +798,9 @@ template <typename T>
 static cudaError_t dd_launch_t(const tm_gauge *g, DslashArgs<T> &a, const DDArgs<T> *dd, void *fp, void *fn, bool pro,
                                int pidx, cudaStream_t s)
 {
-    if constexpr (std::is_same<T, double>::value) return launch_dd_p64(a, dd, fp, fn, g->nf, g->p.recon, pro, s);
-    else return pidx == 1 ? launch_dd_p32(a, dd, fp, fn, g->nf, g->p.recon, pro, s)
-                          : launch_dd_p16(a, dd, fp, fn, g->nf, g->p.recon, pro, s);
+    if constexpr (std::is_same<T, double>::value) return launch_dd_p64(a, dd, fp, fn, g->nf, link_recon(g, 0), pro, s);
+    else return pidx == 1 ? launch_dd_p32(a, dd, fp, fn, g->nf, link_recon(g, pidx), pro, s)
+                          : launch_dd_p16(a, dd, fp, fn, g->nf, link_recon(g, pidx), pro, s);
 }
 
 template <typename T>
@@ -824,7 +859,9 @@ tm_status tm_gauge_create(const tm_params *p, const void *U_canon, void *stream,
 tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_mask, void *stream, tm_gauge **out)
 {
     TM_NVTX("tm_gauge_create");
-    if (prec_mask < 0 || prec_mask > 15) { set_error("tm_gauge_create_ex: prec_mask must be in [0, 15]"); return TM_ERR_ARG; }
+    if (prec_mask < 0 || prec_mask > 31) { set_error("tm_gauge_create_ex: prec_mask must be in [0, 31]"); return TM_ERR_ARG; }
+    const bool f64_full = (prec_mask & TM_GAUGE_F64_FULL_LINKS) != 0;
+    prec_mask &= 15;
     if (prec_mask == 0) prec_mask = 15;
     TM_TRY(check_params(p));
     if (!U_canon || !out) { set_error("tm_gauge_create: null pointer"); return TM_ERR_ARG; }
@@ -836,6 +873,11 @@ tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_m
     const long V = (long)p->L[0] * p->L[1] * p->L[2] * p->L[3];
     g->Vh = (int)(V / 2);
     g->X1h = p->L[0] / 2;
+    // link format per storage form: the handle's recon, except 18 reals for FP64 on request and at
+    // least 12 for DF64 (no 8-real DF64 kernels)
+    g->recon[0] = f64_full ? 18 : p->recon;
+    g->recon[1] = g->recon[2] = p->recon;
+    g->recon[3] = p->recon == 8 ? 12 : p->recon;
     for (int i = 0; i < 4; i++) {
         // measured on GB300 at 32^3x64: the register cap (3) for FP64; for FP32 and FP16 the
         // shared-memory staged pipeline with the paired hop: the doublet's flavours paired (FP32
@@ -866,7 +908,7 @@ tm_status tm_gauge_create_ex(const tm_params *p, const void *U_canon, int prec_m
     const int precs[4] = {TM_PREC_F64, TM_PREC_F32, TM_PREC_F16, TM_PREC_DF64};
     for (int i = 0; i < 4 && st == TM_OK; i++) {
         if (!(prec_mask & (1 << i))) continue;  // this storage form is not packed: its operators are refused
-        const int recon_i = (precs[i] == TM_PREC_DF64 && p->recon == 8) ? 12 : p->recon;
+        const int recon_i = g->recon[i];
         const size_t per_link = (size_t)recon_i * real_bytes(precs[i]);
         const size_t chunks = per_link / link_chunk_bytes(precs[i], recon_i);
         g->link_bytes[i] = 8ull * g->Vh * chunks * link_chunk_bytes(precs[i], recon_i);

@@ -245,17 +245,31 @@ static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
 // The end of a reduction whose partial sums another kernel wrote (the hopping kernel's fused
 // reduction, one partial per warp): one block, thread t adds partials t, t + 256, ... in order,
 // then the block tree, then the scalar update -- a fixed order, so the result is reproducible.
-__global__ void __launch_bounds__(256) k_finish_partials(const double *__restrict__ partials, long n, RedArgs r)
+// Thread t adds partials t, t + 1024, t + 2048, ... into four independent running sums (index
+// (b / 1024) mod 4), which it combines as (s0 + s1) + (s2 + s3); the block then sums the threads in
+// block_sum's fixed order.  The order depends only on n, so the result is reproducible, and the
+// four chains keep four loads in flight per thread.
+__global__ void __launch_bounds__(1024) k_finish_partials(const double *__restrict__ partials, long n, RedArgs r)
 {
-    double s = 0.0;
-    for (long b = threadIdx.x; b < n; b += blockDim.x) s += partials[b];
-    s = block_sum(s);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const long t = threadIdx.x;
+    long b = t;
+    for (; b + 3 * 1024 < n; b += 4 * 1024) {
+        s0 += partials[b];
+        s1 += partials[b + 1024];
+        s2 += partials[b + 2 * 1024];
+        s3 += partials[b + 3 * 1024];
+    }
+    if (b < n) s0 += partials[b];
+    if (b + 1024 < n) s1 += partials[b + 1024];
+    if (b + 2 * 1024 < n) s2 += partials[b + 2 * 1024];
+    double s = block_sum((s0 + s1) + (s2 + s3));
     if (threadIdx.x == 0) apply_fin(s, r, 0);
 }
 
 cudaError_t launch_finish_partials(const double *partials, long n, const RedArgs &r, cudaStream_t s)
 {
-    k_finish_partials<<<1, 256, 0, s>>>(partials, n, r);
+    k_finish_partials<<<1, 1024, 0, s>>>(partials, n, r);
     return cudaGetLastError();
 }
 

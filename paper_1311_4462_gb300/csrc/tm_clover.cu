@@ -398,7 +398,7 @@ tm_status clover_build(tm_gauge *g, double csw, cudaStream_t s)
         a.err = err;
         const long n = 2L * g->Vh;
         const unsigned grid = (unsigned)((n + 127) / 128);
-        switch (g->p.recon) {
+        switch (link_recon(g, 0)) {  // the clover term is built from the FP64 links
         case 18: k_clover_build<18><<<grid, 128, 0, s>>>(a); break;
         case 12: k_clover_build<12><<<grid, 128, 0, s>>>(a); break;
         default: k_clover_build<8><<<grid, 128, 0, s>>>(a); break;

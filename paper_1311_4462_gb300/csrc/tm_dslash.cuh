@@ -17,6 +17,9 @@
 //   EPI_TW_XPAY    out = T (x + c acc)             odd reconstruction, symmetric RHS
 //   EPI_TWX_AXPY_TW out = Q (T x + c acc)          (R R^dag)^-1 M_asym: the first factor of the
 //                                                  symmetric normal operator (Q = tw_acc)
+//   EPI_TWX_AXPY_RUPD out = out - s (T x + c acc)  CG's r <- r - alpha A^dag A p in the launch that
+//                                                  produces A^dag A p (s = *scal_in; staged forms
+//                                                  with the fused reduction of |out|^2 only)
 // and, as a compile-time option, a prologue that twists every neighbour spinor before the
 // projection (in -> T_pro in), which the adjoint of the symmetric operator needs.
 // For the doublet both flavours are computed by the same thread, so each link is loaded once
@@ -50,6 +53,7 @@ struct DslashArgs {
     T coef;
     Twist<T> tw_epi, tw_pro;
     Twist<T> tw_acc;         // Q of EPI_TWX_AXPY_TW
+    const double *scal_in;   // device scalar s of EPI_TWX_AXPY_RUPD
     const void *clov;        // clover handles: per-site local operator of this precision (tm_clover.cuh)
     const float *clov_norm;  // FP16 block scales
 };
@@ -1281,6 +1285,16 @@ __device__ __forceinline__ double async_site(const DslashArgs<typename Traits<PR
                                                      a.x_norm ? a.x_norm + noff : nullptr, cb, a.Vh);
             cp_commit();
         }
+        if constexpr (RED) {
+            if (h == 7 && epi == EPI_TWX_AXPY_RUPD) {
+                // the residual this launch updates in place streams into the buffer hop 7 used
+                // while the twist of x is computed
+                async_fetch_x<PREC, RECON, NF>(smem_async + (7 % NB) * H::BUF, tid,
+                                               reinterpret_cast<const SC *>(a.out) + boff,
+                                               a.out_norm ? a.out_norm + noff : nullptr, cb, a.Vh);
+                cp_commit();
+            }
+        }
     }
     const char *xbuf = smem_async + ((8 - NB) % NB) * H::BUF;
 
@@ -1294,9 +1308,15 @@ __device__ __forceinline__ double async_site(const DslashArgs<typename Traits<PR
         local_op<PREC, NF, CLOV, true>(a, cb, acc);
     } else {
         T xv[NF][24];
-        cp_wait<0>();
+        if constexpr (RED) {
+            if (epi == EPI_TWX_AXPY_RUPD) cp_wait<1>();  // x; the residual may still be in flight
+            else cp_wait<0>();
+        } else {
+            cp_wait<0>();
+        }
         async_read_x<PREC, RECON, NF>(xbuf, tid, xv);
-        if (epi == EPI_TWX_AXPY || epi == EPI_TWX_AXPY_TW) local_op<PREC, NF, CLOV, false>(a, cb, xv);
+        if (epi == EPI_TWX_AXPY || epi == EPI_TWX_AXPY_TW || epi == EPI_TWX_AXPY_RUPD)
+            local_op<PREC, NF, CLOV, false>(a, cb, xv);
         else if (epi == EPI_X_TWAXPY) local_op<PREC, NF, CLOV, true>(a, cb, acc);
 #pragma unroll
         for (int f = 0; f < NF; f++)
@@ -1304,6 +1324,18 @@ __device__ __forceinline__ double async_site(const DslashArgs<typename Traits<PR
             for (int k = 0; k < 24; k++) acc[f][k] = fma(a.coef, acc[f][k], xv[f][k]);
         if (epi == EPI_TW_XPAY) {
             local_op<PREC, NF, CLOV, true>(a, cb, acc);
+        } else if (epi == EPI_TWX_AXPY_RUPD) {
+            if constexpr (RED) {
+                // r - s u with u = T x + c acc as the separate pass computes it from a stored u
+                // (binary32: the same bits); the |out|^2 share below is then |r|^2
+                cp_wait<0>();
+                async_read_x<PREC, RECON, NF>(smem_async + (7 % NB) * H::BUF, tid, xv);
+                const T ms = -T(__ldg(a.scal_in));
+#pragma unroll
+                for (int f = 0; f < NF; f++)
+#pragma unroll
+                    for (int k = 0; k < 24; k++) acc[f][k] = fma(ms, acc[f][k], xv[f][k]);
+            }
         } else if (epi == EPI_TWX_AXPY_TW) {
             if constexpr (RED) {  // Re<u, Q u> (Q hermitian): u is acc before the twist
 #pragma unroll

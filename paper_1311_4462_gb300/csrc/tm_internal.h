@@ -24,7 +24,9 @@ enum Epilogue {
     EPI_X_TWAXPY = 3,  // out = x + c T acc
     EPI_XPAY = 4,      // out = x + c acc
     EPI_TW_XPAY = 5,   // out = T (x + c acc)
-    EPI_TWX_AXPY_TW = 6  // out = Q (T x + c acc), Q a second constant local matrix
+    EPI_TWX_AXPY_TW = 6,  // out = Q (T x + c acc), Q a second constant local matrix
+    EPI_TWX_AXPY_RUPD = 7  // out = out - s (T x + c acc), s = *scal_in: CG's residual update in place
+                           // (staged launch forms with the fused reduction only)
 };
 
 // twist selector for host-built coefficient tables
@@ -42,6 +44,9 @@ tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *
                       const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact,
                       const RedArgs *red = nullptr);
 bool normal_red_supported(const tm_gauge *g, int prec, int dagger);
+tm_status normal_rupd_core(const tm_gauge *g, const tm_field *r_e, const tm_field *p_e, const tm_field *te_e,
+                           const tm_field *tmp_o, int pc, cudaStream_t s, const RedArgs *red_a, const RedArgs *red_r,
+                           const double *alpha_dev);
 }  // namespace tmk
 
 // Launch choice of the hopping kernel for one (precision, prologue) pair.
@@ -60,6 +65,7 @@ struct tm_gauge {
     int num_sms;
     void *links[4];     // packed links, index 0: FP64, 1: FP32, 2: FP16, 3: DF64
     size_t link_bytes[4];
+    int recon[4];       // reals per stored link of each storage form (p.recon unless overridden)
     double *scratch;    // reduction partials + device scalars (library-owned)
     double *host_scalars;  // pinned mirror for scalar readback
     tm_tune_entry tune[4][2];  // [precision index][prologue]
@@ -88,4 +94,5 @@ size_t chunk_bytes(int prec);      // always 16
 void set_error(const char *fmt, ...);
 tm_status cuda_check(cudaError_t e, const char *what);
 tm_status need_links(const tm_gauge *g, int prec);  // TM_ERR_ARG when the handle did not pack prec
+inline int link_recon(const tm_gauge *g, int pidx) { return g->recon[pidx]; }  // link format of a storage form
 }  // namespace tmk

@@ -394,10 +394,10 @@ cudaError_t launch_pack_gauge(const tm_gauge *g, int pidx, void *out, const void
     const int block = 128;
     const long grid = (n + block - 1) / block;
     const double2 *c = (const double2 *)canon;
-    if (pidx == 0) k_pack_gauge<P64><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
-    else if (pidx == 1) k_pack_gauge<P32><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
-    else if (pidx == 2) k_pack_gauge<P16><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
-    else k_pack_gauge<PDF><<<grid, block, 0, s>>>(out, c, g->p.recon, G);
+    if (pidx == 0) k_pack_gauge<P64><<<grid, block, 0, s>>>(out, c, link_recon(g, pidx), G);
+    else if (pidx == 1) k_pack_gauge<P32><<<grid, block, 0, s>>>(out, c, link_recon(g, pidx), G);
+    else if (pidx == 2) k_pack_gauge<P16><<<grid, block, 0, s>>>(out, c, link_recon(g, pidx), G);
+    else k_pack_gauge<PDF><<<grid, block, 0, s>>>(out, c, link_recon(g, pidx), G);
     return cudaGetLastError();
 }
 

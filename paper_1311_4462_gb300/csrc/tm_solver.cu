@@ -144,13 +144,28 @@ class Solver {
             if (st != TM_OK) return st;
             return site(OP_DOT, fref(p), fref(out), fnone(), fnone(), sv(0), sv(0), 1, FIN_ALPHA, 0);
         }
+        RedArgs r = red_args(FIN_ALPHA, 0);
+        return normal_core(g, out, p, te, to, sp->pc, sp->dagger, s, nullptr, 1, &r);
+    }
+    // r -= alpha A^dag A p with alpha = |r|^2 / |A p|^2 and |r|^2 in SL_RRNEW, A^dag A p never stored:
+    // the update and its norm are computed in the epilogue of the launch that produces A^dag A p
+    // (normal_rupd_core).  Available where normal_op_alpha fuses its reduction, for A = M_pc.
+    bool rupd_supported(int prec) const { return !sp->dagger && normal_red_supported(g, prec, 0); }
+    tm_status normal_rupd(const tm_field *r, const tm_field *p, const tm_field *te, const tm_field *to)
+    {
+        RedArgs ra = red_args(FIN_ALPHA, 0), rr = red_args(FIN_STORE, SL_RRNEW);
+        return normal_rupd_core(g, r, p, te, to, sp->pc, s, &ra, &rr, S + SL_ALPHA * TM_MAX_RHS);
+    }
+    RedArgs red_args(int fin, int slot) const
+    {
         RedArgs r;
         memset(&r, 0, sizeof(r));
         r.partials = reinterpret_cast<double *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_PARTIALS_OFF);
         r.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(g->scratch) + SCRATCH_COUNTER_OFF);
         r.scalars = S;
-        r.fin = FIN_ALPHA;
-        return normal_core(g, out, p, te, to, sp->pc, sp->dagger, s, nullptr, 1, &r);
+        r.fin = fin;
+        r.slot = slot;
+        return r;
     }
 };
 
@@ -289,12 +304,19 @@ static tm_status solve(const tm_gauge *g, const tm_field *x, const tm_field *b, 
         TRY(V.norm2(&rs, SL_RR));
         double maxr = sqrt(r2);
         bool converged = r2 <= tol2 * bb;
+        const bool rupd = V.rupd_supported(sp->sloppy_prec);
         while (!converged && it < sp->maxiter) {
-            TRY(V.normal_op_alpha(&Aps, &ps, &tes, &tos));
-            // r_s -= alpha A p with |r_s|^2; the increment x_s += alpha p waits for beta and shares
-            // the pass of the search-direction update (one field pass fewer per iteration)
-            TRY(V.site(OP_R_UPDATE, fref(&rs), fref(&rs), fnone(), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
-                       FIN_STORE, SL_RRNEW));
+            // r_s -= alpha A p with |r_s|^2, in the epilogue of the last hopping launch where the
+            // launch form allows it (A p is then never stored), else as a pass of its own; the
+            // increment x_s += alpha p waits for beta and shares the pass of the search-direction
+            // update (one field pass fewer per iteration)
+            if (rupd) {
+                TRY(V.normal_rupd(&rs, &ps, &tes, &tos));
+            } else {
+                TRY(V.normal_op_alpha(&Aps, &ps, &tes, &tos));
+                TRY(V.site(OP_R_UPDATE, fref(&rs), fref(&rs), fnone(), fref(&Aps), sslot(SL_ALPHA, 1.0), sv(0), 1,
+                           FIN_STORE, SL_RRNEW));
+            }
             TRY(V.read(SL_RRNEW, &rr));
             it++;
             if (!isfinite(rr)) { set_error("tm_solve: non-finite residual at iteration %d", it); st = TM_ERR_NAN; goto done; }

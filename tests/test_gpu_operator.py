@@ -121,6 +121,37 @@ def test_normal_op(case, prec, pc, dagger, variant):
     assert rel(get(tmq, g, out, 0), ref) < (2 * TOL[prec] if prec == 2 else TOL[prec])
 
 
+@pytest.mark.parametrize("case", CASES[:5], ids=[c[0] for c in CASES[:5]])
+@pytest.mark.parametrize("recon", [12, 8])
+@pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
+@pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])
+def test_f64_full_links(case, recon, pc, dagger):
+    """TM_GAUGE_F64_FULL_LINKS: the FP64 links keep all 18 reals, so the FP64 operator gives the
+    bits of an 18-real handle (and meets the oracle at the FP64 bound), while FP32 and FP16 follow
+    the handle's recon and give the bits of a handle without the flag."""
+    import paper_1311_4462_gb300 as tmq
+    _, p, po, U, g, psi, chi = setup(case, recon)
+    g18 = setup(case, 18)[4]
+    gf = tmq.Gauge(p, torch.from_numpy(U), f64_full_links=True)
+    try:
+        for h in (g, g18, gf):
+            use_variant(tmq, h, 3)
+        outs = {}
+        for name, h in (("flag", gf), ("plain", g), ("r18", g18)):
+            for prec in (8, 4, 2):
+                xe, _ = fields(tmq, h, prec, psi)
+                out, tmp = tmq.Field(h, prec), tmq.Field(h, prec)
+                tmq.precond_op(h, out, xe, tmp, pc, dagger)
+                outs[name, prec] = get(tmq, h, out, 0)
+        assert np.array_equal(outs["flag", 8], outs["r18", 8])
+        ref = orc.apply_M_pc(po, U, mask(po, psi, 0), sym=bool(pc), dagger=dagger)
+        assert rel(outs["flag", 8], ref) < TOL[8]
+        for prec in (4, 2):
+            assert np.array_equal(outs["flag", prec], outs["plain", prec])
+    finally:
+        gf.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dagger", [False, True], ids=["", "dag"])

@@ -194,17 +194,40 @@ def test_df64_cg_to_1e12():
 @pytest.mark.parametrize("pc", [0, 1], ids=["asym", "sym"])
 @pytest.mark.parametrize("sloppy", [4, 2], ids=["f32", "f16"])
 def test_fused_pap_matches_the_separate_reduction(case, pc, sloppy):
-    """<p, A^dag A p> summed in the hopping epilogue (staged launch forms) or by a separate pass
-    (register-capped form): both mixed solves converge to the same solution."""
+    """<p, A^dag A p> and the residual update r -= alpha A^dag A p with |r|^2 computed in the
+    hopping epilogues (staged launch forms; A^dag A p never stored) or by separate passes
+    (register-capped form): both mixed solves converge to the same solution in about the same
+    number of iterations."""
     tmq, p, po, U, g, b = setup(case)
     name = {4: "f32", 2: "f16"}[sloppy]
     saved = tmq.tune_export(g)
-    sols = []
+    sols, its = [], []
     for table in (f"{name}:0:{8 if p.nf == 2 else 9}:128", f"{name}:0:3:128"):
         tmq.tune_import(g, table)
         psi, st = full_solve(tmq, g, b, pc, False, solver="mixed", sloppy_prec=sloppy, tol=1e-10, maxiter=5000)
         assert st["true_residual"] <= 1e-10
         assert rel(orc.apply_M(po, U, psi), b) < 1e-7
         sols.append(psi)
+        its.append(st["iterations"])
     tmq.tune_import(g, saved)
     assert rel(sols[0], sols[1]) < 1e-7
+    assert abs(its[0] - its[1]) <= max(2, its[1] // 20), its
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("solver", ["cg", "mixed"])
+def test_f64_full_links_solve(case, solver):
+    """A handle whose FP64 links keep 18 reals (TM_GAUGE_F64_FULL_LINKS, used for the FP64 true
+    residuals) solves to the same tolerance and the same solution as the recon-12 handle."""
+    tmq, p, po, U, g, b = setup(case)
+    gf = tmq.Gauge(p, torch.from_numpy(U), f64_full_links=True)
+    try:
+        tmq.tune_import(gf, tmq.tune_export(g))
+        psi_f, st_f = full_solve(tmq, gf, b, 0, False, solver=solver, tol=1e-10, maxiter=5000)
+        psi, st = full_solve(tmq, g, b, 0, False, solver=solver, tol=1e-10, maxiter=5000)
+        assert st_f["status"] == 0 and st_f["true_residual"] <= 1e-10
+        assert rel(orc.apply_M(po, U, psi_f), b) < 1e-7
+        assert rel(psi_f, psi) < 1e-7
+        assert abs(st_f["iterations"] - st["iterations"]) <= 2
+    finally:
+        gf.close()
