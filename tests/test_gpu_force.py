@@ -177,3 +177,40 @@ def test_handle_with_a_subset_of_link_precisions():
         tmq.set_clover(g, 1.0)  # the clover field is built from the FP64 links
     tmq.autotune(g)  # tunes the packed precision only
     g.close()
+
+
+@pytest.mark.parametrize("recon", [12, 8])
+def test_force_and_clover_with_full_fp64_links(recon):
+    """TM_GAUGE_F64_FULL_LINKS: the FP64 force reads the 18-real FP64 links (the bits of an 18-real
+    handle), the FP32 force the handle's recon, and the clover term builds from the FP64 links."""
+    import paper_1311_4462_gb300 as tmq
+    name, L, flavor, kappa, mu, eps = CASES[1]
+    U = inputs.gauge_field(L, 1306)
+    psi, gv = inputs.spinor_field(L, 2, 2411), inputs.spinor_field(L, 2, 2412)
+    tp, tg = torch.from_numpy(psi), torch.from_numpy(gv)
+    hs = {"flag": tmq.Gauge(tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=recon), torch.from_numpy(U),
+                            f64_full_links=True),
+          "plain": tmq.Gauge(tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=recon), torch.from_numpy(U)),
+          "r18": tmq.Gauge(tmq.Params(L, kappa, mu, eps, flavor=flavor, recon=18), torch.from_numpy(U))}
+    F = {}
+    for k, g in hs.items():
+        for prec in (8, 4):
+            F[k, prec] = tmq.force(g, tmq.pack(g, tp, 0, prec), tmq.pack(g, tp, 1, prec), tmq.pack(g, tg, 0, prec),
+                                   tmq.pack(g, tg, 1, prec), coef=0.7, project=True).cpu().numpy()
+    assert np.array_equal(F["flag", 8], F["r18", 8])
+    assert np.array_equal(F["flag", 4], F["plain", 4])
+    po = orc.Params(L, kappa, mu, eps, flavor=flavor)
+    assert rel(F["flag", 8], orc.force(po, U, psi, gv, coef=0.7, project=True)) < 1e-13
+    g = hs["flag"]
+    tmq.set_clover(g, 1.6)
+    x = tmq.pack(g, tp, 0, 8)
+    out, tmp = tmq.Field(g, 8), tmq.Field(g, 8)
+    tmq.precond_op(g, out, x, tmp, 0, False)
+    ref = hs["r18"]
+    tmq.set_clover(ref, 1.6)
+    x18 = tmq.pack(ref, tp, 0, 8)
+    out18, tmp18 = tmq.Field(ref, 8), tmq.Field(ref, 8)
+    tmq.precond_op(ref, out18, x18, tmp18, 0, False)
+    assert torch.equal(out.data, out18.data)
+    for h in hs.values():
+        h.close()
