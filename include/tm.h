@@ -286,7 +286,10 @@ typedef struct {
     int pc;          /* tm_pc */
     int dagger;      /* 1: A = M_pc^dag */
     double tol;      /* stop when |bhat - A^dag A x| / |bhat| <= tol (FP64 true residual);
-                        bhat = A^dag b (MAT) or b (MATDAG_MAT) */
+                        bhat = A^dag b (MAT) or b (MATDAG_MAT).  The mixed solver of a MAT
+                        solution computes the residual as A^dag (b - A x) and, with FP32 sloppy
+                        fields, |bhat| from A^dag b in binary32 (about 1e-7 relative): bhat then
+                        never exists in FP64, saving two FP64 operator applications */
     int maxiter;     /* CG iterations (sloppy iterations for the mixed solver) */
     double delta;    /* mixed: reliable update when |r_sloppy| < delta * max |r| since the last one */
     int sloppy_prec; /* mixed: TM_PREC_F32 or TM_PREC_F16 storage for the inner iteration */
@@ -301,7 +304,8 @@ typedef struct {
 typedef struct {
     int iterations;
     int reliable_updates; /* mixed: reliable updates; FP64 CG: restarts from the true residual */
-    double true_residual; /* |bhat - A^dag A x| / |bhat|, recomputed in FP64 at exit */
+    double true_residual; /* |bhat - A^dag A x| / |bhat|, recomputed in FP64 at exit (|bhat| as
+                             the stopping test takes it, see tol) */
     double pc_residual;   /* |A x - b| / |b| for MAT solutions when want_pc_residual, else -1 */
     double seconds;       /* host wall time of the call */
 } tm_solver_stats;

@@ -735,6 +735,20 @@ tm_status normal_rupd_core(const tm_gauge *g, const tm_field *r_e, const tm_fiel
     return red_launch(g, r_e, tmp_o, te_e, 1, EPI_TWX_AXPY_RUPD, -k2, Rd, nullptr, alpha_dev, red_r, s);
 }
 
+// out = A^dag in with A = M_pc (A = M_pc^dag when dagger); in is overwritten.  For A = M_sym,
+// A^dag = M_sym^dag = M_asym^dag R_ee^-dag (M_sym = R_ee^-1 M_asym): R_ee^-dag as a site pass on in,
+// then M_asym^dag, which needs no input-twist prologue.
+tm_status adjoint_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                       int dagger, cudaStream_t s)
+{
+    if (pc == TM_PC_SYM && !dagger && g->csw == 0.0) {
+        const Twist<double> Rid = make_twist(g, TW_RINV, 1);
+        TM_TRY(cuda_check(launch_twist_active(g, in_e, in_e, Rid, nullptr, 1, s), "twist"));
+        return precond_core(g, out_e, in_e, tmp_o, TM_PC_ASYM, 1, s, nullptr, 1);
+    }
+    return precond_core(g, out_e, in_e, tmp_o, pc, !dagger, s, nullptr, 1);
+}
+
 // out = A^dag A in with A = M_pc, or A = M_pc^dag when dagger (tm_normal_op).  For the symmetric
 // operator (no dagger, no clover term) M_sym = R_ee^-1 M_asym gives
 //   M_sym^dag M_sym = M_asym^dag (R_ee R_ee^dag)^-1 M_asym,

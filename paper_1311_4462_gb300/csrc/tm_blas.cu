@@ -243,9 +243,7 @@ static int pc_of(const FieldRef &f, int dflt) { return f.data ? f.prec : dflt; }
     X(PDF, PDF, P16, PDF)
 
 // The end of a reduction whose partial sums another kernel wrote (the hopping kernel's fused
-// reduction, one partial per warp): one block, thread t adds partials t, t + 256, ... in order,
-// then the block tree, then the scalar update -- a fixed order, so the result is reproducible.
-// Thread t adds partials t, t + 1024, t + 2048, ... into four independent running sums (index
+// reduction, one partial per warp), then the scalar update, in one block.  Thread t adds partials t, t + 1024, t + 2048, ... into four independent running sums (index
 // (b / 1024) mod 4), which it combines as (s0 + s1) + (s2 + s3); the block then sums the threads in
 // block_sum's fixed order.  The order depends only on n, so the result is reproducible, and the
 // four chains keep four loads in flight per thread.

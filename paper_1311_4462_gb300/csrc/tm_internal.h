@@ -44,6 +44,8 @@ tm_status normal_core(const tm_gauge *g, const tm_field *out_e, const tm_field *
                       const tm_field *tmp_o, int pc, int dagger, cudaStream_t s, const int *act, int nact,
                       const RedArgs *red = nullptr);
 bool normal_red_supported(const tm_gauge *g, int prec, int dagger);
+tm_status adjoint_core(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o, int pc,
+                       int dagger, cudaStream_t s);
 tm_status normal_rupd_core(const tm_gauge *g, const tm_field *r_e, const tm_field *p_e, const tm_field *te_e,
                            const tm_field *tmp_o, int pc, cudaStream_t s, const RedArgs *red_a, const RedArgs *red_r,
                            const double *alpha_dev);
