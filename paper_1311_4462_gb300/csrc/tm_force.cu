@@ -70,6 +70,36 @@ __device__ __forceinline__ void load_sp(const void *base, const float *norm, int
         for (int c = 0; c < 3; c++) v[s][c] = {(T)r[2 * (3 * s + c)], (T)r[2 * (3 * s + c) + 1]};
 }
 
+// Complex multiply-adds as chains of fused multiply-adds.  binary32 pairs the real and imaginary
+// parts in one packed f32x2 FMA per step (the same rounding as the two scalar FMAs of that step),
+// so a complex multiply-add is two instructions instead of four.
+// s += a conj(b):  s.r += a.i b.i, s.i -= a.r b.i, then s.r += a.r b.r, s.i += a.i b.r
+template <typename T>
+__device__ __forceinline__ void cmacc(C<T> &s, C<T> a, C<T> b)
+{
+    s.r = fma(a.r, b.r, fma(a.i, b.i, s.r));
+    s.i = fma(a.i, b.r, fma(-a.r, b.i, s.i));
+}
+__device__ __forceinline__ void cmacc(C<float> &s, C<float> a, C<float> b)
+{
+    float2 t = __ffma2_rn(make_float2(a.i, -a.r), make_float2(b.i, b.i), make_float2(s.r, s.i));
+    t = __ffma2_rn(make_float2(a.r, a.i), make_float2(b.r, b.r), t);
+    s = {t.x, t.y};
+}
+// s += a b:  s.r -= a.i b.i, s.i += a.r b.i, then s.r += a.r b.r, s.i += a.i b.r
+template <typename T>
+__device__ __forceinline__ void cmac(C<T> &s, C<T> a, C<T> b)
+{
+    s.r = fma(a.r, b.r, fma(-a.i, b.i, s.r));
+    s.i = fma(a.i, b.r, fma(a.r, b.i, s.i));
+}
+__device__ __forceinline__ void cmac(C<float> &s, C<float> a, C<float> b)
+{
+    float2 t = __ffma2_rn(make_float2(-a.i, a.r), make_float2(b.i, b.i), make_float2(s.r, s.i));
+    t = __ffma2_rn(make_float2(a.r, a.i), make_float2(b.r, b.r), t);
+    s = {t.x, t.y};
+}
+
 // m += sum_{s=0,1} a_s b_s^dag (colour outer products of two projected half-spinors)
 template <typename T>
 __device__ __forceinline__ void outer_add(const C<T> a[2][3], const C<T> b[2][3], C<T> m[3][3])
@@ -79,10 +109,7 @@ __device__ __forceinline__ void outer_add(const C<T> a[2][3], const C<T> b[2][3]
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) {  // a_i conj(b_j)
-                m[i][j].r = fma(a[s][i].r, b[s][j].r, fma(a[s][i].i, b[s][j].i, m[i][j].r));
-                m[i][j].i = fma(a[s][i].i, b[s][j].r, fma(-a[s][i].r, b[s][j].i, m[i][j].i));
-            }
+            for (int j = 0; j < 3; j++) cmacc(m[i][j], a[s][i], b[s][j]);  // a_i conj(b_j)
 }
 
 // neighbour x + mu of site (x, y, z, t) with checkerboard index cb, and the boundary sign
@@ -139,7 +166,7 @@ __device__ __forceinline__ void gradient_core(const ForceArgs &a, T bc, LV loadv
             for (int j = 0; j < 3; j++) {
                 C<T> s = {T(0), T(0)};
 #pragma unroll
-                for (int k = 0; k < 3; k++) s = cadd(s, cmul(m[i][k], cconj(U.u[j][k])));
+                for (int k = 0; k < 3; k++) cmacc(s, m[i][k], U.u[j][k]);  // (m U^dag)_ij
                 zz[i][j] = s;
             }
         // TA(Z) = (Z - Z^dag)/2 - i Im tr(Z)/3 (the trace of (Z - Z^dag)/2 is i Im tr Z)
@@ -158,7 +185,7 @@ __device__ __forceinline__ void gradient_core(const ForceArgs &a, T bc, LV loadv
             for (int j = 0; j < 3; j++) {
                 C<T> s = {T(0), T(0)};
 #pragma unroll
-                for (int k = 0; k < 3; k++) s = cadd(s, cmul(ta[i][k], U.u[k][j]));
+                for (int k = 0; k < 3; k++) cmac(s, ta[i][k], U.u[k][j]);  // (TA U)_ij
                 m[i][j] = s;
             }
     }
@@ -184,17 +211,20 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
     gradient_core<MU, NF, T>(a, bc, loadv, loadu, m);
 }
 
-// One thread per site x (both parities, lexicographic order, so a block covers a contiguous run
+// One thread per site x (both parities, lexicographic order, so a warp covers a contiguous run
 // of the canonical output) computes its four links in turn, re-reading psi(x), g(x) from L1;
-// each link's 3x3 gradient goes through shared memory so that the block writes its contiguous
-// run of the canonical layout with 16-byte stores.  (Measured alternatives, slower at 24^3x48 in
-// FP32: one warp per direction and 32 sites, 143 us; every operand of a warp's links copied into
-// shared memory by cp.async first, 181-254 us; this form 133 us.)
-// the block's run of sites for direction MU: stage in shared memory, then 16-byte stores
+// each link's 3x3 gradient goes through the warp's part of a shared-memory tile so that the warp
+// writes its contiguous run of the canonical layout with 16-byte stores (warp-level syncs only: no
+// block barrier holds the other warps).  (Measured alternatives, slower at 24^3x48 in FP32: one
+// warp per direction and 32 sites, 143 us; every operand of a warp's links copied into shared
+// memory by cp.async first, 181-254 us; the same form as here with block barriers, 133 us.)
+// the warp's run of sites for direction MU: stage in shared memory, then 16-byte stores
 template <int MU, typename CT, typename T>
-__device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long V, bool valid, const C<T> m[3][3],
-                                           CT *tile)
+__device__ __forceinline__ void store_links(const ForceArgs &a, long V, bool valid, const C<T> m[3][3], CT *tile)
 {
+    const int lane = threadIdx.x & 31;
+    const long w0 = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);  // the warp's first site
+    CT *wt = tile + (threadIdx.x & ~31) * 9;
     if (valid) {
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -203,19 +233,23 @@ __device__ __forceinline__ void store_links(const ForceArgs &a, long lex0, long 
                 CT v;
                 v.x = m[i][j].r;
                 v.y = m[i][j].i;
-                tile[threadIdx.x * 9 + 3 * i + j] = v;
+                wt[lane * 9 + 3 * i + j] = v;
             }
     }
-    __syncthreads();
-    const long nsite = (V - lex0) < (long)blockDim.x ? (V - lex0) : (long)blockDim.x;
-    const long nvec = nsite * 9 * (long)sizeof(CT) / 16;  // 9 complex per site, a multiple of 16 bytes per 2 sites
-    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)MU * V + lex0) * 9);
-    const uint4 *src = reinterpret_cast<const uint4 *>(tile);
-    for (long k = threadIdx.x; k < nvec; k += blockDim.x) dst[k] = src[k];
-    // an odd number of complex64 sites leaves 8 bytes: written element-wise
-    if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && threadIdx.x == 0)
-        reinterpret_cast<CT *>(a.out)[((long)MU * V + lex0) * 9 + nsite * 9 - 1] = tile[nsite * 9 - 1];
-    __syncthreads();
+    __syncwarp();
+    const long nsite = (V - w0) < 32 ? (V - w0) : 32;
+    if (nsite > 0) {
+        // 9 complex per site: a multiple of 16 bytes per 2 sites, and the warp's run starts at an
+        // even site (w0 is a multiple of 32), so its output starts 16-byte aligned
+        const long nvec = nsite * 9 * (long)sizeof(CT) / 16;
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<CT *>(a.out) + ((long)MU * V + w0) * 9);
+        const uint4 *src = reinterpret_cast<const uint4 *>(wt);
+        for (long k = lane; k < nvec; k += 32) dst[k] = src[k];
+        // an odd number of complex64 sites leaves 8 bytes: written element-wise
+        if (sizeof(CT) == 8 && (nsite * 9) % 2 == 1 && lane == 0)
+            reinterpret_cast<CT *>(a.out)[((long)MU * V + w0) * 9 + nsite * 9 - 1] = wt[nsite * 9 - 1];
+    }
+    __syncwarp();  // the tile is rewritten by the next direction
 }
 
 template <int PREC, int RECON, int NF, typename CT>
@@ -226,7 +260,7 @@ __global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __gr
     const long V = 2L * a.Vh;
     const long lex0 = (long)blockIdx.x * blockDim.x;
     const long lex = lex0 + threadIdx.x;
-    const bool valid = lex < V;  // every thread takes part in the block's barriers
+    const bool valid = lex < V;  // every thread takes part in its warp's syncs
     int x = 0, y = 0, z = 0, t = 0, par = 0, cb = 0;
     if (valid) {
         long r = lex;
@@ -241,13 +275,13 @@ __global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __gr
     }
     C<T> m[3][3];
     if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
-    store_links<0>(a, lex0, V, valid, m, tile);
+    store_links<0>(a, V, valid, m, tile);
     if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
-    store_links<1>(a, lex0, V, valid, m, tile);
+    store_links<1>(a, V, valid, m, tile);
     if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
-    store_links<2>(a, lex0, V, valid, m, tile);
+    store_links<2>(a, V, valid, m, tile);
     if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m);
-    store_links<3>(a, lex0, V, valid, m, tile);
+    store_links<3>(a, V, valid, m, tile);
 }
 
 }  // namespace tmk
@@ -302,7 +336,7 @@ extern "C" tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, 
     const int block = 128;
     const long grid = (n + block - 1) / block;
     cudaStream_t s = (cudaStream_t)stream;
-    const int recon = g->p.recon;
+    const int recon = link_recon(g, pidx);
 #define TM_F1(P, R, CT) \
     if (g->nf == 1) k_force<P, R, 1, CT><<<grid, block, 0, s>>>(a); else k_force<P, R, 2, CT><<<grid, block, 0, s>>>(a);
 #define TM_FR(P, CT)                              \
