@@ -186,6 +186,35 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
     else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 }
 
+// The rank-2 projection (1 + sp g_MU) of one hop keeps spin rows h0, h1; each of their 12 reals
+// is one FMA  p[a] + q p[b]  with a in the upper spin rows (reals 0..11), b in the lower ones
+// (reals 12..23) and q = +-sp.  proj_term gives (b, sign of q) for real k = 6 row + 2 colour +
+// re/im of the projected rows (a = k).
+template <int MU>
+__device__ __forceinline__ constexpr int proj_b(int k)
+{
+    const int row = k / 6, c = (k % 6) / 2, im = k & 1;
+    // MU 0: h0 = p0 + sp i p3,  h1 = p1 + sp i p2      MU 1: h0 = p0 - sp p3,  h1 = p1 + sp p2
+    // MU 2: h0 = p0 + sp i p2,  h1 = p1 - sp i p3      MU 3: h0 = p0 + sp p2,  h1 = p1 + sp p3
+    const int lower = (MU == 0 || MU == 1) ? (row == 0 ? 3 : 2) : (row == 0 ? 2 : 3);
+    const bool times_i = (MU == 0 || MU == 2);
+    return 6 * lower + 2 * c + (times_i ? 1 - im : im);
+}
+template <int MU>
+__device__ __forceinline__ constexpr bool proj_neg(int k)
+{
+    const int row = k / 6, im = k & 1;
+    if (MU == 0) return im == 0;                      // i p: re takes -p.i
+    if (MU == 1) return row == 0;                     // -sp p3 for h0
+    if (MU == 2) return row == 0 ? im == 0 : im == 1; // +i p2 for h0, -i p3 for h1
+    return false;
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void pair_mul_acc(float (&acc)[2][24], const Link<float> &U, const float2 (&h0r)[3],
+                                             const float2 (&h0i)[3], const float2 (&h1r)[3], const float2 (&h1i)[3],
+                                             float sp, float2 sg);
+
 template <int MU, bool FWD, bool PACK>
 __device__ __forceinline__ void hop_pair(float (&acc)[2][24], const Link<float> &U, const float (&v)[2][24], float sp,
                                          float2 sg)
@@ -211,6 +240,78 @@ __device__ __forceinline__ void hop_pair(float (&acc)[2][24], const Link<float> 
             h1r[c] = pfma<PACK>(s, V(p3), V(p1)); h1i[c] = pfma<PACK>(s, V(p3 + 1), V(p1 + 1));
         }
     }
+    pair_mul_acc<MU, FWD>(acc, U, h0r, h0i, h1r, h1i, sp, sg);
+}
+
+// ---- binary16 neighbours: the projection straight from the stored halves ----
+// d = q h + c with h, q binary16 and c binary32 (Blackwell's mixed-precision FMA): both halves
+// widen exactly, so this is the binary32 FMA of the converted values with one rounding, and the
+// lower spin rows' halves never pass through a separate conversion.
+template <int HI>
+__device__ __forceinline__ float fma_f16(uint32_t w, unsigned short q, float c)
+{
+    float d;
+    if constexpr (HI)
+        asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\tfma.rn.f32.f16 %0, hi, %2, %3;\n\t}"
+            : "=f"(d) : "r"(w), "h"(q), "f"(c));
+    else
+        asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\tfma.rn.f32.f16 %0, lo, %2, %3;\n\t}"
+            : "=f"(d) : "r"(w), "h"(q), "f"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t chunk_word(const uint4 (&c)[3], int w)
+{
+    const uint4 &q = c[w >> 2];
+    return (w & 3) == 0 ? q.x : (w & 3) == 1 ? q.y : (w & 3) == 2 ? q.z : q.w;
+}
+// The 12 projected reals of one flavour (index as in proj_b) from its three raw 16-byte chunks:
+// the upper spin rows converted to binary32, the lower rows taken as halves by the FMA.  The
+// operations per value are those of hop_pair / hop_rows (the same FMA of the same operands).
+template <int MU>
+__device__ __forceinline__ void proj_f16(const uint4 (&c)[3], float sp, float (&h)[12])
+{
+    const unsigned short qp = sp > 0.f ? (unsigned short)0x3c00 : (unsigned short)0xbc00;  // binary16 +-1
+    const unsigned short qn = qp ^ (unsigned short)0x8000;
+    float a[12];
+#pragma unroll
+    for (int w = 0; w < 6; w++) {
+        const float2 f = h2f(chunk_word(c, w));
+        a[2 * w] = f.x;
+        a[2 * w + 1] = f.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const int b = proj_b<MU>(k);
+        const unsigned short q = proj_neg<MU>(k) ? qn : qp;
+        const uint32_t w = chunk_word(c, b >> 1);
+        h[k] = (b & 1) ? fma_f16<1>(w, q, a[k]) : fma_f16<0>(w, q, a[k]);
+    }
+}
+
+// hop_pair for binary16 neighbours (the two flavours' raw chunks; sg includes the site norms)
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_pair_f16(float (&acc)[2][24], const Link<float> &U, const uint4 (&s)[2][3],
+                                             float sp, float2 sg)
+{
+    float p0[12], p1[12];
+    proj_f16<MU>(s[0], sp, p0);
+    proj_f16<MU>(s[1], sp, p1);
+    float2 h0r[3], h0i[3], h1r[3], h1i[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        h0r[c] = make_float2(p0[2 * c], p1[2 * c]);
+        h0i[c] = make_float2(p0[2 * c + 1], p1[2 * c + 1]);
+        h1r[c] = make_float2(p0[6 + 2 * c], p1[6 + 2 * c]);
+        h1i[c] = make_float2(p0[7 + 2 * c], p1[7 + 2 * c]);
+    }
+    pair_mul_acc<MU, FWD>(acc, U, h0r, h0i, h1r, h1i, sp, sg);
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void pair_mul_acc(float (&acc)[2][24], const Link<float> &U, const float2 (&h0r)[3],
+                                             const float2 (&h0i)[3], const float2 (&h1r)[3], const float2 (&h1i)[3],
+                                             float sp, float2 sg)
+{
     // w = U h:      re = sum ur hr + ui (-hi),  im = sum ur hi + ui hr
     // w = U^dag h:  re = sum ur hr + ui hi,     im = sum ur hi + ui (-hr)   (u = U[b][a])
     const float2 m1 = make_float2(-1.f, -1.f);
@@ -280,6 +381,10 @@ __device__ __forceinline__ void hop_pair(float (&acc)[2][24], const Link<float> 
 // h0 and of h1 share a register pair and the link products are the packed FMAs of hop_pair.
 // The accumulator pairs rows (0, 1) and (2, 3); the hops whose lower rows take (h1, h0) in
 // swapped order (mu = x, y) accumulate those two rows with scalar FMAs instead of moving pairs.
+template <int MU, bool FWD>
+__device__ __forceinline__ void rows_mul_acc(float (&acc)[24], const Link<float> &U, const float2 (&hr)[3],
+                                             const float2 (&hi)[3], float sp, float sg);
+
 template <int MU, bool FWD, bool PACK>
 __device__ __forceinline__ void hop_rows(float (&acc)[24], const Link<float> &U, const float (&v)[24], float sp, float sg)
 {
@@ -300,6 +405,29 @@ __device__ __forceinline__ void hop_rows(float (&acc)[24], const Link<float> &U,
             hr[c] = pfma<PACK>(s, V(2, 3, r), V(0, 1, r)); hi[c] = pfma<PACK>(s, V(2, 3, i), V(0, 1, i));
         }
     }
+    rows_mul_acc<MU, FWD>(acc, U, hr, hi, sp, sg);
+}
+
+// hop_rows for a binary16 neighbour (its raw chunks; sg includes the site norm)
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_rows_f16(float (&acc)[24], const Link<float> &U, const uint4 (&s)[3], float sp,
+                                             float sg)
+{
+    float p[12];
+    proj_f16<MU>(s, sp, p);
+    float2 hr[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        hr[c] = make_float2(p[2 * c], p[6 + 2 * c]);
+        hi[c] = make_float2(p[2 * c + 1], p[7 + 2 * c]);
+    }
+    rows_mul_acc<MU, FWD>(acc, U, hr, hi, sp, sg);
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void rows_mul_acc(float (&acc)[24], const Link<float> &U, const float2 (&hr)[3],
+                                             const float2 (&hi)[3], float sp, float sg)
+{
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 g[3];  // -hi (forward) or -hr (backward)
 #pragma unroll
@@ -856,7 +984,12 @@ __device__ __forceinline__ void compute_hop(T (&acc)[NF][24], const HopRaw<PREC,
 {
     Link<T> U;
     decode_link_raw<PREC, RECON, NF>(r, U);
-    if constexpr (PAIR && NF == 2 && std::is_same<T, float>::value) {
+    if constexpr (PAIR && NF == 2 && PREC == P16 && !PRO) {
+        // the site norms fold into the per-flavour scale; the projection reads the halves
+        hop_pair_f16<MU, FWD>(acc, U, r.s, sp, make_float2(sg * r.n[0], sg * r.n[1]));
+    } else if constexpr (PAIR && NF == 1 && PREC == P16 && !PRO) {
+        hop_rows_f16<MU, FWD>(acc[0], U, r.s[0], sp, sg * r.n[0]);
+    } else if constexpr (PAIR && NF == 2 && std::is_same<T, float>::value) {
         float v[2][24];
         spinor_from_chunks<PREC>(r.s[0], v[0]);
         spinor_from_chunks<PREC>(r.s[1], v[1]);
