@@ -231,13 +231,24 @@ struct Link {
     C<T> u[3][3];
 };
 
-// row 3 of an SU(3) matrix from rows 1 and 2: conj(row1 x row2)
+// row 3 of an SU(3) matrix from rows 1 and 2: conj(row1 x row2).  Element k is
+// conj(a_j b_l - a_l b_j) with (j, l) the cyclic successors of k; each real part is one chain of
+// four FMAs (no separate subtraction of two rounded products).
+template <typename T>
+__device__ __forceinline__ C<T> cross_conj(C<T> aj, C<T> bl, C<T> al, C<T> bj)
+{
+    // re = aj.r bl.r - aj.i bl.i - al.r bj.r + al.i bj.i
+    // im = -(aj.r bl.i + aj.i bl.r) + al.r bj.i + al.i bj.r
+    const T re = fma(aj.r, bl.r, fma(-aj.i, bl.i, fma(-al.r, bj.r, al.i * bj.i)));
+    const T im = fma(-aj.r, bl.i, fma(-aj.i, bl.r, fma(al.r, bj.i, al.i * bj.r)));
+    return {re, im};
+}
 template <typename T>
 __device__ __forceinline__ void complete_row3(Link<T> &U)
 {
-    U.u[2][0] = cconj(csub(cmul(U.u[0][1], U.u[1][2]), cmul(U.u[0][2], U.u[1][1])));
-    U.u[2][1] = cconj(csub(cmul(U.u[0][2], U.u[1][0]), cmul(U.u[0][0], U.u[1][2])));
-    U.u[2][2] = cconj(csub(cmul(U.u[0][0], U.u[1][1]), cmul(U.u[0][1], U.u[1][0])));
+    U.u[2][0] = cross_conj(U.u[0][1], U.u[1][2], U.u[0][2], U.u[1][1]);
+    U.u[2][1] = cross_conj(U.u[0][2], U.u[1][0], U.u[0][0], U.u[1][2]);
+    U.u[2][2] = cross_conj(U.u[0][0], U.u[1][1], U.u[0][1], U.u[1][0]);
 }
 
 // 8-real form: r = (a2, a3, b1, arg a1, arg c1) with U = [[a1,a2,a3],[b1,b2,b3],[c1,c2,c3]].

@@ -312,24 +312,17 @@ __device__ __forceinline__ void pair_mul_acc(float (&acc)[2][24], const Link<flo
                                              const float2 (&h0i)[3], const float2 (&h1r)[3], const float2 (&h1i)[3],
                                              float sp, float2 sg)
 {
-    // w = U h:      re = sum ur hr + ui (-hi),  im = sum ur hi + ui hr
-    // w = U^dag h:  re = sum ur hr + ui hi,     im = sum ur hi + ui (-hr)   (u = U[b][a])
-    const float2 m1 = make_float2(-1.f, -1.f);
-    float2 g0[3], g1[3];  // the negated pair of each colour: -hi (forward) or -hr (backward)
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        g0[c] = __fmul2_rn(m1, FWD ? h0i[c] : h0r[c]);
-        g1[c] = __fmul2_rn(m1, FWD ? h1i[c] : h1r[c]);
-    }
+    // w = U h:      re = sum ur hr + (-ui) hi,  im = sum ur hi + ui hr
+    // w = U^dag h:  re = sum ur hr + ui hi,     im = sum ur hi + (-ui) hr   (u = U[b][a])
+    // The minus sign rides on the broadcast link element (a sign flip of one value per element,
+    // no arithmetic on the projected pairs); (-ui) x = -(ui x) exactly, so the bits do not change.
     float2 w0r[3], w0i[3], w1r[3], w1i[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             const C<float> u = FWD ? U.u[a][b] : U.u[b][a];
-            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i);
-            const float2 x0 = FWD ? g0[b] : h0i[b], x1 = FWD ? g1[b] : h1i[b];  // partner of ui in re
-            const float2 y0 = FWD ? h0r[b] : g0[b], y1 = FWD ? h1r[b] : g1[b];  // partner of ui in im
+            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i), nui = make_float2(-u.i, -u.i);
             if (b == 0) {
                 w0r[a] = __fmul2_rn(ur, h0r[b]); w0i[a] = __fmul2_rn(ur, h0i[b]);
                 w1r[a] = __fmul2_rn(ur, h1r[b]); w1i[a] = __fmul2_rn(ur, h1i[b]);
@@ -337,8 +330,8 @@ __device__ __forceinline__ void pair_mul_acc(float (&acc)[2][24], const Link<flo
                 w0r[a] = __ffma2_rn(ur, h0r[b], w0r[a]); w0i[a] = __ffma2_rn(ur, h0i[b], w0i[a]);
                 w1r[a] = __ffma2_rn(ur, h1r[b], w1r[a]); w1i[a] = __ffma2_rn(ur, h1i[b], w1i[a]);
             }
-            w0r[a] = __ffma2_rn(ui, x0, w0r[a]); w0i[a] = __ffma2_rn(ui, y0, w0i[a]);
-            w1r[a] = __ffma2_rn(ui, x1, w1r[a]); w1i[a] = __ffma2_rn(ui, y1, w1i[a]);
+            w0r[a] = __ffma2_rn(FWD ? nui : ui, h0i[b], w0r[a]); w0i[a] = __ffma2_rn(FWD ? ui : nui, h0r[b], w0i[a]);
+            w1r[a] = __ffma2_rn(FWD ? nui : ui, h1i[b], w1r[a]); w1i[a] = __ffma2_rn(FWD ? ui : nui, h1r[b], w1i[a]);
         }
     }
     // accumulate the four spin rows (the same reconstruction as hop_one)
@@ -428,17 +421,13 @@ template <int MU, bool FWD>
 __device__ __forceinline__ void rows_mul_acc(float (&acc)[24], const Link<float> &U, const float2 (&hr)[3],
                                              const float2 (&hi)[3], float sp, float sg)
 {
-    const float2 m1 = make_float2(-1.f, -1.f);
-    float2 g[3];  // -hi (forward) or -hr (backward)
-#pragma unroll
-    for (int c = 0; c < 3; c++) g[c] = __fmul2_rn(m1, FWD ? hi[c] : hr[c]);
-    float2 wr[3], wi[3];  // (w0, w1) = U (h0, h1) or U^dag (h0, h1)
+    float2 wr[3], wi[3];  // (w0, w1) = U (h0, h1) or U^dag (h0, h1); signs as in pair_mul_acc
 #pragma unroll
     for (int a = 0; a < 3; a++) {
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             const C<float> u = FWD ? U.u[a][b] : U.u[b][a];
-            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i);
+            const float2 ur = make_float2(u.r, u.r), ui = make_float2(u.i, u.i), nui = make_float2(-u.i, -u.i);
             if (b == 0) {
                 wr[a] = __fmul2_rn(ur, hr[b]);
                 wi[a] = __fmul2_rn(ur, hi[b]);
@@ -446,8 +435,8 @@ __device__ __forceinline__ void rows_mul_acc(float (&acc)[24], const Link<float>
                 wr[a] = __ffma2_rn(ur, hr[b], wr[a]);
                 wi[a] = __ffma2_rn(ur, hi[b], wi[a]);
             }
-            wr[a] = __ffma2_rn(ui, FWD ? g[b] : hi[b], wr[a]);
-            wi[a] = __ffma2_rn(ui, FWD ? hr[b] : g[b], wi[a]);
+            wr[a] = __ffma2_rn(FWD ? nui : ui, hi[b], wr[a]);
+            wi[a] = __ffma2_rn(FWD ? ui : nui, hr[b], wi[a]);
         }
     }
     const float q = sg * sp;
