@@ -484,9 +484,14 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
             apply_twist<T, NF>(a.tw_pro, v);
             hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg, sg));
         } else if constexpr (PREC == P16) {
-            const float n0 = load_spinor_f16_unscaled(in, a.in_norm, nb, a.Vh, v[0]);
-            const float n1 = load_spinor_f16_unscaled(in + fstride, a.in_norm + (size_t)a.Vh, nb, a.Vh, v[1]);
-            hop_pair<MU, FWD, true>(acc, U, v, sp, make_float2(sg * n0, sg * n1));
+            // raw halves into the mixed-precision projection; the site norms fold into the scale
+            uint4 c[2][3];
+#pragma unroll
+            for (int f = 0; f < 2; f++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) c[f][k] = ldg(reinterpret_cast<const uint4 *>(in + f * fstride) + (size_t)k * a.Vh + nb);
+            const float n0 = __ldg(a.in_norm + nb), n1 = __ldg(a.in_norm + (size_t)a.Vh + nb);
+            hop_pair_f16<MU, FWD>(acc, U, c, sp, make_float2(sg * n0, sg * n1));
         } else {
             load_spinor<PREC>(in, nullptr, nb, a.Vh, v[0]);
             load_spinor<PREC>(in + fstride, nullptr, nb, a.Vh, v[1]);
@@ -499,8 +504,10 @@ __device__ __forceinline__ void hop(T (&acc)[NF][24], const Link<T> &U, const Ds
             apply_twist<T, NF>(a.tw_pro, v);
             hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg);
         } else if constexpr (PREC == P16) {
-            const float n = load_spinor_f16_unscaled(in, a.in_norm, nb, a.Vh, v[0]);
-            hop_rows<MU, FWD, true>(acc[0], U, v[0], sp, sg * n);
+            uint4 c[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) c[k] = ldg(reinterpret_cast<const uint4 *>(in) + (size_t)k * a.Vh + nb);
+            hop_rows_f16<MU, FWD>(acc[0], U, c, sp, sg * __ldg(a.in_norm + nb));
         } else {
             load_spinor<PREC>(in, nullptr, nb, a.Vh, v[0]);
             hop_rows<MU, FWD, false>(acc[0], U, v[0], sp, sg);

@@ -211,6 +211,31 @@ __device__ __forceinline__ void link_gradient(const ForceArgs &a, int par, int c
     gradient_core<MU, NF, T>(a, bc, loadv, loadu, m);
 }
 
+// Ask L1 for the operands of direction MU that do not come from this site: the neighbour's psi
+// and g (every flavour, every chunk) and the link.  Issued one direction ahead, so their DRAM
+// latency overlaps the arithmetic of the current direction without holding registers.
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+template <int PREC, int RECON, int NF, int MU>
+__device__ __forceinline__ void prefetch_dir(const ForceArgs &a, int par, int cb, int x, int y, int z, int t)
+{
+    using SC = typename Traits<PREC>::schunk;
+    using LL = LinkLayout<PREC, RECON>;
+    typename Traits<PREC>::real bc;
+    const int nb = force_neighbour<MU>(a, cb, x, y, z, t, bc);
+    const SC *ps = reinterpret_cast<const SC *>(a.psi[1 - par]), *gs = reinterpret_cast<const SC *>(a.gv[1 - par]);
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+#pragma unroll
+        for (int k = 0; k < Traits<PREC>::SCHUNKS; k++) {
+            const size_t off = ((size_t)f * Traits<PREC>::SCHUNKS + k) * a.Vh + nb;
+            prefetch_l1(ps + off);
+            prefetch_l1(gs + off);
+        }
+    const typename LL::chunk *G = reinterpret_cast<const typename LL::chunk *>(a.gauge) + (size_t)(MU * 2 + par) * LL::N * a.Vh;
+#pragma unroll
+    for (int k = 0; k < LL::N; k++) prefetch_l1(G + (size_t)k * a.Vh + cb);
+}
+
 // One thread per site x (both parities, lexicographic order, so a warp covers a contiguous run
 // of the canonical output) computes its four links in turn, re-reading psi(x), g(x) from L1;
 // each link's 3x3 gradient goes through the warp's part of a shared-memory tile so that the warp
@@ -274,11 +299,20 @@ __global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __gr
         cb = (int)(lex >> 1);
     }
     C<T> m[3][3];
-    if (valid) link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
+    if (valid) {
+        prefetch_dir<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t);
+        link_gradient<PREC, RECON, NF, 0>(a, par, cb, x, y, z, t, m);
+    }
     store_links<0>(a, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
+    if (valid) {
+        prefetch_dir<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t);
+        link_gradient<PREC, RECON, NF, 1>(a, par, cb, x, y, z, t, m);
+    }
     store_links<1>(a, V, valid, m, tile);
-    if (valid) link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
+    if (valid) {
+        prefetch_dir<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t);
+        link_gradient<PREC, RECON, NF, 2>(a, par, cb, x, y, z, t, m);
+    }
     store_links<2>(a, V, valid, m, tile);
     if (valid) link_gradient<PREC, RECON, NF, 3>(a, par, cb, x, y, z, t, m);
     store_links<3>(a, V, valid, m, tile);
