@@ -145,6 +145,19 @@ tm_status tm_gauge_destroy(tm_gauge *g);
 tm_status tm_field_bytes(const tm_gauge *g, int prec, int nrhs, size_t *data_bytes, size_t *norm_bytes);
 
 /*
+ * Copy a field between device memory and host memory in the library's own layout (the bytes of
+ * data, and of norm for FP16, unchanged; tm_field_bytes() sizes), for clients that keep fields on
+ * the host in this form between host-driven steps or for checkpoints, so that no conversion
+ * pass runs.  The paper has no counterpart; this is a library-usage addition.  host_data /
+ * host_norm are host pointers (page-locked memory for the copies to be asynchronous); host_norm
+ * is ignored, and may be NULL, unless the field is FP16.  One cudaMemcpyAsync per array on
+ * `stream`.  Errors: TM_ERR_ARG (null pointers, bad field), TM_ERR_CUDA.
+ */
+tm_status tm_field_upload(const tm_gauge *g, const tm_field *dev, const void *host_data, const void *host_norm,
+                          void *stream);
+tm_status tm_field_download(const tm_gauge *g, void *host_data, void *host_norm, const tm_field *dev, void *stream);
+
+/*
  * Convert between the canonical full-lattice layout and one parity of a tm_field (the
  * "converting routines" between a client's layout and the internal one, sec. 2).  pack reads
  * the sites of `parity` from canon (canon_type = tm_canon); unpack writes only those sites of
@@ -180,8 +193,9 @@ tm_status tm_dslash_dagger(const tm_gauge *g, const tm_field *out, const tm_fiel
  *   TM_PC_ASYM:  out = (R_ee - kappa^2 H_eo R_oo^-1 H_oe) in               (eq. 2.2 LHS)
  *   TM_PC_SYM:   out = (1 - kappa^2 R_ee^-1 H_eo R_oo^-1 H_oe) in          (eq. 2.3 LHS)
  * dagger = 1 applies the adjoint (for SYM: 1 - kappa^2 H^dag_eo R_oo^-dag H^dag_oe R_ee^-dag,
- * whose first launch twists every neighbour before the projection).  Fields share one
- * precision; tmp_o is overwritten.
+ * whose first launch twists every neighbour before the projection; for DF64 and FP16 doublet
+ * fields R_ee^-dag in is instead one elementwise launch into out_e).  Fields share one
+ * precision; tmp_o is overwritten; out_e must not alias in_e or tmp_o.
  */
 tm_status tm_precond_op(const tm_gauge *g, const tm_field *out_e, const tm_field *in_e, const tm_field *tmp_o,
                         int pc, int dagger, void *stream);

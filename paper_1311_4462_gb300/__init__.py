@@ -132,6 +132,32 @@ class Field:
         return self
 
 
+def host_buffers(gauge: Gauge, prec=TM_PREC_F32, nrhs=1):
+    """Page-locked host tensors (data as uint8, norm as float32 or None) sized for a field in the
+    library's layout, for tm_field_upload / tm_field_download."""
+    torch = _torch()
+    nd, nn = gauge.field_bytes(prec, nrhs)
+    data = torch.empty(nd, dtype=torch.uint8).pin_memory()
+    norm = torch.empty(nn // 4, dtype=torch.float32).pin_memory() if nn else None
+    return data, norm
+
+
+def upload(gauge: Gauge, field: Field, host_data, host_norm=None, stream=None) -> Field:
+    """tm_field_upload: host copy of a field in the library's layout -> device Field."""
+    L.check(L.load().tm_field_upload(gauge.h, field.ref(), ctypes.c_void_p(host_data.data_ptr()),
+                                     ctypes.c_void_p(host_norm.data_ptr()) if host_norm is not None else None,
+                                     _stream(stream)))
+    return field
+
+
+def download(gauge: Gauge, field: Field, host_data, host_norm=None, stream=None):
+    """tm_field_download: device Field -> host copy in the library's layout."""
+    L.check(L.load().tm_field_download(gauge.h, ctypes.c_void_p(host_data.data_ptr()),
+                                       ctypes.c_void_p(host_norm.data_ptr()) if host_norm is not None else None,
+                                       field.ref(), _stream(stream)))
+    return host_data, host_norm
+
+
 def pack(gauge: Gauge, canon, parity: int, prec=TM_PREC_F32, nrhs=1, out: Field = None, stream=None) -> Field:
     """tm_pack: canonical complex128/complex64 device tensor -> one parity Field."""
     torch = _torch()

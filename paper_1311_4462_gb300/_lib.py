@@ -61,6 +61,8 @@ _SIGS = {
     "tm_gauge_destroy": [vp],
     "tm_field_bytes": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
                        ctypes.POINTER(ctypes.c_size_t)],
+    "tm_field_upload": [vp, FP, vp, vp, vp],
+    "tm_field_download": [vp, vp, vp, FP, vp],
     "tm_pack": [vp, FP, vp, ctypes.c_int, ctypes.c_int, vp],
     "tm_unpack": [vp, vp, ctypes.c_int, FP, ctypes.c_int, vp],
     "tm_dslash": [vp, FP, FP, ctypes.c_int, ctypes.c_int, FP, vp],

@@ -491,6 +491,15 @@ struct Twist {
     C<T> m[2][2][2];
 };
 
+// m0 a + m1 b with each real part one chain of four FMAs (no separate addition of two rounded
+// complex products)
+template <typename T>
+__device__ __forceinline__ C<T> cmul_add2(C<T> m0, C<T> a, C<T> m1, C<T> b)
+{
+    return {fma(m0.r, a.r, fma(-m0.i, a.i, fma(m1.r, b.r, -m1.i * b.i))),
+            fma(m0.r, a.i, fma(m0.i, a.r, fma(m1.r, b.i, m1.i * b.r)))};
+}
+
 template <typename T, int NF>
 __device__ __forceinline__ void apply_twist(const Twist<T> &tw, T v[NF][24])
 {
@@ -506,8 +515,8 @@ __device__ __forceinline__ void apply_twist(const Twist<T> &tw, T v[NF][24])
                 v[0][k] = r.r; v[0][k + 1] = r.i;
             } else {
                 C<T> a = {v[0][k], v[0][k + 1]}, b = {v[NF - 1][k], v[NF - 1][k + 1]};
-                C<T> r0 = cadd(cmul(tw.m[g][0][0], a), cmul(tw.m[g][0][1], b));
-                C<T> r1 = cadd(cmul(tw.m[g][1][0], a), cmul(tw.m[g][1][1], b));
+                C<T> r0 = cmul_add2(tw.m[g][0][0], a, tw.m[g][0][1], b);
+                C<T> r1 = cmul_add2(tw.m[g][1][0], a, tw.m[g][1][1], b);
                 v[0][k] = r0.r; v[0][k + 1] = r0.i;
                 v[NF - 1][k] = r1.r; v[NF - 1][k + 1] = r1.i;
             }

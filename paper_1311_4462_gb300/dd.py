@@ -23,8 +23,8 @@ import math
 
 from . import _lib as L
 from . import (TM_EPI_TWINV, TM_EPI_TWINV_XPAY, TM_EPI_TWXPAY_ASYM, TM_EPI_TWXPAY_SYM, TM_EPI_XMAY_K2, TM_EPI_XPAY,
-               TM_PC_ASYM, TM_PREC_F64, Field,
-               Gauge, Params, _stream, axpby, dot, norm2, pack, unpack)
+               TM_PC_ASYM, TM_PREC_DF64, TM_PREC_F16, TM_PREC_F64, Field,
+               Gauge, Params, _stream, axpby, dot, norm2, pack, twist, unpack)
 
 
 def _torch():
@@ -250,8 +250,16 @@ def precond_op(slabs, outs, ins, tmps, transport, pc=TM_PC_ASYM, dagger=False):
     if not dagger:
         dslash(slabs, tmps, ins, 1, TM_EPI_TWINV, None, transport, False)
         return dslash(slabs, outs, tmps, 0, TM_EPI_TWXPAY_SYM, ins, transport, False)
-    # adjoint of the symmetric operator: R^-dag_ee on the input (prologue), then x - kappa^2 H^dag t
-    dslash(slabs, tmps, ins, 1, TM_EPI_TWINV, None, transport, True, twist_in=True)
+    # adjoint of the symmetric operator: R^-dag_ee on the input, then x - kappa^2 H^dag t.  The
+    # input twist is the first launch's prologue, or (DF64, and the FP16 doublet, as tm_precond_op
+    # does it) an elementwise pass into outs, which the last launch overwrites.
+    prec = ins[0].prec
+    if prec == TM_PREC_DF64 or (prec == TM_PREC_F16 and slabs[0].params.nf == 2):
+        for s, o, i in zip(slabs, outs, ins):
+            twist(s.g, o, i, inverse=True, dagger=True)
+        dslash(slabs, tmps, outs, 1, TM_EPI_TWINV, None, transport, True)
+    else:
+        dslash(slabs, tmps, ins, 1, TM_EPI_TWINV, None, transport, True, twist_in=True)
     return dslash(slabs, outs, tmps, 0, TM_EPI_XMAY_K2, ins, transport, True)
 
 

@@ -77,3 +77,5 @@ def test_host_side_parameter_validation_without_gpu(lib):
     assert lib.tm_field_bytes(None, 4, 1, ctypes.byref(d), ctypes.byref(n)) == L.TM_ERR_ARG
     assert lib.tm_gauge_set_clover(None, 1.0, None) == L.TM_ERR_ARG
     assert lib.tm_local_op(None, None, None, 0, 0, 0, None) == L.TM_ERR_ARG
+    assert lib.tm_field_upload(None, None, None, None, None) == L.TM_ERR_ARG
+    assert lib.tm_field_download(None, None, None, None, None) == L.TM_ERR_ARG
