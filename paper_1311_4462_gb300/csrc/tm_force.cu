@@ -278,7 +278,7 @@ __device__ __forceinline__ void store_links(const ForceArgs &a, long V, bool val
 }
 
 template <int PREC, int RECON, int NF, typename CT>
-__global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 4)) k_force(const __grid_constant__ ForceArgs a)
+__global__ void __launch_bounds__(128, (PREC == P64 ? 2 : 5)) k_force(const __grid_constant__ ForceArgs a)
 {
     using T = typename Traits<PREC>::real;
     __shared__ __align__(16) CT tile[128 * 9];
