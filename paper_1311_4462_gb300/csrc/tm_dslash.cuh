@@ -188,8 +188,8 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
 
 // The rank-2 projection (1 + sp g_MU) of one hop keeps spin rows h0, h1; each of their 12 reals
 // is one FMA  p[a] + q p[b]  with a in the upper spin rows (reals 0..11), b in the lower ones
-// (reals 12..23) and q = +-sp.  proj_term gives (b, sign of q) for real k = 6 row + 2 colour +
-// re/im of the projected rows (a = k).
+// (reals 12..23) and q = +-sp.  For real k = 6 row + 2 colour + re/im of the projected rows
+// (a = k), proj_b gives b and proj_neg whether q = -sp.
 template <int MU>
 __device__ __forceinline__ constexpr int proj_b(int k)
 {
