@@ -424,7 +424,9 @@ tm_status tm_autotune(tm_gauge *g, void *stream);
  * right-hand side of an even count, two sources at a time through the doublet's staged kernels
  * (a one-flavour field with 2k sources has a doublet field's layout with k), else as 14; 32 / 34
  * / 36 = 12 / 14 / 16 with the blocks ordered group by group (one sweep over the sites per group
- * of sources) instead of interleaving the groups of a site block; clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
+ * of sources) instead of interleaving the groups of a site block; for FP16 also 13 / 15 (33 / 35):
+ * 12 / 14 (32 / 34) with three staging buffers, used for the doublet without the input prologue
+ * (otherwise they run as 12 / 14); clover entries "f32:c:3" = precision:c:resident 128-thread blocks per SM the clover
  * kernel's register allocation allows (1, 3 or 4), or 6 for its shared-memory staged pipeline;
  * fused-operator entries "f32:p:1" = precision:p:1 when tm_precond_op runs as one fused launch
  * (FP64 and FP32; see tm_device_status).  Import accepts any subset of the entries; an

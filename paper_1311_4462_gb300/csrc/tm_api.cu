@@ -1375,10 +1375,13 @@ tm_status tm_autotune(tm_gauge *g0, void *stream)
             f[k].nrhs = nr;
         }
         const Twist<double> Ri = make_twist(g, TW_RINV, 0);
-        const int rpbs[9] = {2, 4, 8, 12, 14, 32, 34, 16, 36};  // the paired forms last: one flavour only
+        // the paired forms only for one flavour, the three-buffer staged forms only for the FP16 doublet
+        const int rpbs[13] = {2, 4, 8, 12, 14, 32, 34, 16, 36, 13, 15, 33, 35};
         float best = 1e30f;
         int bestr = g->multi_rpb[pi];
-        for (int ri = 0; ri < (g->nf == 1 ? 9 : 7) && st == TM_OK; ri++) {
+        for (int ri = 0; ri < 13 && st == TM_OK; ri++) {
+            if (ri >= 7 && ri < 9 && g->nf != 1) continue;
+            if (ri >= 9 && (g->nf != 2 || pi != 2)) continue;
             g->multi_rpb[pi] = rpbs[ri];
             float ms = 0;
             for (int rep = 0; rep < 4 && st == TM_OK; rep++) {
@@ -1457,7 +1460,8 @@ tm_status tm_tune_import(tm_gauge *g, const char *text)
             // multi-RHS entry "<prec>:m:<right-hand sides per block>"
             const int pi = !strcmp(name, "f64") ? 0 : (!strcmp(name, "f32") ? 1 : (!strcmp(name, "f16") ? 2 : -1));
             const bool okm = block == 2 || block == 4 || block == 8 || block == 12 || block == 14 || block == 16 ||
-                             block == 32 || block == 34 || block == 36;
+                             block == 32 || block == 34 || block == 36 ||
+                             (pi == 2 && (block == 13 || block == 15 || block == 33 || block == 35));
             if (pi < 0 || !okm) {
                 set_error("tm_tune_import: invalid entry '%.32s'", p);
                 return TM_ERR_ARG;

@@ -1614,8 +1614,8 @@ cudaError_t launch_async(const DslashArgs<typename Traits<PREC>::real> &a, cudaS
 // the link chunks are copied with L1 allocation, so the RPB warps that read the same links are
 // served by one trip to L2, and consecutive blocks take the next RPB sources of the same sites,
 // so links leave DRAM about once per site for all sources.
-template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
-__global__ void __launch_bounds__(128, 3)
+template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR, int NB = 2>
+__global__ void __launch_bounds__(128, NB == 3 ? 2 : 3)
     k_dslash_multi_async(const __grid_constant__ DslashArgs<typename Traits<PREC>::real> a, const int *__restrict__ act,
                          int nact, int nrhs, int gmajor)
 {
@@ -1634,28 +1634,28 @@ __global__ void __launch_bounds__(128, 3)
     if (slot >= nact || cb >= a.Vh) return;
     const int rhs = act ? __ldg(act + slot) : slot;
     if (rhs < 0 || rhs >= nrhs) return;  // an index outside the fields is skipped, never dereferenced
-    async_site<PREC, NF, RECON, false, 2, PRO, false, PAIR, true>(a, (int)cb, tid, smem_async, nullptr, nullptr, 0, rhs);
+    async_site<PREC, NF, RECON, false, NB, PRO, false, PAIR, true>(a, (int)cb, tid, smem_async, nullptr, nullptr, 0, rhs);
 }
 
-template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR>
+template <int PREC, int NF, int RECON, bool PRO, int RPB, bool PAIR, int NB = 2>
 cudaError_t launch_multi_async(const DslashArgs<typename Traits<PREC>::real> &a, const int *act, int nact, int nrhs,
                                bool gmajor, cudaStream_t s)
 {
-    constexpr int bytes = 2 * AsyncHop<PREC, RECON, NF>::BUF;
+    constexpr int bytes = NB * AsyncHop<PREC, RECON, NF>::BUF;
     static std::atomic<unsigned long long> opted{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(opted.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR>,
+        e = cudaFuncSetAttribute(k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR, NB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         opted.fetch_or(bit, std::memory_order_acq_rel);
     }
     constexpr int SPB = 128 / RPB;  // sites per block
     const unsigned grid = (unsigned)(((long)a.Vh + SPB - 1) / SPB * ((nact + RPB - 1) / RPB));
-    k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR><<<grid, 128, bytes, s>>>(a, act, nact, nrhs, gmajor ? 1 : 0);
+    k_dslash_multi_async<PREC, NF, RECON, PRO, RPB, PAIR, NB><<<grid, 128, bytes, s>>>(a, act, nact, nrhs, gmajor ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1869,10 +1869,29 @@ cudaError_t launch_dslash_multi_impl(const DslashArgs<typename Traits<PREC>::rea
                                      const int *act, int nact, int nrhs, int rpb, cudaStream_t s)
 {
     // staged forms: 12 / 14 (2 / 4 per block, interleaved order), + 20 for the group-major order;
-    // 16 / 36 (paired sources) are arranged by the caller, otherwise they run as 14 / 34
+    // 16 / 36 (paired sources) are arranged by the caller, otherwise they run as 14 / 34;
+    // 13 / 15 (+ 20): the same with three staging buffers (two hops in flight, as the single-RHS
+    // form 9) for the binary16 doublet without the input prologue; every other case runs 12 / 14
     const bool gmajor = rpb >= 32;
     if (gmajor) rpb -= 20;
     if (rpb == 16) rpb = 14;
+    if (rpb == 13 || rpb == 15) {
+        if constexpr (PREC == P16) {
+#define TM_MB1(R)                                                                                         \
+    return rpb == 13 ? launch_multi_async<PREC, 2, R, false, 2, true, 3>(a, act, nact, nrhs, gmajor, s)   \
+                     : launch_multi_async<PREC, 2, R, false, 4, true, 3>(a, act, nact, nrhs, gmajor, s);
+            if (nf == 2 && !pro) {
+                switch (recon) {
+                case 18: TM_MB1(18)
+                case 12: TM_MB1(12)
+                case 8: TM_MB1(8)
+                default: return cudaErrorInvalidValue;
+                }
+            }
+#undef TM_MB1
+        }
+        rpb -= 1;
+    }
     if (rpb == 12 || rpb == 14) {
         // staged multi-RHS forms, 2 or 4 right-hand sides per block; the hop pairs as form 8 / 9 does
         // (binary32 and binary16, except one flavour with 18-real links)

@@ -285,13 +285,16 @@ def test_autotune_roundtrip_and_parity():
     clov = [e for e in entries if e.split(":")[1] == "c"]
     fused = [e for e in entries if e.split(":")[1] == "p"]
     assert len(single) == 6 and all(len(e.split(":")) == 4 for e in single)
-    assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8", "12", "14", "16", "32", "34", "36") for e in multi)
+    assert len(multi) == 3 and all(e.split(":")[2] in ("2", "4", "8", "12", "14", "16", "32", "34", "36")
+                                   or (e.startswith("f16") and e.split(":")[2] in ("13", "15", "33", "35"))
+                                   for e in multi)
     assert len(clov) == 3 and all(e.split(":")[2] in ("1", "3", "4", "6") for e in clov)
     assert len(fused) == 2 and all(e.split(":")[2] in ("0", "1") for e in fused)
     tmq.tune_import(g, table)
     assert tmq.tune_export(g) == table
     for bad in ("f32:0:3:100",   # block not a multiple of 32
                 "f32:m:3",       # right-hand sides per block not 2, 4 or 8 (or staged 12, 14)
+                "f32:m:15",      # three-buffer staged multi-RHS forms: FP16 only
                 "f16:c:2",       # clover occupancy not 1, 3 or 4
                 "f16:p:1",       # no fused FP16 operator
                 "f32:0:10:128",  # no such variant
