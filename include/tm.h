@@ -399,10 +399,10 @@ tm_status tm_force(const tm_gauge *g, void *F_canon, int canon_type, const tm_fi
  * Time every launch choice of the hopping kernel (thread per site with 64-256 threads per block,
  * the same with a two-stage load pipeline in registers or in shared memory, or with a
  * 128-register cap in three block shapes) for
- * each precision, with and without the input-twist prologue, and the multi-RHS block shape (2, 4
- * or 8 right-hand sides per block, timed on 8 right-hand sides), on this handle's lattice, and
+ * each precision, with and without the input-twist prologue, and the multi-RHS form (the tune
+ * entries below, timed on 16 right-hand sides, 8 in FP64), on this handle's lattice, and
  * keep the fastest; with a clover term also the clover kernel's form (1, 3 or 4 blocks per SM,
- * or the staged pipeline).  Allocates three single-RHS and three 8-RHS scratch fields for the duration of the call
+ * or the staged pipeline).  Allocates three single-RHS and three 16-RHS (FP64: 8-RHS) scratch fields for the duration of the call
  * (the multi-RHS shape keeps its default when the latter do not fit) and synchronises `stream`;
  * do not call it while capturing a graph.  Until it runs (or a table is imported) the handle
  * uses defaults (FP64 capped 128 x 4; FP32 and FP16 the shared-memory pipeline with the paired
