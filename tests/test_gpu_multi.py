@@ -33,16 +33,20 @@ def make(case, nrhs, recon=12):
 B3 = (13, 15, 33, 35)  # FP16 staged multi-RHS forms with three buffers
 
 
+RPB_IDS = {2: "rpb2", 4: "rpb4", 8: "rpb8", 12: "staged2", 14: "staged4", 16: "paired", 32: "staged2g",
+           34: "staged4g", 36: "pairedg", 13: "staged2b3", 15: "staged4b3", 33: "staged2gb3", 35: "staged4gb3"}
+
+
+def prec_rpb(rpbs):
+    """(precision, form) pairs: every form for every precision, the three-buffer forms for FP16 only."""
+    return [pytest.param(p, r, id=f"{p}-{RPB_IDS[r]}") for p in (8, 4, 2) for r in rpbs if r not in B3 or p == 2]
+
+
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("prec", [8, 4, 2])
-@pytest.mark.parametrize("rpb", [2, 4, 8, 12, 14, 16, 32, 34, 36, 13, 15, 33, 35],
-                         ids=["rpb2", "rpb4", "rpb8", "staged2", "staged4", "paired", "staged2g", "staged4g", "pairedg",
-                              "staged2b3", "staged4b3", "staged2gb3", "staged4gb3"])
+@pytest.mark.parametrize("prec,rpb", prec_rpb([2, 4, 8, 12, 14, 16, 32, 34, 36, 13, 15, 33, 35]))
 def test_multi_rhs_operators_match_oracle(case, prec, rpb):
     # not a multiple of any block shape: the last group of every shape is ragged; the paired-source
     # form (one flavour, two sources through the doublet's kernels) needs an even count
-    if rpb in B3 and prec != 2:
-        pytest.skip("the three-buffer multi-RHS forms are tune entries of FP16 only")
     nr = 6 if rpb in (16, 36) else 5
     tmq, p, po, U, g, src = make(case, nr)
     tmq.tune_import(g, f"f16:m:{rpb}" if rpb in B3 else f"f64:m:{rpb} f32:m:{rpb} f16:m:{rpb}")
@@ -191,14 +195,10 @@ def test_device_noise_matches_counter_definition(prec):
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("prec", [8, 4, 2])
-@pytest.mark.parametrize("rpb", [4, 14, 16, 34, 36, 15, 35],
-                         ids=["rpb4", "staged4", "paired", "staged4g", "pairedg", "staged4b3", "staged4gb3"])
+@pytest.mark.parametrize("prec,rpb", prec_rpb([4, 14, 16, 34, 36, 15, 35]))
 def test_multi_rhs_gives_the_single_rhs_bits(case, prec, rpb):
     """Every multi-RHS form (register, staged, paired sources, either block order) performs the same
     operations per source as the single-RHS forms, so each source's output has the same bits."""
-    if rpb in B3 and prec != 2:
-        pytest.skip("the three-buffer multi-RHS forms are tune entries of FP16 only")
     nr = 6
     tmq, p, po, U, g, src = make(case, nr)
     name = {8: "f64", 4: "f32", 2: "f16"}[prec]
